@@ -1,0 +1,198 @@
+"""jqcd oracle: plain FP64 CPU Wilson-Dirac operator, Schur complement and CG.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import this package.  It
+shares no code with the CUDA library (``paper_2409_03030_gb300``) and never
+imports it.  The arithmetic lives in ``jqcd_oracle.c`` (compiled with gcc);
+this module only marshals numpy arrays.
+
+All arrays are complex128 in the canonical host layouts of the generators in
+``paper_2409_03030_gb300.synth``: spinors ``[alpha, t, z, y, x, colour]`` and
+links ``[mu, t, z, y, x, b, a]`` (element (a, b) of U_mu).  ``dims`` is
+``(NX, NY, NZ, NT)``.  Even-odd routines take whole-lattice arrays whose
+other-parity sites are ignored on input and zero on output.
+
+Parity pins (tests marked ``not gpu``): free-field closed form, gauge
+covariance, adjointness and gamma5-hermiticity, a dense matrix assembled
+independently on 2^4 and 2^3x4 lattices (including the Schur complement), and
+CG against dense LU and the free-field inverse.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jqcd_oracle.c")
+_LIB = os.path.join(_HERE, "libjqcd_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over sites in the hop if available)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off"]
+    tmp = _LIB + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _configure(lib):
+    """Declare the C signatures on a loaded oracle library."""
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    c_int, c_double = ctypes.c_int, ctypes.c_double
+    lib.jo_gamma.argtypes = [dp]
+    lib.jo_hop.argtypes = [ip, c_int, dp, dp, dp, c_int, c_int]
+    lib.jo_dirac.argtypes = [ip, c_int, c_double, dp, dp, dp, c_int]
+    lib.jo_hop_sites.argtypes = [ip, c_int, dp, dp, c_int, i64p, ctypes.c_int64, dp]
+    lib.jo_schur.argtypes = [ip, c_int, c_double, dp, dp, dp, c_int]
+    lib.jo_normal_apply.argtypes = [ip, c_int, c_double, dp, c_int, dp, dp]
+    lib.jo_cg.argtypes = [ip, c_int, c_double, dp, c_int, dp, dp, c_double, c_int,
+                          ip, dp]
+    lib.jo_solve.argtypes = [ip, c_int, c_double, dp, c_int, dp, dp, c_double, c_int,
+                             ip, dp, dp]
+    lib.jo_zero_parity.argtypes = [ip, dp, c_int]
+    for name in ("jo_hop", "jo_dirac", "jo_hop_sites", "jo_schur", "jo_normal_apply",
+                 "jo_cg", "jo_solve", "jo_zero_parity"):
+        getattr(lib, name).restype = c_int
+    lib.jo_gamma.restype = None
+    return lib
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = _configure(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _dims(dims):
+    d = tuple(int(v) for v in dims)
+    if len(d) != 4 or min(d) < 1:
+        raise ValueError(f"bad dims {dims}")
+    return d, (ctypes.c_int * 4)(*d)
+
+
+def _p(a):
+    if a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError("oracle arrays must be C-contiguous complex128")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise RuntimeError(f"{what} failed with status {rc}")
+    return rc
+
+
+def _spinor(dims):
+    nx, ny, nz, nt = dims
+    return np.zeros((4, nt, nz, ny, nx, 3), dtype=np.complex128)
+
+
+def gamma() -> np.ndarray:
+    """The oracle's gamma matrices, shape (4, 4, 4), [mu, alpha, beta]."""
+    out = np.zeros((4, 4, 4), dtype=np.complex128)
+    _load().jo_gamma(_p(out))
+    return out
+
+
+def hop(dims, U, psi, dagger=False, out_parity=-1, t_antiperiodic=True):
+    """H psi (or the adjoint hop), at sites of `out_parity` (-1: all)."""
+    d, cd = _dims(dims)
+    out = _spinor(d)
+    _check(_load().jo_hop(cd, int(t_antiperiodic), _p(U), _p(psi), _p(out), int(dagger),
+                          int(out_parity)), "jo_hop")
+    return out
+
+
+def dirac(dims, U, psi, kappa, dagger=False, t_antiperiodic=True):
+    """D psi = psi - kappa H psi (paper: mul!(y, D, x)); dagger: D'."""
+    d, cd = _dims(dims)
+    out = _spinor(d)
+    _check(_load().jo_dirac(cd, int(t_antiperiodic), float(kappa), _p(U), _p(psi), _p(out),
+                            int(dagger)), "jo_dirac")
+    return out
+
+
+def hop_sites(dims, U, psi, sites, dagger=False, t_antiperiodic=True):
+    """(H psi) at the given lexicographic site indices; shape (n, 4, 3)."""
+    d, cd = _dims(dims)
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    out = np.zeros((len(s), 4, 3), dtype=np.complex128)
+    _check(_load().jo_hop_sites(cd, int(t_antiperiodic), _p(U), _p(psi), int(dagger),
+                                s.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(s),
+                                _p(out)), "jo_hop_sites")
+    return out
+
+
+def schur(dims, U, psi_e, kappa, dagger=False, t_antiperiodic=True):
+    """Mhat psi_e = psi_e - kappa^2 H_eo H_oe psi_e on even sites (dagger: Mhat^dag)."""
+    d, cd = _dims(dims)
+    out = _spinor(d)
+    _check(_load().jo_schur(cd, int(t_antiperiodic), float(kappa), _p(U), _p(psi_e), _p(out),
+                            int(dagger)), "jo_schur")
+    return out
+
+
+def normal_apply(dims, U, psi, kappa, eo=True, t_antiperiodic=True):
+    """Mhat^dag Mhat psi (eo) or D^dag D psi (not eo); paper: DdagD_operator."""
+    d, cd = _dims(dims)
+    out = _spinor(d)
+    _check(_load().jo_normal_apply(cd, int(t_antiperiodic), float(kappa), _p(U), int(bool(eo)),
+                                   _p(psi), _p(out)), "jo_normal_apply")
+    return out
+
+
+def cg(dims, U, rhs, kappa, eo=True, tol=1e-10, maxiter=10000, x0=None, t_antiperiodic=True):
+    """Textbook CG on the normal equations A x = rhs.  Returns (x, iters, true_rel, converged)."""
+    d, cd = _dims(dims)
+    x = _spinor(d) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
+    it = ctypes.c_int(0)
+    tr = ctypes.c_double(0)
+    rc = _check(_load().jo_cg(cd, int(t_antiperiodic), float(kappa), _p(U), int(bool(eo)),
+                              _p(rhs), _p(x), float(tol), int(maxiter), ctypes.byref(it),
+                              ctypes.byref(tr)), "jo_cg")
+    return x, it.value, tr.value, rc == 0
+
+
+def solve(dims, U, b, kappa, eo=True, tol=1e-10, maxiter=10000, t_antiperiodic=True):
+    """Solve D x = b (paper: solve_DinvX!).  Returns
+    (x, iters, system_true_rel, full_rel, converged)."""
+    d, cd = _dims(dims)
+    x = _spinor(d)
+    it = ctypes.c_int(0)
+    sr = ctypes.c_double(0)
+    fr = ctypes.c_double(0)
+    rc = _check(_load().jo_solve(cd, int(t_antiperiodic), float(kappa), _p(U), int(bool(eo)),
+                                 _p(b), _p(x), float(tol), int(maxiter), ctypes.byref(it),
+                                 ctypes.byref(sr), ctypes.byref(fr)), "jo_solve")
+    return x, it.value, sr.value, fr.value, rc == 0
+
+
+def zero_parity(dims, psi, parity):
+    """Copy of psi with the sites of `parity` set to zero."""
+    d, cd = _dims(dims)
+    out = np.array(psi, dtype=np.complex128, order="C")
+    _check(_load().jo_zero_parity(cd, _p(out), int(parity)), "jo_zero_parity")
+    return out
+
+
+def parity_mask(dims) -> np.ndarray:
+    """Boolean array [t, z, y, x]: True on odd sites."""
+    nx, ny, nz, nt = dims
+    t, z, y, x = np.meshgrid(np.arange(nt), np.arange(nz), np.arange(ny), np.arange(nx),
+                             indexing="ij")
+    return ((x + y + z + t) % 2) == 1

@@ -1,0 +1,69 @@
+"""Plant plausible mistakes in a copy of the oracle (CPU only) and check that
+the pins in test_oracle_pins catch every one of them."""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "jqcd_oracle.c")
+
+MUTATIONS = {
+    "gamma_x_sign": ("{{0, 0, 0, 1}, {0, 0, 1, 0}, {0, -1, 0, 0}, {-1, 0, 0, 0}},",
+                     "{{0, 0, 0, -1}, {0, 0, -1, 0}, {0, 1, 0, 0}, {1, 0, 0, 0}},"),
+    "backward_link_not_daggered": ("cconj(link(L, U, mu, y, b, a))", "link(L, U, mu, y, a, b)"),
+    "backward_link_transposed_only": ("cconj(link(L, U, mu, y, b, a))", "link(L, U, mu, y, b, a)"),
+    "backward_link_wrong_site": ("cconj(link(L, U, mu, y, b, a))", "cconj(link(L, U, mu, x, b, a))"),
+    "forward_link_transposed": ("link(L, U, mu, x, a, b) :", "link(L, U, mu, x, b, a) :"),
+    "spin_projector_swapped": ("double s = (dir == 0) ? -(double)sgn : (double)sgn;",
+                               "double s = (dir == 0) ? (double)sgn : -(double)sgn;"),
+    "no_backward_bc_sign": ("nc[mu] = L->n[mu] - 1;\n          if (mu == 3 && L->tanti) bc = -1.0;",
+                            "nc[mu] = L->n[mu] - 1;"),
+    "bc_on_wrong_axis": ("if (mu == 3 && L->tanti) bc = -1.0;\n        }\n      } else",
+                         "if (mu == 2 && L->tanti) bc = -1.0;\n        }\n      } else"),
+    "schur_kappa_not_squared": ("-kappa * kappa); /* out_e", "-kappa); /* out_e"),
+    "cg_beta_inverted": ("double beta = rr_new / rr;", "double beta = rr / rr_new;"),
+    "eo_reconstruction_sign": ("hop_axpy(&L, U, x, t, 1, 1, 0.0, kappa);",
+                               "hop_axpy(&L, U, x, t, 1, 1, 0.0, -kappa);"),
+    "eo_source_sign": ("hop_axpy(&L, U, b, t, 1, 0, 0.0, kappa);",
+                       "hop_axpy(&L, U, b, t, 1, 0, 0.0, -kappa);"),
+    "eo_rhs_without_dagger": ("schur(&L, kappa, U, t, rhs, -1, t2);",
+                              "schur(&L, kappa, U, t, rhs, 1, t2);"),
+}
+
+PINS = [
+    ("gamma_basis", lambda: pins.test_gamma_basis()),
+    ("free_field", lambda: [pins.test_free_field_closed_form(t, d) for t in (True, False)
+                            for d in (False, True)]),
+    ("gauge_covariance", lambda: pins.test_gauge_covariance(True)),
+    ("adjoint", lambda: pins.test_adjoint_and_gamma5_hermiticity()),
+    ("dense", lambda: pins.test_dense_brute_force((2, 2, 2, 4), True)),
+    ("cg_free", lambda: pins.test_cg_free_field_inverse()),
+]
+
+
+def _build_mutant(tmp_path, name):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation {name} does not match the oracle source"
+    path = tmp_path / f"{name}.c"
+    path.write_text(src.replace(old, new))
+    lib = tmp_path / f"lib_{name}.so"
+    subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-std=c11", str(path), "-o", str(lib),
+                    "-lm"], check=True)
+    return oracle._configure(ctypes.CDLL(str(lib)))
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_mutation(name, tmp_path, monkeypatch):
+    monkeypatch.setattr(oracle, "_lib", _build_mutant(tmp_path, name))
+    caught = []
+    for pin, fn in PINS:
+        try:
+            fn()
+        except (AssertionError, RuntimeError, ValueError, FloatingPointError):
+            caught.append(pin)
+    assert caught, f"no pin detects mutation {name}"
