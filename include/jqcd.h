@@ -1,0 +1,213 @@
+/*
+ * jqcd -- even-odd preconditioned Wilson-Dirac operator and conjugate-gradient
+ * solvers for one NVIDIA GB300 GPU (sm_103a).  C ABI.
+ *
+ * The method is the fermion part of JuliaQCD's two-flavour Wilson HMC
+ * (Nagai & Tomiya, arXiv:2409.03030): applying the Wilson-Dirac operator with
+ * hopping parameter kappa,
+ *     D = 1 - kappa H,
+ *     (H psi)(x) = sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                         + (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ * its adjoint D' and the normal operator D'D (paper, section "Definition of
+ * Dirac operators": Dirac_operator(U,x,params) with params "kappa",
+ * "eps_CG", "verbose_level"; mul!(y,D,x); solve_DinvX!(y,D,x); D';
+ * DdagD_operator), and the CG solve that dominates the fermion action and
+ * force (paper, "Definition of fermion actions" and "Hybrid Monte Carlo").
+ *
+ * Conventions fixed by this library where the paper is silent:
+ *  - gamma matrices: DeGrand-Rossi chiral basis, mu = 0..3 <-> x, y, z, t;
+ *  - boundaries periodic in x, y, z; if t_antiperiodic, every hop crossing
+ *    the time boundary carries a factor -1;
+ *  - even-odd: parity (x+y+z+t) mod 2, all extents even; the preconditioned
+ *    operator is the Schur complement on the even sites
+ *        Mhat = 1 - kappa^2 H_eo H_oe,
+ *    where H_eo maps odd sites to even sites;
+ *  - CG tolerance: relative 2-norm of the residual of the CG system,
+ *    ||rhs - A x|| / ||rhs|| <= tol, A = Mhat'Mhat (even-odd) or D'D.
+ *
+ * Host layouts (canonical; the column-major index order of JuliaQCD's
+ * x[ic,ix,iy,iz,it,ialpha] and U[a,b,ix,iy,iz,it], paper "Definition of
+ * pseudo-fermion fields"), complex numbers as interleaved (re, im) doubles:
+ *     site = ix + NX*(iy + NY*(iz + NZ*it))
+ *     spinor element (ic, site, alpha)  at complex index ic + 3*(site + V*alpha)
+ *     link element (a, b) of U_mu(site) at complex index a + 3*(b + 3*(site + V*mu))
+ *
+ * Device layouts are per parity (V/2 sites) and per precision; their sizes
+ * come from jqcd_spinor_bytes.  JQCD_PREC_DW ("double-word") stores every
+ * real as a pair of floats (hi, lo) -- 8 bytes per real like FP64, about 48
+ * significant bits -- and computes with error-free FP32 transformations; it
+ * is the library's FP64-class precision.  JQCD_PREC_F64 is IEEE double with
+ * native FP64 arithmetic.
+ *
+ * Errors: every call returns a jqcd_status and never aborts.  A message for
+ * the last failure is available from jqcd_last_error.  After a CUDA error
+ * raised by a kernel the context is poisoned: later calls return JQCD_ECUDA.
+ * Ownership: the library never frees caller memory.  Host inputs are copied
+ * during the call; device buffers passed to kernel-level calls stay owned by
+ * the caller and must stay valid until the work on `stream` has completed.
+ * Threading: one caller thread per context.
+ */
+#ifndef JQCD_H
+#define JQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JQCD_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define JQCD_API __attribute__((visibility("default")))
+#else
+#define JQCD_API
+#endif
+
+typedef struct jqcd_ctx jqcd_ctx;
+typedef int32_t jqcd_status;
+
+enum {
+  JQCD_OK = 0,
+  JQCD_EINVAL = -1,     /* bad argument (null pointer, odd extent, unknown id ...) */
+  JQCD_ENOMEM = -2,     /* device or host allocation failed */
+  JQCD_ECUDA = -3,      /* CUDA error; the context is poisoned */
+  JQCD_ENOCONV = -4,    /* solver reached maxiter; info is filled in */
+  JQCD_EBUSY = -5,      /* queue full (serving) */
+  JQCD_ETIMEOUT = -6,   /* a bounded device wait gave up */
+  JQCD_ENOTFOUND = -7,  /* unknown gauge id or ticket */
+  JQCD_EBREAKDOWN = -8, /* CG breakdown: <p, A p> <= 0 or not finite */
+  JQCD_PENDING = 1      /* serving: request not finished yet */
+};
+
+/* Device storage/arithmetic precisions. */
+enum {
+  JQCD_PREC_DW = 0,   /* FP64-class: float pairs, 8 B per real */
+  JQCD_PREC_F32 = 1,  /* FP32 spinors; FP32 links with 12 stored reals */
+  JQCD_PREC_F16N = 2, /* FP16 spinors scaled by a per-site FP32 norm; FP32 links */
+  JQCD_PREC_F64 = 3   /* IEEE FP64 spinors and links, native FP64 arithmetic */
+};
+
+typedef struct {
+  int32_t dims[4];        /* NX, NY, NZ, NT: each even and >= 2 */
+  int32_t t_antiperiodic; /* 1: antiperiodic in time, 0: periodic */
+} jqcd_lattice;
+
+JQCD_API int32_t jqcd_abi_version(void);
+
+/* Create a context on CUDA device `device` (makes it current for the calling
+ * thread).  *out receives the context; release it with jqcd_finalize. */
+JQCD_API jqcd_status jqcd_init(int device, jqcd_ctx **out);
+/* Free every gauge field and workspace of the context, then the context. */
+JQCD_API jqcd_status jqcd_finalize(jqcd_ctx *ctx);
+/* Message of the last failed call on ctx (never NULL; "" if none). */
+JQCD_API const char *jqcd_last_error(const jqcd_ctx *ctx);
+
+/* Upload a gauge field U_mu(x) (paper: Initialize_Gaugefields / the U passed
+ * to Dirac_operator).  `links`: host, 4*V SU(3) matrices in the canonical
+ * link layout, copied during the call.  The device copy is stored in every
+ * layout the precisions need (double-word 18 reals, FP64 18 reals, FP32 12
+ * reals with the third row recomputed as conj(row0 x row1), which assumes
+ * det U = 1).  flags: reserved, pass 0.  *gauge_id names the field in later
+ * calls. */
+JQCD_API jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const double *links,
+                              uint32_t flags, uint64_t *gauge_id);
+JQCD_API jqcd_status jqcd_gauge_free(jqcd_ctx *ctx, uint64_t gauge_id);
+
+/* Bytes of one parity of a spinor field of lattice `lat` in precision `prec`. */
+JQCD_API jqcd_status jqcd_spinor_bytes(const jqcd_lattice *lat, int32_t prec, size_t *bytes_per_parity);
+
+/* Convert a whole-lattice spinor between the canonical host layout (`host`,
+ * 12*V complex doubles) and the device layout of `prec` (two caller-owned
+ * device buffers of jqcd_spinor_bytes each), on `stream` (a cudaStream_t;
+ * NULL = legacy default stream).  pack returns once `host` has been read;
+ * unpack synchronises `stream` and returns with `host` written. */
+JQCD_API jqcd_status jqcd_spinor_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, int32_t prec,
+                             void *dev_even, void *dev_odd, void *stream);
+JQCD_API jqcd_status jqcd_spinor_unpack(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
+                               const void *dev_even, const void *dev_odd, double *host,
+                               void *stream);
+
+/* Even-odd hop (the hopping term of mul!(y,D,x), paper "Definition of Dirac
+ * operators"):
+ *     out_p = a * x_p + b * H_{p,1-p} in_{1-p}
+ * with p = out_parity (0 even, 1 odd); dagger != 0 uses the adjoint hop
+ * (gamma_mu -> -gamma_mu).  in, x, out: caller-owned device buffers in the
+ * layout of `prec`; x may be NULL (then a is ignored); out must not alias in.
+ * norm2_dev: NULL or a device double that receives ||out_p||^2.
+ * Asynchronous on `stream`. */
+JQCD_API jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, int32_t out_parity,
+                           int32_t dagger, const void *in, const void *x, void *out, double a,
+                           double b, double *norm2_dev, void *stream);
+
+/* out = Mhat' Mhat in on the even sites, Mhat = 1 - kappa^2 H_eo H_oe (the
+ * even-odd form of DdagD_operator, paper "Definition of Dirac operators").
+ * in, out: even-parity device buffers of `prec`, out must not alias in.
+ * norm2_dev: NULL or a device double receiving ||Mhat in||^2 = <in, out>.
+ * Uses a context-owned odd-parity temporary; asynchronous on `stream`. */
+JQCD_API jqcd_status jqcd_mdagm(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa, const void *in,
+                       void *out, double *norm2_dev, void *stream);
+
+/* Whole-lattice out = D in (dagger: D' in), paper mul!(y,D,x) and D'.
+ * Four caller-owned device buffers of `prec` (in and out must not alias). */
+JQCD_API jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa,
+                             int32_t dagger, const void *in_even, const void *in_odd,
+                             void *out_even, void *out_odd, void *stream);
+
+/* Solver modes. */
+enum {
+  JQCD_CG_DW = 0,        /* every vector and operator in double-word precision */
+  JQCD_CG_F64 = 1,       /* native FP64 operator and vectors */
+  JQCD_CG_MIXED_F32 = 2, /* FP32 inner CG, double-word reliable updates */
+  JQCD_CG_MIXED_F16 = 3  /* FP16+norm inner operator, FP32 inner vectors,
+                            double-word reliable updates */
+};
+
+typedef struct {
+  double kappa;      /* hopping parameter (paper params["kappa"]) */
+  double tol;        /* relative residual of the CG system (paper params["eps_CG"]) */
+  int32_t maxiter;   /* iteration cap, counted in operator applications of A */
+  int32_t eo;        /* 1: even-odd preconditioned, 0: CG on D'D, whole lattice */
+  int32_t mode;      /* JQCD_CG_* */
+  int32_t verbose;   /* 0 quiet; >= 3 prints residuals to stderr (paper verbose_level) */
+  double delta;      /* mixed modes: reliable-update threshold, 0 -> 0.1 */
+  int32_t use_x0;    /* 1: x holds the start vector on entry; 0: start from 0 */
+  int32_t reserved;
+} jqcd_solve_params;
+
+typedef struct {
+  int32_t iters;            /* CG iterations (applications of A) */
+  int32_t reliable_updates; /* mixed modes */
+  int32_t restarts;         /* restarts after a true-residual check failed */
+  int32_t status;           /* same as the return value */
+  double true_rel_resid;    /* ||rhs - A x|| / ||rhs|| of the CG system, recomputed
+                               in double-word after exit */
+  double full_rel_resid;    /* ||b - D x|| / ||b|| */
+  double seconds;           /* host wall time of the call */
+  double gpu_seconds;       /* device time of the solve proper (CUDA events) */
+  double hop_bytes;         /* algorithmic bytes moved by hop kernels */
+  double hop_count;         /* number of hop launches */
+} jqcd_solve_info;
+
+/* Solve D x = b (paper: solve_DinvX!(x, D, b) -- note this call orders its
+ * arguments input first, output second).  b, x: host, 12*V complex doubles
+ * in the canonical spinor layout; b is copied, x is written before return.
+ * Even-odd: bhat_e = b_e + kappa H_eo b_o, CG on Mhat'Mhat x_e = Mhat' bhat_e,
+ * x_o = b_o + kappa H_oe x_e.  Returns JQCD_OK on convergence of the CG
+ * system to `tol` (checked on the recomputed residual), JQCD_ENOCONV if
+ * maxiter was hit (x holds the last iterate).  info may be NULL. */
+JQCD_API jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                          const double *b, double *x, jqcd_solve_info *info);
+
+/* The same solve on device-resident fields: b_even, b_odd, x_even, x_odd are
+ * caller-owned device buffers in the JQCD_PREC_DW layout (x is used as the
+ * start vector when params->use_x0).  Synchronises `stream` before return. */
+JQCD_API jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                              const void *b_even, const void *b_odd, void *x_even, void *x_odd,
+                              jqcd_solve_info *info, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JQCD_H */

@@ -1,0 +1,335 @@
+// C-ABI entry points: context, gauge fields, spinor conversion, operator
+// applications and the conjugate-gradient drivers.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+
+#include "jqcd.h"
+#include "kernels.h"
+#include "solver.h"
+
+using namespace jqcd;
+
+struct jqcd_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool poisoned = false;
+  std::string err;
+  uint64_t next_id = 1;
+  std::map<uint64_t, std::unique_ptr<GaugeEntry>> gauges;
+};
+
+namespace {
+
+jqcd_status fail(jqcd_ctx *ctx, jqcd_status st, const char *fmt, ...) {
+  if (ctx) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    ctx->err = buf;
+  }
+  return st;
+}
+
+jqcd_status cuda_fail(jqcd_ctx *ctx, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(ctx, JQCD_ENOMEM, "%s: out of device memory", where);
+  }
+  ctx->poisoned = true;
+  return fail(ctx, JQCD_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+jqcd_status check_ctx(jqcd_ctx *ctx) {
+  if (!ctx) return JQCD_EINVAL;
+  if (ctx->poisoned) return fail(ctx, JQCD_ECUDA, "context poisoned by an earlier CUDA error");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  return JQCD_OK;
+}
+
+jqcd_status lattice_geom(jqcd_ctx *ctx, const jqcd_lattice *lat, Geom *g) {
+  if (!lat) return fail(ctx, JQCD_EINVAL, "lattice is NULL");
+  for (int d = 0; d < 4; ++d)
+    if (lat->dims[d] < 2 || (lat->dims[d] & 1))
+      return fail(ctx, JQCD_EINVAL, "extent %d of direction %d must be even and >= 2",
+                  lat->dims[d], d);
+  g->nx = lat->dims[0];
+  g->ny = lat->dims[1];
+  g->nz = lat->dims[2];
+  g->nt = lat->dims[3];
+  g->nxh = g->nx / 2;
+  const int64_t V = (int64_t)g->nx * g->ny * g->nz * g->nt;
+  if (V > ((int64_t)1 << 34)) return fail(ctx, JQCD_EINVAL, "lattice too large");
+  g->vh = V / 2;
+  g->tanti = lat->t_antiperiodic ? 1 : 0;
+  return JQCD_OK;
+}
+
+GaugeEntry *find_gauge(jqcd_ctx *ctx, uint64_t id) {
+  auto it = ctx->gauges.find(id);
+  return it == ctx->gauges.end() ? nullptr : it->second.get();
+}
+
+bool valid_prec(int32_t p) { return p >= 0 && p <= 3; }
+
+}  // namespace
+
+extern "C" {
+
+int32_t jqcd_abi_version(void) { return JQCD_ABI_VERSION; }
+
+jqcd_status jqcd_init(int device, jqcd_ctx **out) {
+  if (!out) return JQCD_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    return JQCD_ECUDA;
+  }
+  if (device < 0 || device >= n) return JQCD_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return JQCD_ECUDA;
+  std::unique_ptr<jqcd_ctx> ctx(new (std::nothrow) jqcd_ctx());
+  if (!ctx) return JQCD_ENOMEM;
+  ctx->device = device;
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) return JQCD_ECUDA;
+  *out = ctx.release();
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_finalize(jqcd_ctx *ctx) {
+  if (!ctx) return JQCD_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (!ctx->poisoned) cudaStreamSynchronize(ctx->stream);
+  ctx->gauges.clear();
+  if (ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return JQCD_OK;
+}
+
+const char *jqcd_last_error(const jqcd_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const double *links,
+                              uint32_t flags, uint64_t *gauge_id) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  if (!links || !gauge_id) return fail(ctx, JQCD_EINVAL, "links or gauge_id is NULL");
+  if (flags != 0) return fail(ctx, JQCD_EINVAL, "flags must be 0");
+  Geom g;
+  if ((st = lattice_geom(ctx, lat, &g))) return st;
+  std::unique_ptr<GaugeEntry> G(new GaugeEntry());
+  G->g = g;
+  const size_t canon_bytes = sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh);
+  const size_t dw_bytes = (size_t)16 * kLinkChunksDW * 8 * g.vh;
+  const size_t f64_bytes = (size_t)16 * kLinkChunksF64 * 8 * g.vh;
+  const size_t f32_bytes = (size_t)16 * kLinkChunksF32 * 8 * g.vh;
+  double *canon = nullptr;
+  CK(G->alloc(&G->gauge_dw, dw_bytes), "gauge alloc");
+  CK(G->alloc(&G->gauge_f64, f64_bytes), "gauge alloc");
+  CK(G->alloc(&G->gauge_f32, f32_bytes), "gauge alloc");
+  CK(cudaMalloc(&canon, canon_bytes), "gauge staging alloc");
+  cudaError_t e = cudaMemcpyAsync(canon, links, canon_bytes, cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = launch_gauge_pack(g, canon, G->gauge_dw, G->gauge_f64, G->gauge_f32, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(canon);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "gauge upload");
+  const uint64_t id = ctx->next_id++;
+  ctx->gauges[id] = std::move(G);
+  *gauge_id = id;
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_gauge_free(jqcd_ctx *ctx, uint64_t gauge_id) {
+  if (!ctx) return JQCD_EINVAL;
+  auto it = ctx->gauges.find(gauge_id);
+  if (it == ctx->gauges.end()) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id %llu",
+                                           (unsigned long long)gauge_id);
+  cudaSetDevice(ctx->device);
+  if (!ctx->poisoned) cudaDeviceSynchronize();
+  ctx->gauges.erase(it);
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_spinor_bytes(const jqcd_lattice *lat, int32_t prec, size_t *bytes) {
+  if (!bytes || !valid_prec(prec)) return JQCD_EINVAL;
+  Geom g;
+  if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
+  *bytes = spinor_parity_bytes(prec, g.vh);
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_spinor_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, int32_t prec,
+                             void *dev_even, void *dev_odd, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!host || !dev_even || !dev_odd || !valid_prec(prec))
+    return fail(ctx, JQCD_EINVAL, "spinor_pack: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_canon(), "staging alloc");
+  CK(cudaMemcpyAsync(G->canon, host, G->canon_bytes(), cudaMemcpyHostToDevice, s), "spinor H2D");
+  CK(launch_spinor_pack(G->g, prec, G->canon, dev_even, dev_odd, s), "spinor pack");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_spinor_unpack(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
+                               const void *dev_even, const void *dev_odd, double *host,
+                               void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!host || !dev_even || !dev_odd || !valid_prec(prec))
+    return fail(ctx, JQCD_EINVAL, "spinor_unpack: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_canon(), "staging alloc");
+  CK(launch_spinor_unpack(G->g, prec, dev_even, dev_odd, G->canon, s), "spinor unpack");
+  CK(cudaMemcpyAsync(host, G->canon, G->canon_bytes(), cudaMemcpyDeviceToHost, s), "spinor D2H");
+  CK(cudaStreamSynchronize(s), "spinor unpack sync");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, int32_t out_parity,
+                           int32_t dagger, const void *in, const void *x, void *out, double a,
+                           double b, double *norm2_dev, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in || !out || in == out || (out_parity != 0 && out_parity != 1) || !valid_prec(prec))
+    return fail(ctx, JQCD_EINVAL, "dslash_eo: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (norm2_dev) CK(G->ensure_reduce(), "workspace alloc");
+  HopParams P = G->hop_params(prec, out_parity, in, x, out, a, b, norm2_dev ? G->partials : nullptr);
+  CK(launch_hop(prec, P, dagger != 0, x != nullptr, norm2_dev != nullptr, s), "hop launch");
+  if (norm2_dev) CK(launch_finalize_sum(G->partials, (int)hop_blocks(G->g.vh), norm2_dev, s), "norm");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_mdagm(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa, const void *in,
+                       void *out, double *norm2_dev, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in || !out || in == out || !valid_prec(prec)) return fail(ctx, JQCD_EINVAL, "mdagm: bad argument");
+  CK(G->ensure_tmp(prec), "workspace alloc");
+  CK(G->ensure_reduce(), "workspace alloc");
+  CK(apply_mdagm(*G, prec, kappa, in, out, G->tmp[prec], G->tmp2[prec],
+                 norm2_dev ? G->partials : nullptr, nullptr, (cudaStream_t)stream),
+     "mdagm");
+  if (norm2_dev)
+    CK(launch_finalize_sum(G->partials, (int)hop_blocks(G->g.vh), norm2_dev, (cudaStream_t)stream), "norm");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa,
+                             int32_t dagger, const void *in_even, const void *in_odd,
+                             void *out_even, void *out_odd, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in_even || !in_odd || !out_even || !out_odd || !valid_prec(prec) || in_even == out_even ||
+      in_odd == out_odd || in_even == out_odd || in_odd == out_even)
+    return fail(ctx, JQCD_EINVAL, "dirac_apply: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  HopParams Pe = G->hop_params(prec, 0, in_odd, in_even, out_even, 1.0, -kappa, nullptr);
+  HopParams Po = G->hop_params(prec, 1, in_even, in_odd, out_odd, 1.0, -kappa, nullptr);
+  CK(launch_hop(prec, Pe, dagger != 0, true, false, s), "hop launch");
+  CK(launch_hop(prec, Po, dagger != 0, true, false, s), "hop launch");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                          const double *b, double *x, jqcd_solve_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !b || !x) return fail(ctx, JQCD_EINVAL, "cg_solve: bad argument");
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_solver(), "solver workspace alloc");
+  // host -> device: canonical b (and x0) into the solver's double-word vectors
+  CK(cudaMemcpyAsync(G->canon, b, G->canon_bytes(), cudaMemcpyHostToDevice, s), "b H2D");
+  CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->vec_even(G->vb), G->vec_odd(G->vb), s), "b pack");
+  if (params->use_x0) {
+    CK(cudaMemcpyAsync(G->canon, x, G->canon_bytes(), cudaMemcpyHostToDevice, s), "x0 H2D");
+    CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->vec_even(G->vsol), G->vec_odd(G->vsol), s),
+       "x0 pack");
+  }
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  std::string msg;
+  st = solve_resident(*G, *params, s, &inf, &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    CK(launch_spinor_unpack(G->g, PREC_DW, G->vec_even(G->vsol), G->vec_odd(G->vsol), G->canon, s),
+       "x unpack");
+    CK(cudaMemcpyAsync(x, G->canon, G->canon_bytes(), cudaMemcpyDeviceToHost, s), "x D2H");
+    CK(cudaStreamSynchronize(s), "solve sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (st != JQCD_OK) return fail(ctx, st, "cg_solve: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                              const void *b_even, const void *b_odd, void *x_even, void *x_odd,
+                              jqcd_solve_info *info, void *stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !b_even || !b_odd || !x_even || !x_odd)
+    return fail(ctx, JQCD_EINVAL, "cg_solve_dev: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_solver(), "solver workspace alloc");
+  const int64_t nh = 12 * G->g.vh;  // complex DW numbers per parity
+  CK(launch_dw_copy(G->vec_even(G->vb), (const float4 *)b_even, nh, s), "copy b");
+  CK(launch_dw_copy(G->vec_odd(G->vb), (const float4 *)b_odd, nh, s), "copy b");
+  if (params->use_x0) {
+    CK(launch_dw_copy(G->vec_even(G->vsol), (const float4 *)x_even, nh, s), "copy x0");
+    CK(launch_dw_copy(G->vec_odd(G->vsol), (const float4 *)x_odd, nh, s), "copy x0");
+  }
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  std::string msg;
+  st = solve_resident(*G, *params, s, &inf, &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    CK(launch_dw_copy((float4 *)x_even, G->vec_even(G->vsol), nh, s), "copy x");
+    CK(launch_dw_copy((float4 *)x_odd, G->vec_odd(G->vsol), nh, s), "copy x");
+    CK(cudaStreamSynchronize(s), "solve sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (st != JQCD_OK) return fail(ctx, st, "cg_solve_dev: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+}  // extern "C"

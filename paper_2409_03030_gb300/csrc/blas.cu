@@ -1,0 +1,223 @@
+// Vector kernels and the scalar steps of conjugate gradient.
+//
+// Double-word vectors are handled as flat arrays of float4 = one complex
+// double-word number (re.h, re.l, im.h, im.l).  Vector kernels use a fixed
+// grid with grid-stride loops, so the number of partial sums (and with it the
+// rounding of every reduction) depends only on the vector length.
+#include <cuda_runtime.h>
+
+#include "dw.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace jqcd {
+
+unsigned blas_blocks(int64_t n) {
+  const int64_t per = (int64_t)kBlasThreads * 4;
+  int64_t b = (n + per - 1) / per;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  return (unsigned)b;
+}
+
+__device__ __forceinline__ dw lo_dw(float h, float l) { return dw_make(h, l); }
+
+__device__ __forceinline__ void accum_sq4(dwacc &A, float4 v) {
+  acc_sq(A, dw_make(v.x, v.y));
+  acc_sq(A, dw_make(v.z, v.w));
+}
+
+__global__ void dw_copy_kernel(float4 *__restrict__ d, const float4 *__restrict__ s, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = s[i];
+}
+
+__global__ void dw_zero_kernel(float4 *__restrict__ d, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void dw_add_kernel(float4 *__restrict__ y, const float4 *__restrict__ x, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 a = y[i], b = x[i];
+    dw re = dw_add(dw_make(a.x, a.y), dw_make(b.x, b.y));
+    dw im = dw_add(dw_make(a.z, a.w), dw_make(b.z, b.w));
+    y[i] = make_float4(re.h, re.l, im.h, im.l);
+  }
+}
+
+__global__ void dw_norm2_kernel(const float4 *__restrict__ a, int64_t n, double *partials) {
+  dwacc A{0.f, 0.f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    accum_sq4(A, a[i]);
+  const double s = block_sum_dw(A);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void dw_xmy_norm_kernel(float4 *__restrict__ r, const float4 *__restrict__ b,
+                                   const float4 *__restrict__ y, int64_t n, double *partials) {
+  dwacc A{0.f, 0.f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 bv = b[i], yv = y[i];
+    dw re = dw_add(dw_make(bv.x, bv.y), dw_make(-yv.x, -yv.y));
+    dw im = dw_add(dw_make(bv.z, bv.w), dw_make(-yv.z, -yv.w));
+    r[i] = make_float4(re.h, re.l, im.h, im.l);
+    acc_sq(A, re);
+    acc_sq(A, im);
+  }
+  const double s = block_sum_dw(A);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void dw_cg_update_kernel(float4 *__restrict__ x, float4 *__restrict__ r,
+                                    const float4 *__restrict__ p, const float4 *__restrict__ Ap,
+                                    int64_t n, const SolverScalars *S, double *partials) {
+  if (S->done) return;
+  const dw al = dw_make(S->alpha_dw.x, S->alpha_dw.y);
+  const dw mal = dw_neg(al);
+  dwacc A{0.f, 0.f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 xv = x[i], pv = p[i], rv = r[i], av = Ap[i];
+    dw xr = dw_add(dw_make(xv.x, xv.y), dw_mul(al, dw_make(pv.x, pv.y)));
+    dw xi = dw_add(dw_make(xv.z, xv.w), dw_mul(al, dw_make(pv.z, pv.w)));
+    dw rr = dw_add(dw_make(rv.x, rv.y), dw_mul(mal, dw_make(av.x, av.y)));
+    dw ri = dw_add(dw_make(rv.z, rv.w), dw_mul(mal, dw_make(av.z, av.w)));
+    x[i] = make_float4(xr.h, xr.l, xi.h, xi.l);
+    r[i] = make_float4(rr.h, rr.l, ri.h, ri.l);
+    acc_sq(A, rr);
+    acc_sq(A, ri);
+  }
+  const double s = block_sum_dw(A);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void dw_xpay_kernel(float4 *__restrict__ p, const float4 *__restrict__ r, int64_t n,
+                               const SolverScalars *S) {
+  if (S->done) return;
+  const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 pv = p[i], rv = r[i];
+    dw pr = dw_add(dw_make(rv.x, rv.y), dw_mul(be, dw_make(pv.x, pv.y)));
+    dw pi = dw_add(dw_make(rv.z, rv.w), dw_mul(be, dw_make(pv.z, pv.w)));
+    p[i] = make_float4(pr.h, pr.l, pi.h, pi.l);
+  }
+}
+
+// ---- single-block scalar steps -------------------------------------------------
+__device__ __forceinline__ double sum_partials(const double *partials, int n) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+  return block_sum_d(v);  // valid in thread 0
+}
+
+__device__ __forceinline__ float2 split_d(double v) {
+  const float h = __double2float_rn(v);
+  return make_float2(h, __double2float_rn(v - (double)h));
+}
+
+__global__ void finalize_sum_kernel(const double *partials, int n, double *out) {
+  const double s = sum_partials(partials, n);
+  if (threadIdx.x == 0) *out = s;
+}
+
+__global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S) {
+  if (S->done) return;
+  const double pAp = sum_partials(partials, n);
+  if (threadIdx.x == 0) {
+    S->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {  // breakdown: A not positive or NaN
+      S->done = 2;
+      return;
+    }
+    const double a = S->rr / pAp;
+    S->alpha = a;
+    S->alpha_dw = split_d(a);
+    S->malpha_dw = split_d(-a);
+    S->alpha_f = (float)a;
+    S->malpha_f = (float)-a;
+  }
+}
+
+__global__ void cg_beta_kernel(const double *partials, int n, SolverScalars *S) {
+  if (S->done) return;
+  const double rr_new = sum_partials(partials, n);
+  if (threadIdx.x == 0) {
+    S->rr_new = rr_new;
+    S->iters += 1;
+    if (!isfinite(rr_new)) { S->done = 2; return; }
+    if (rr_new <= S->stop_rr) {
+      S->rr = rr_new;
+      S->done = 1;
+      return;
+    }
+    if (S->iters >= S->max_iters) S->done = 3;
+    const double b = rr_new / S->rr;
+    S->beta = b;
+    S->beta_dw = split_d(b);
+    S->beta_f = (float)b;
+    S->rr = rr_new;
+  }
+}
+
+__global__ void cg_start_kernel(const double *partials, int n, SolverScalars *S, double tol2,
+                                int max_iters) {
+  const double rr = sum_partials(partials, n);
+  if (threadIdx.x == 0) {
+    S->rr = rr;
+    S->stop_rr = tol2 * S->rhs2;
+    S->max_iters = max_iters;
+    S->done = rr <= S->stop_rr ? 1 : (S->iters >= max_iters ? 3 : 0);
+    S->rr_max = rr;
+  }
+}
+
+cudaError_t launch_finalize_sum(const double *partials, int n, double *out, cudaStream_t s) {
+  finalize_sum_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, out);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_copy(float4 *dst, const float4 *src, int64_t n, cudaStream_t s) {
+  dw_copy_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_zero(float4 *dst, int64_t n, cudaStream_t s) {
+  dw_zero_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(dst, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s) {
+  dw_add_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(y, x, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_norm2(const float4 *a, int64_t n, double *partials, cudaStream_t s) {
+  dw_norm2_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(a, n, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_xmy_norm(float4 *r, const float4 *b, const float4 *y, int64_t n,
+                               double *partials, cudaStream_t s) {
+  dw_xmy_norm_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(r, b, y, n, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const float4 *Ap, int64_t n,
+                                const SolverScalars *S, double *partials, cudaStream_t s) {
+  dw_cg_update_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(x, r, p, Ap, n, S, partials);
+  return cudaGetLastError();
+}
+cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
+                           cudaStream_t s) {
+  dw_xpay_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(p, r, n, S);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_alpha(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
+  cg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
+  cg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
+                            int max_iters, cudaStream_t s) {
+  cg_start_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S, tol2, max_iters);
+  return cudaGetLastError();
+}
+
+}  // namespace jqcd

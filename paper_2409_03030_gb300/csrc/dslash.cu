@@ -1,0 +1,173 @@
+// Even-odd Wilson hop kernels: out_p = a * x_p + b * H_{p,1-p} in_{1-p}
+// with an optional fused per-block partial of ||out_p||^2.
+//
+// One thread per output site.  Each of the 8 neighbours is loaded as a full
+// spinor (16-byte chunks, read-only path), spin-projected to a half-spinor,
+// multiplied by its link (streamed, each link is used once per hop) and
+// spread back onto four spins in registers.  Neighbour reuse across threads
+// is served by L1/L2: in the checkerboard order the x, y, z neighbours of a
+// warp's sites are within a few kB and the t neighbours within one time slice.
+#include <cuda_runtime.h>
+
+#include "fields.cuh"
+#include "hop.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace jqcd {
+
+template <int MU, int PREC, bool DAG>
+__device__ __forceinline__ void hop_dir(const HopParams &P, int x, int y, int z, int t,
+                                        int64_t idx, typename PT<PREC>::C (&acc)[4][3]) {
+  typedef PT<PREC> T;
+  typedef typename T::C C;
+  const Geom &g = P.g;
+  const int p = P.out_parity;
+  const char *gbase = reinterpret_cast<const char *>(P.gauge);
+  const size_t link_bytes = (size_t)T::kLinkChunks * 16 * g.vh;  // one (parity, mu) block
+  // forward neighbour x + mu: (1 - gamma_mu) U_mu(x) psi(x+mu)
+  {
+    int xf = x, yf = y, zf = z, tf = t;
+    bool neg = false;
+    if (MU == 0) xf = (x + 1 == g.nx) ? 0 : x + 1;
+    if (MU == 1) yf = (y + 1 == g.ny) ? 0 : y + 1;
+    if (MU == 2) zf = (z + 1 == g.nz) ? 0 : z + 1;
+    if (MU == 3) {
+      if (t + 1 == g.nt) { tf = 0; neg = g.tanti != 0; } else tf = t + 1;
+    }
+    const int64_t nf = cb_index(g, xf, yf, zf, tf);
+    C psi[4][3], h[2][3], r[2][3], u[3][3];
+    T::load_spinor(P.in, g.vh, nf, psi);
+    project<MU, DAG ? 1 : -1>(psi, h);
+    T::negate_if(h, neg);
+    T::load_link(gbase + link_bytes * (size_t)(p * 4 + MU), g.vh, idx, u);
+    matvec2<false>(u, h, r);
+    reconstruct<MU, DAG ? 1 : -1>(r, acc);
+  }
+  // backward neighbour x - mu: (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu)
+  {
+    int xb = x, yb = y, zb = z, tb = t;
+    bool neg = false;
+    if (MU == 0) xb = (x == 0) ? g.nx - 1 : x - 1;
+    if (MU == 1) yb = (y == 0) ? g.ny - 1 : y - 1;
+    if (MU == 2) zb = (z == 0) ? g.nz - 1 : z - 1;
+    if (MU == 3) {
+      if (t == 0) { tb = g.nt - 1; neg = g.tanti != 0; } else tb = t - 1;
+    }
+    const int64_t nb = cb_index(g, xb, yb, zb, tb);
+    C psi[4][3], h[2][3], r[2][3], u[3][3];
+    T::load_spinor(P.in, g.vh, nb, psi);
+    project<MU, DAG ? -1 : 1>(psi, h);
+    T::negate_if(h, neg);
+    T::load_link(gbase + link_bytes * (size_t)((1 - p) * 4 + MU), g.vh, nb, u);
+    matvec2<true>(u, h, r);
+    reconstruct<MU, DAG ? -1 : 1>(r, acc);
+  }
+}
+
+template <int PREC> __device__ __forceinline__ dwacc site_norm2(const typename PT<PREC>::C (&o)[4][3]);
+template <> __device__ __forceinline__ dwacc site_norm2<PREC_DW>(const cw (&o)[4][3]) {
+  dwacc A = acc_first(o[0][0].re, o[0][0].re);
+  acc_sq(A, o[0][0].im);
+#pragma unroll
+  for (int k = 1; k < 12; ++k) {
+    acc_sq(A, o[k / 3][k % 3].re);
+    acc_sq(A, o[k / 3][k % 3].im);
+  }
+  return A;
+}
+template <> __device__ __forceinline__ dwacc site_norm2<PREC_F64>(const cd (&o)[4][3]) {
+  double s = 0.;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s += o[k / 3][k % 3].re * o[k / 3][k % 3].re + o[k / 3][k % 3].im * o[k / 3][k % 3].im;
+  float h = (float)s;
+  return dwacc{h, (float)(s - (double)h)};
+}
+template <int PREC> __device__ __forceinline__ dwacc site_norm2_f(const cf (&o)[4][3]) {
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) s = fmaf(o[k / 3][k % 3].re, o[k / 3][k % 3].re, fmaf(o[k / 3][k % 3].im, o[k / 3][k % 3].im, s));
+  return dwacc{s, 0.f};
+}
+template <> __device__ __forceinline__ dwacc site_norm2<PREC_F32>(const cf (&o)[4][3]) { return site_norm2_f<PREC_F32>(o); }
+template <> __device__ __forceinline__ dwacc site_norm2<PREC_F16N>(const cf (&o)[4][3]) { return site_norm2_f<PREC_F16N>(o); }
+
+template <int PREC, bool DAG, bool AXPY, bool NORM>
+__global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
+  typedef PT<PREC> T;
+  typedef typename T::C C;
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = idx < P.g.vh;
+  dwacc nrm{0.f, 0.f};
+  if (active) {
+    int x, y, z, t;
+    cb_coords(P.g, idx, P.out_parity, x, y, z, t);
+    C acc[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[a][c] = T::zero();
+    hop_dir<0, PREC, DAG>(P, x, y, z, t, idx, acc);
+    hop_dir<1, PREC, DAG>(P, x, y, z, t, idx, acc);
+    hop_dir<2, PREC, DAG>(P, x, y, z, t, idx, acc);
+    hop_dir<3, PREC, DAG>(P, x, y, z, t, idx, acc);
+    const typename T::Scalar b = T::scalar(P.b, P.b_split);
+    C o[4][3];
+    if (AXPY) {
+      const typename T::Scalar a = T::scalar(P.a, P.a_split);
+      C xs[4][3];
+      T::load_spinor(P.x, P.g.vh, idx, xs);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::axpby(a, xs[s][c], b, acc[s][c]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::scale(b, acc[s][c]);
+    }
+    T::store_spinor(P.out, P.g.vh, idx, o);
+    if (NORM) nrm = site_norm2<PREC>(o);
+  }
+  if (NORM) {
+    const double s = block_sum_dw(nrm);
+    if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+  }
+}
+
+template <int PREC, bool DAG, bool AXPY, bool NORM>
+static cudaError_t launch_hop_t(const HopParams &P, cudaStream_t s) {
+  const unsigned blocks = hop_blocks(P.g.vh);
+  hop_kernel<PREC, DAG, AXPY, NORM><<<blocks, kHopThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool norm, cudaStream_t s) {
+  const int key = (dag ? 4 : 0) | (axpy ? 2 : 0) | (norm ? 1 : 0);
+  switch (key) {
+    case 0: return launch_hop_t<PREC, false, false, false>(P, s);
+    case 1: return launch_hop_t<PREC, false, false, true>(P, s);
+    case 2: return launch_hop_t<PREC, false, true, false>(P, s);
+    case 3: return launch_hop_t<PREC, false, true, true>(P, s);
+    case 4: return launch_hop_t<PREC, true, false, false>(P, s);
+    case 5: return launch_hop_t<PREC, true, false, true>(P, s);
+    case 6: return launch_hop_t<PREC, true, true, false>(P, s);
+    default: return launch_hop_t<PREC, true, true, true>(P, s);
+  }
+}
+
+cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool norm,
+                       cudaStream_t s) {
+  switch (prec) {
+    case PREC_DW: return launch_hop_p<PREC_DW>(P, dag, axpy, norm, s);
+    case PREC_F64: return launch_hop_p<PREC_F64>(P, dag, axpy, norm, s);
+    case PREC_F32: return launch_hop_p<PREC_F32>(P, dag, axpy, norm, s);
+    case PREC_F16N: return launch_hop_p<PREC_F16N>(P, dag, axpy, norm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace jqcd

@@ -1,0 +1,96 @@
+// Internal launch interface of the jqcd kernels (host side of the library).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lattice.cuh"
+
+namespace jqcd {
+
+constexpr int kHopThreads = 128;
+inline unsigned hop_blocks(int64_t vh) { return (unsigned)((vh + kHopThreads - 1) / kHopThreads); }
+
+struct HopParams {
+  void *out;
+  const void *in;
+  const void *x;      // same parity as out, used when axpy
+  const void *gauge;  // gauge field in the layout of the precision
+  Geom g;
+  int out_parity;
+  double a, b;        // out = a*x + b*H in
+  float2 a_split, b_split;
+  double *partials;   // one per hop block when norm
+  const int *guard;   // when non-null and *guard != 0 the launch does nothing
+};
+
+// out_p = a x_p + b H_{p,1-p} in (dag: adjoint hop); partials get per-block
+// ||out||^2 when norm.
+cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool norm,
+                       cudaStream_t s);
+
+// ---- layouts ----------------------------------------------------------------
+// Canonical FP64 links on the device -> every device layout requested
+// (null destination pointers are skipped).
+cudaError_t launch_gauge_pack(const Geom &g, const double *canon, void *dw, void *f64, void *f32,
+                              cudaStream_t s);
+// Canonical FP64 spinor (device) <-> per-parity device layout.
+cudaError_t launch_spinor_pack(const Geom &g, int prec, const double *canon, void *even, void *odd,
+                               cudaStream_t s);
+cudaError_t launch_spinor_unpack(const Geom &g, int prec, const void *even, const void *odd,
+                                 double *canon, cudaStream_t s);
+
+// ---- BLAS-1 and reductions ---------------------------------------------------
+constexpr int kBlasThreads = 256;
+constexpr int kReduceThreads = 256;
+unsigned blas_blocks(int64_t n);   // grid of the grid-stride vector kernels
+
+// Device-resident solver scalars.
+struct SolverScalars {
+  double rr;        // current ||r||^2
+  double rr_new;
+  double pAp;
+  double alpha, beta;
+  double stop_rr;   // stop when rr <= stop_rr
+  double rhs2;      // ||rhs||^2
+  double rr_max;    // mixed precision: max ||r_inner||^2 since last reliable update
+  double delta2;    // reliable update threshold (squared)
+  double true_rr;   // ||rhs - A x||^2 recomputed after the loop
+  double b2;        // ||b||^2 of the original system D x = b
+  double full_rr;   // ||b - D x||^2
+  double tmp0, tmp1;
+  float2 alpha_dw, beta_dw, malpha_dw;
+  float alpha_f, beta_f, malpha_f;
+  int done;         // 0 running, 1 converged, 2 breakdown, 3 iteration cap reached
+  int iters;
+  int need_update;  // mixed: reliable update requested
+  int max_iters;
+};
+
+// sum of partials[0..n) in a fixed order -> *out
+cudaError_t launch_finalize_sum(const double *partials, int n, double *out, cudaStream_t s);
+
+// Flat double-word complex vectors (float4 = one complex DW), n elements.
+cudaError_t launch_dw_copy(float4 *dst, const float4 *src, int64_t n, cudaStream_t s);
+cudaError_t launch_dw_zero(float4 *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_dw_norm2(const float4 *a, int64_t n, double *partials, cudaStream_t s);
+// r = b - y, partials of ||r||^2
+cudaError_t launch_dw_xmy_norm(float4 *r, const float4 *b, const float4 *y, int64_t n,
+                               double *partials, cudaStream_t s);
+// x += alpha p; r -= alpha Ap; partials ||r||^2 (alpha from S; skipped when S->done)
+cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const float4 *Ap, int64_t n,
+                                const SolverScalars *S, double *partials, cudaStream_t s);
+// p = r + beta p (skipped when S->done)
+cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
+                           cudaStream_t s);
+// y += x
+cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s);
+
+// CG scalar steps (single block): alpha = rr / sum(partials)
+cudaError_t launch_cg_alpha(const double *partials, int n, SolverScalars *S, cudaStream_t s);
+// rr_new = sum(partials); iters++; done when rr_new <= stop_rr; beta = rr_new/rr
+cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s);
+// S->rr = sum(partials) and reset the loop state (start or restart of CG)
+cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
+                            int max_iters, cudaStream_t s);
+
+}  // namespace jqcd

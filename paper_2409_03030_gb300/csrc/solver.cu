@@ -1,0 +1,320 @@
+// Solver drivers: conjugate gradient on the normal equations, even-odd
+// source preparation and reconstruction (paper: solve_DinvX! with eps_CG).
+//
+// Conjugate gradient (Hestenes-Stiefel) on A x = rhs, A Hermitian positive
+// definite (A = Mhat^dag Mhat on the even sites, or D^dag D):
+//   r = rhs - A x, p = r, rr = <r,r>
+//   loop: alpha = rr / <p,Ap>;  x += alpha p;  r -= alpha Ap;
+//         rr' = <r,r>;  stop if rr' <= tol^2 <rhs,rhs>;  p = r + (rr'/rr) p
+// All scalars live on the device: <p,Ap> = ||Mhat p||^2 comes fused out of
+// the second hop, <r,r> out of the vector update, and single-block kernels
+// turn the partial sums into alpha and beta.  The host only polls the
+// scalars every kCheckEvery iterations; kernels of finished solves return
+// at once.  After the loop the residual is recomputed from x; if it misses
+// the tolerance CG restarts from x.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "kernels.h"
+#include "solver.h"
+
+namespace jqcd {
+
+namespace {
+constexpr int kCheckEvery = 8;
+constexpr int kMaxRestarts = 8;
+}  // namespace
+
+GaugeEntry::~GaugeEntry() {
+  for (void *p : device_allocs) cudaFree(p);
+  if (S_host) cudaFreeHost(S_host);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+}
+
+cudaError_t GaugeEntry::alloc(void **p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes < 256 ? 256 : bytes);
+  if (e == cudaSuccess) device_allocs.push_back(*p);
+  return e;
+}
+
+cudaError_t GaugeEntry::ensure_canon() {
+  if (canon) return cudaSuccess;
+  return alloc_t(&canon, canon_bytes());
+}
+
+int GaugeEntry::n_partials() const {
+  return 2 * (int)hop_blocks(g.vh) + (int)blas_blocks(24 * g.vh) + 64;
+}
+
+cudaError_t GaugeEntry::ensure_reduce() {
+  cudaError_t e = cudaSuccess;
+  if (!partials) e = alloc_t(&partials, sizeof(double) * n_partials());
+  if (e == cudaSuccess && !S) e = alloc_t(&S, sizeof(SolverScalars));
+  if (e == cudaSuccess && !S_host) e = cudaMallocHost(&S_host, sizeof(SolverScalars));
+  if (e == cudaSuccess && !ev0) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess && !ev1) e = cudaEventCreate(&ev1);
+  return e;
+}
+
+cudaError_t GaugeEntry::ensure_tmp(int prec) {
+  cudaError_t e = cudaSuccess;
+  const size_t b = spinor_parity_bytes(prec, g.vh);
+  if (!tmp[prec]) e = alloc(&tmp[prec], b);
+  if (e == cudaSuccess && !tmp2[prec]) e = alloc(&tmp2[prec], b);
+  return e;
+}
+
+cudaError_t GaugeEntry::ensure_solver() {
+  cudaError_t e = ensure_canon();
+  if (e == cudaSuccess) e = ensure_reduce();
+  const size_t full = 2 * spinor_parity_bytes(PREC_DW, g.vh);
+  float4 **vs[] = {&vb, &vsol, &vr, &vp, &vAp, &vw, &vt, &vrhs};
+  for (float4 **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc_t(v, full);
+  return e;
+}
+
+const void *GaugeEntry::gauge_for(int prec) const {
+  switch (prec) {
+    case PREC_DW: return gauge_dw;
+    case PREC_F64: return gauge_f64;
+    default: return gauge_f32;
+  }
+}
+
+HopParams GaugeEntry::hop_params(int prec, int out_parity, const void *in, const void *x, void *out,
+                                 double a, double b, double *parts) const {
+  HopParams P;
+  memset(&P, 0, sizeof P);
+  P.out = out;
+  P.in = in;
+  P.x = x;
+  P.gauge = gauge_for(prec);
+  P.g = g;
+  P.out_parity = out_parity;
+  P.a = a;
+  P.b = b;
+  const float ah = (float)a, bh = (float)b;
+  P.a_split = make_float2(ah, (float)(a - (double)ah));
+  P.b_split = make_float2(bh, (float)(b - (double)bh));
+  P.partials = parts;
+  P.guard = nullptr;
+  return P;
+}
+
+cudaError_t apply_mdagm(const GaugeEntry &G, int prec, double kappa, const void *in, void *out,
+                        void *t_odd, void *w_even, double *partials, const int *guard,
+                        cudaStream_t s) {
+  const double k2 = -kappa * kappa;
+  HopParams P = G.hop_params(prec, 1, in, nullptr, t_odd, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  cudaError_t e = launch_hop(prec, P, false, false, false, s);           // t = H_oe in
+  if (e) return e;
+  P = G.hop_params(prec, 0, t_odd, in, w_even, 1.0, k2, partials);
+  P.guard = guard;
+  e = launch_hop(prec, P, false, true, partials != nullptr, s);          // w = in - k^2 H_eo t
+  if (e) return e;
+  P = G.hop_params(prec, 1, w_even, nullptr, t_odd, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  e = launch_hop(prec, P, true, false, false, s);                        // t = H^dag_oe w
+  if (e) return e;
+  P = G.hop_params(prec, 0, t_odd, w_even, out, 1.0, k2, nullptr);
+  P.guard = guard;
+  return launch_hop(prec, P, true, true, false, s);                      // out = w - k^2 H^dag_eo t
+}
+
+namespace {
+
+// Whole-lattice D (or D^dag) on double-word vectors: out = in - kappa H in,
+// optional per-block partials of ||out||^2 (2 * hop_blocks entries).
+cudaError_t apply_dirac_dw(const GaugeEntry &G, double kappa, bool dag, float4 *in, float4 *out,
+                           double *partials, const int *guard, cudaStream_t s) {
+  const int nb = (int)hop_blocks(G.g.vh);
+  HopParams Pe = G.hop_params(PREC_DW, 0, G.vec_odd(in), G.vec_even(in), G.vec_even(out), 1.0,
+                              -kappa, partials);
+  Pe.guard = guard;
+  cudaError_t e = launch_hop(PREC_DW, Pe, dag, true, partials != nullptr, s);
+  if (e) return e;
+  HopParams Po = G.hop_params(PREC_DW, 1, G.vec_even(in), G.vec_odd(in), G.vec_odd(out), 1.0,
+                              -kappa, partials ? partials + nb : nullptr);
+  Po.guard = guard;
+  return launch_hop(PREC_DW, Po, dag, true, partials != nullptr, s);
+}
+
+struct DwSystem {
+  GaugeEntry &G;
+  double kappa;
+  bool eo;
+  cudaStream_t s;
+  int64_t n;      // complex elements of the system's vectors
+  int n_hop_partials;
+  long long hops = 0;
+  double hop_bytes = 0;
+
+  void count(int plain, int axpy) {
+    hops += plain + axpy;
+    hop_bytes += (double)G.g.vh * (1536.0 * (plain + axpy) + 192.0 * axpy);
+  }
+
+  // out = A in, partials <- ||M in||^2 (M = Mhat or D).  Guarded applies
+  // inside the CG loop are counted from the iteration count instead.
+  cudaError_t apply(float4 *in, float4 *out, double *partials, const int *guard) {
+    if (!guard) count(eo ? 2 : 0, eo ? 2 : 4);
+    if (eo) {
+      return apply_mdagm(G, PREC_DW, kappa, in, out, G.vec_odd(G.vt), G.vec_even(G.vw), partials,
+                         guard, s);
+    }
+    cudaError_t e = apply_dirac_dw(G, kappa, false, in, G.vw, partials, guard, s);
+    if (e) return e;
+    return apply_dirac_dw(G, kappa, true, G.vw, out, nullptr, guard, s);
+  }
+};
+
+}  // namespace
+
+static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                            jqcd_solve_info *info, std::string *msg) {
+  const bool eo = P.eo != 0;
+  DwSystem A{G, P.kappa, eo, s, (eo ? 12 : 24) * G.g.vh, (eo ? 1 : 2) * (int)hop_blocks(G.g.vh)};
+  const int nblas = (int)blas_blocks(A.n);
+  const double tol2 = P.tol * P.tol;
+  SolverScalars *S = G.S;
+#define CKS(call)                                              \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      *msg = cudaGetErrorString(e_);                           \
+      return e_ == cudaErrorMemoryAllocation ? JQCD_ENOMEM : JQCD_ECUDA; \
+    }                                                          \
+  } while (0)
+
+  CKS(cudaEventRecord(G.ev0, s));
+  CKS(cudaMemsetAsync(S, 0, sizeof(SolverScalars), s));
+  // ||b||^2 of D x = b
+  CKS(launch_dw_norm2(G.vb, 24 * G.g.vh, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * G.g.vh), &S->b2, s));
+  // right-hand side of the CG system
+  if (eo) {
+    // bhat_e = b_e + kappa H_eo b_o  (into vw even)
+    HopParams Pb = G.hop_params(PREC_DW, 0, G.vec_odd(G.vb), G.vec_even(G.vb), G.vec_even(G.vw),
+                                1.0, P.kappa, nullptr);
+    CKS(launch_hop(PREC_DW, Pb, false, true, false, s));
+    // rhs = Mhat^dag bhat: t = H^dag_oe bhat; rhs = bhat - kappa^2 H^dag_eo t
+    HopParams P1 = G.hop_params(PREC_DW, 1, G.vec_even(G.vw), nullptr, G.vec_odd(G.vt), 0.0, 1.0,
+                                nullptr);
+    CKS(launch_hop(PREC_DW, P1, true, false, false, s));
+    HopParams P2 = G.hop_params(PREC_DW, 0, G.vec_odd(G.vt), G.vec_even(G.vw), G.vec_even(G.vrhs),
+                                1.0, -P.kappa * P.kappa, nullptr);
+    CKS(launch_hop(PREC_DW, P2, true, true, false, s));
+    A.count(2, 1);
+  } else {
+    CKS(apply_dirac_dw(G, P.kappa, true, G.vb, G.vrhs, nullptr, nullptr, s));  // rhs = D^dag b
+    A.count(0, 2);
+  }
+  CKS(launch_dw_norm2(G.vrhs, A.n, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, nblas, &S->rhs2, s));
+  // start vector and residual
+  if (P.use_x0) {
+    CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
+    CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
+  } else {
+    CKS(launch_dw_zero(G.vsol, 24 * G.g.vh, s));
+    CKS(launch_dw_copy(G.vr, G.vrhs, A.n, s));
+    CKS(launch_dw_norm2(G.vr, A.n, G.partials, s));
+  }
+  CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, s));
+  CKS(launch_dw_copy(G.vp, G.vr, A.n, s));
+
+  int restarts = 0;
+  jqcd_status st = JQCD_OK;
+  for (;;) {
+    // main loop: poll the device scalars every kCheckEvery iterations
+    for (;;) {
+      for (int k = 0; k < kCheckEvery; ++k) {
+        CKS(A.apply(G.vp, G.vAp, G.partials, &S->done));
+        CKS(launch_cg_alpha(G.partials, A.n_hop_partials, S, s));
+        CKS(launch_dw_cg_update(G.vsol, G.vr, G.vp, G.vAp, A.n, S, G.partials, s));
+        CKS(launch_cg_beta(G.partials, nblas, S, s));
+        CKS(launch_dw_xpay(G.vp, G.vr, A.n, S, s));
+      }
+      CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+      CKS(cudaStreamSynchronize(s));
+      if (P.verbose >= 3)
+        fprintf(stderr, "jqcd cg: iter %d  |r|/|rhs| = %.3e\n", G.S_host->iters,
+                G.S_host->rhs2 > 0 ? std::sqrt(G.S_host->rr / G.S_host->rhs2) : 0.0);
+      if (G.S_host->done || G.S_host->iters >= P.maxiter) break;
+    }
+    if (G.S_host->done == 2) {
+      *msg = "CG breakdown (<p,Ap> <= 0 or not finite)";
+      st = JQCD_EBREAKDOWN;
+      break;
+    }
+    // true residual of the CG system
+    CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
+    CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
+    CKS(launch_finalize_sum(G.partials, nblas, &S->true_rr, s));
+    CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
+    const double rhs2 = G.S_host->rhs2;
+    const bool ok = G.S_host->true_rr <= tol2 * rhs2;
+    if (ok) break;
+    if (G.S_host->iters >= P.maxiter || restarts >= kMaxRestarts) {
+      st = JQCD_ENOCONV;
+      *msg = "maximum iterations reached";
+      break;
+    }
+    ++restarts;  // restart from x with the recomputed residual
+    CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, s));
+    CKS(launch_dw_copy(G.vp, G.vr, A.n, s));
+  }
+  // even-odd reconstruction x_o = b_o + kappa H_oe x_e
+  if (eo) {
+    HopParams Pr = G.hop_params(PREC_DW, 1, G.vec_even(G.vsol), G.vec_odd(G.vb), G.vec_odd(G.vsol),
+                                1.0, P.kappa, nullptr);
+    CKS(launch_hop(PREC_DW, Pr, false, true, false, s));
+    A.count(0, 1);
+  }
+  CKS(cudaEventRecord(G.ev1, s));
+  // ||b - D x||^2 (not part of the timed solve)
+  CKS(apply_dirac_dw(G, P.kappa, false, G.vsol, G.vw, nullptr, nullptr, s));
+  CKS(launch_dw_xmy_norm(G.vAp, G.vb, G.vw, 24 * G.g.vh, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * G.g.vh), &S->full_rr, s));
+  CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+  CKS(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  CKS(cudaEventElapsedTime(&ms, G.ev0, G.ev1));
+  const SolverScalars &H = *G.S_host;
+  info->iters = H.iters;
+  info->restarts = restarts;
+  info->reliable_updates = 0;
+  info->true_rel_resid = H.rhs2 > 0 ? std::sqrt(H.true_rr / H.rhs2) : 0.0;
+  info->full_rel_resid = H.b2 > 0 ? std::sqrt(H.full_rr / H.b2) : 0.0;
+  info->gpu_seconds = ms * 1e-3;
+  // loop hops: four per completed iteration
+  for (int i = 0; i < H.iters; ++i) A.count(eo ? 2 : 0, eo ? 2 : 4);
+  info->hop_count = (double)A.hops;
+  info->hop_bytes = A.hop_bytes;
+  return st;
+#undef CKS
+}
+
+jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                           jqcd_solve_info *info, std::string *msg) {
+  if (!(P.tol > 0.0) || P.maxiter < 1 || !(P.kappa >= 0.0)) {
+    *msg = "bad solve parameters (tol > 0, maxiter >= 1, kappa >= 0)";
+    return JQCD_EINVAL;
+  }
+  switch (P.mode) {
+    case JQCD_CG_DW: return solve_dw(G, P, s, info, msg);
+    default:
+      *msg = "solver mode not available";
+      return JQCD_EINVAL;
+  }
+}
+
+}  // namespace jqcd

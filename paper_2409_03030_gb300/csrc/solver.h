@@ -1,0 +1,71 @@
+// Host-side state of one resident gauge field and the solver drivers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "jqcd.h"
+#include "kernels.h"
+
+namespace jqcd {
+
+struct GaugeEntry {
+  Geom g{};
+  void *gauge_dw = nullptr, *gauge_f64 = nullptr, *gauge_f32 = nullptr;
+
+  // workspace, allocated on first use
+  double *canon = nullptr;        // 12*V complex doubles: host <-> device staging
+  double *partials = nullptr;     // reduction partial sums
+  SolverScalars *S = nullptr;     // device scalars of the running solve
+  SolverScalars *S_host = nullptr;  // pinned mirror
+  void *tmp[4] = {nullptr, nullptr, nullptr, nullptr};   // odd-parity temporaries per precision
+  void *tmp2[4] = {nullptr, nullptr, nullptr, nullptr};  // even-parity temporaries per precision
+  // whole-lattice double-word solver vectors (even half first, then odd)
+  float4 *vb = nullptr, *vsol = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr,
+         *vw = nullptr, *vt = nullptr, *vrhs = nullptr;
+  // mixed-precision inner vectors (even parity): x, r in FP32; p, Ap, w in the
+  // hop precision; t odd in the hop precision
+  void *mx = nullptr, *mr = nullptr, *mp[2] = {nullptr, nullptr}, *mAp[2] = {nullptr, nullptr},
+       *mw[2] = {nullptr, nullptr}, *mt[2] = {nullptr, nullptr};
+  // native FP64 solver vectors (whole lattice)
+  double2 *fb = nullptr, *fsol = nullptr, *fr = nullptr, *fp = nullptr, *fAp = nullptr,
+          *fw = nullptr, *ft = nullptr, *frhs = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<void *> device_allocs;
+
+  ~GaugeEntry();
+  cudaError_t alloc(void **p, size_t bytes);
+  template <typename T> cudaError_t alloc_t(T **p, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = alloc(&v, bytes);
+    *p = reinterpret_cast<T *>(v);
+    return e;
+  }
+  size_t canon_bytes() const { return sizeof(double) * 2 * 12 * (size_t)(2 * g.vh); }
+  cudaError_t ensure_canon();
+  cudaError_t ensure_reduce();
+  cudaError_t ensure_tmp(int prec);
+  cudaError_t ensure_solver();
+  cudaError_t ensure_mixed(int hop_prec);
+  cudaError_t ensure_f64();
+  int n_partials() const;
+  float4 *vec_even(float4 *v) const { return v; }
+  float4 *vec_odd(float4 *v) const { return v + 12 * g.vh; }
+  const void *gauge_for(int prec) const;
+  HopParams hop_params(int prec, int out_parity, const void *in, const void *x, void *out, double a,
+                       double b, double *partials) const;
+};
+
+// out = Mhat^dag Mhat in (even sites) in precision `prec`; t_odd and w_even are
+// temporaries; partials (if not null) receive ||Mhat in||^2 per hop block.
+cudaError_t apply_mdagm(const GaugeEntry &G, int prec, double kappa, const void *in, void *out,
+                        void *t_odd, void *w_even, double *partials, const int *guard,
+                        cudaStream_t s);
+
+// Run the solve of D x = b for the double-word b in G.vb; the solution is
+// left in G.vsol (whole lattice, double-word).
+jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                           jqcd_solve_info *info, std::string *msg);
+
+}  // namespace jqcd

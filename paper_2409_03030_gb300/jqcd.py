@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libjqcd.so (the C ABI in include/jqcd.h).
+
+The functions ``jqcd_*`` are the C entry points with their C names.  The
+classes below only marshal arguments: numpy arrays for host data, torch
+CUDA tensors (raw byte buffers) for device data, torch streams for streams.
+Every step of the computation runs in the library's CUDA kernels; there is
+no fallback, and importing this module fails loudly when the library has not
+been built (``python -m paper_2409_03030_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "lib", "libjqcd.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBUSY, ETIMEOUT, ENOTFOUND, EBREAKDOWN = 0, -1, -2, -3, -4, -5, -6, -7, -8
+PENDING = 1
+PREC_DW, PREC_F32, PREC_F16N, PREC_F64 = 0, 1, 2, 3
+CG_DW, CG_F64, CG_MIXED_F32, CG_MIXED_F16 = 0, 1, 2, 3
+PRECS = {"dw": PREC_DW, "f32": PREC_F32, "f16n": PREC_F16N, "f64": PREC_F64}
+MODES = {"dw": CG_DW, "f64": CG_F64, "mixed_f32": CG_MIXED_F32, "mixed_f16": CG_MIXED_F16}
+
+
+class JqcdError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"jqcd status {status}: {message}")
+        self.status = status
+
+
+class jqcd_lattice(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 4), ("t_antiperiodic", ctypes.c_int32)]
+
+
+class jqcd_solve_params(ctypes.Structure):
+    _fields_ = [("kappa", ctypes.c_double), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int32),
+                ("eo", ctypes.c_int32), ("mode", ctypes.c_int32), ("verbose", ctypes.c_int32),
+                ("delta", ctypes.c_double), ("use_x0", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class jqcd_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32),
+                ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("true_rel_resid", ctypes.c_double), ("full_rel_resid", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("gpu_seconds", ctypes.c_double),
+                ("hop_bytes", ctypes.c_double), ("hop_count", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_st = ctypes.c_int32
+_u64 = ctypes.c_uint64
+_SIGNATURES = {
+    "jqcd_abi_version": (ctypes.c_int32, []),
+    "jqcd_init": (_st, [ctypes.c_int, ctypes.POINTER(_vp)]),
+    "jqcd_finalize": (_st, [_vp]),
+    "jqcd_last_error": (ctypes.c_char_p, [_vp]),
+    "jqcd_gauge_upload": (_st, [_vp, ctypes.POINTER(jqcd_lattice), _dp, ctypes.c_uint32,
+                                ctypes.POINTER(_u64)]),
+    "jqcd_gauge_free": (_st, [_vp, _u64]),
+    "jqcd_spinor_bytes": (_st, [ctypes.POINTER(jqcd_lattice), ctypes.c_int32,
+                                ctypes.POINTER(ctypes.c_size_t)]),
+    "jqcd_spinor_pack": (_st, [_vp, _u64, _dp, ctypes.c_int32, _vp, _vp, _vp]),
+    "jqcd_spinor_unpack": (_st, [_vp, _u64, ctypes.c_int32, _vp, _vp, _dp, _vp]),
+    "jqcd_dslash_eo": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
+                             _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "jqcd_mdagm": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp, _vp]),
+    "jqcd_dirac_apply": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _vp,
+                               _vp, _vp, _vp, _vp]),
+    "jqcd_cg_solve": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _dp, _dp,
+                            ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_cg_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _vp, _vp, _vp, _vp,
+                                ctypes.POINTER(jqcd_solve_info), _vp]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libjqcd.so not built ({LIB_PATH}); run __graft_entry__.build() or "
+                          "python -m paper_2409_03030_gb300.build")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+        globals()[name] = fn
+    return lib
+
+
+_lib = _load()
+
+
+def exported_symbols():
+    return sorted(_SIGNATURES)
+
+
+def _host_ptr(a: np.ndarray):
+    if a.dtype != np.complex128 or not a.flags.c_contiguous:
+        raise TypeError("host spinors/links must be C-contiguous complex128 arrays")
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(int(t.data_ptr()) if hasattr(t, "data_ptr") else int(t))
+
+
+def lattice(dims, t_antiperiodic=True) -> jqcd_lattice:
+    return jqcd_lattice((ctypes.c_int32 * 4)(*[int(d) for d in dims]), int(bool(t_antiperiodic)))
+
+
+def spinor_bytes(dims, prec, t_antiperiodic=True) -> int:
+    n = ctypes.c_size_t(0)
+    lat = lattice(dims, t_antiperiodic)
+    st = jqcd_spinor_bytes(ctypes.byref(lat), int(prec), ctypes.byref(n))
+    if st != OK:
+        raise JqcdError(st, "jqcd_spinor_bytes: bad lattice or precision")
+    return n.value
+
+
+class Context:
+    """One jqcd context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        h = ctypes.c_void_p()
+        st = jqcd_init(int(device), ctypes.byref(h))
+        if st != OK:
+            raise JqcdError(st, f"jqcd_init({device}) failed")
+        self.h = h
+        self.device = int(device)
+
+    def close(self):
+        if self.h:
+            jqcd_finalize(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def check(self, st, what=""):
+        if st not in (OK, PENDING):
+            raise JqcdError(st, f"{what}: {jqcd_last_error(self.h).decode()}")
+        return st
+
+    # ---- gauge fields -----------------------------------------------------
+    def gauge_upload(self, dims, links: np.ndarray, t_antiperiodic=True) -> "Gauge":
+        lat = lattice(dims, t_antiperiodic)
+        gid = ctypes.c_uint64(0)
+        links = np.ascontiguousarray(links, dtype=np.complex128)
+        self.check(jqcd_gauge_upload(self.h, ctypes.byref(lat), _host_ptr(links), 0,
+                                     ctypes.byref(gid)), "jqcd_gauge_upload")
+        return Gauge(self, gid.value, tuple(int(d) for d in dims), bool(t_antiperiodic))
+
+
+class Gauge:
+    """A gauge field resident on the device, with the operators built on it."""
+
+    def __init__(self, ctx: Context, gid: int, dims, t_antiperiodic: bool):
+        self.ctx, self.id, self.dims, self.t_antiperiodic = ctx, gid, dims, t_antiperiodic
+        self.volume = int(np.prod(dims))
+
+    def free(self):
+        if self.id:
+            self.ctx.check(jqcd_gauge_free(self.ctx.h, self.id), "jqcd_gauge_free")
+            self.id = 0
+
+    def spinor_bytes(self, prec) -> int:
+        return spinor_bytes(self.dims, prec, self.t_antiperiodic)
+
+    def empty(self, prec):
+        """One parity of a device spinor field (torch uint8 buffer)."""
+        import torch
+        return torch.empty(self.spinor_bytes(prec), dtype=torch.uint8,
+                           device=f"cuda:{self.ctx.device}")
+
+    def pack(self, host: np.ndarray, prec, stream=None):
+        host = np.ascontiguousarray(host, dtype=np.complex128)
+        ev, od = self.empty(prec), self.empty(prec)
+        self.ctx.check(jqcd_spinor_pack(self.ctx.h, self.id, _host_ptr(host), int(prec),
+                                        _dev_ptr(ev), _dev_ptr(od), _stream_ptr(stream)),
+                       "jqcd_spinor_pack")
+        return ev, od
+
+    def unpack(self, even, odd, prec, stream=None) -> np.ndarray:
+        nx, ny, nz, nt = self.dims
+        out = np.empty((4, nt, nz, ny, nx, 3), dtype=np.complex128)
+        self.ctx.check(jqcd_spinor_unpack(self.ctx.h, self.id, int(prec), _dev_ptr(even),
+                                          _dev_ptr(odd), _host_ptr(out), _stream_ptr(stream)),
+                       "jqcd_spinor_unpack")
+        return out
+
+    def dslash_eo(self, prec, out_parity, dagger, inp, x, out, a=0.0, b=1.0, norm2=None,
+                  stream=None):
+        self.ctx.check(jqcd_dslash_eo(self.ctx.h, self.id, int(prec), int(out_parity), int(dagger),
+                                      _dev_ptr(inp), _dev_ptr(x), _dev_ptr(out), float(a),
+                                      float(b), _dev_ptr(norm2), _stream_ptr(stream)),
+                       "jqcd_dslash_eo")
+
+    def mdagm(self, prec, kappa, inp, out, norm2=None, stream=None):
+        self.ctx.check(jqcd_mdagm(self.ctx.h, self.id, int(prec), float(kappa), _dev_ptr(inp),
+                                  _dev_ptr(out), _dev_ptr(norm2), _stream_ptr(stream)),
+                       "jqcd_mdagm")
+
+    def dirac_apply(self, prec, kappa, dagger, in_even, in_odd, out_even, out_odd, stream=None):
+        self.ctx.check(jqcd_dirac_apply(self.ctx.h, self.id, int(prec), float(kappa), int(dagger),
+                                        _dev_ptr(in_even), _dev_ptr(in_odd), _dev_ptr(out_even),
+                                        _dev_ptr(out_odd), _stream_ptr(stream)),
+                       "jqcd_dirac_apply")
+
+    @staticmethod
+    def params(kappa, tol=1e-10, maxiter=20000, eo=True, mode=CG_DW, verbose=0, delta=0.0,
+               use_x0=False) -> jqcd_solve_params:
+        return jqcd_solve_params(float(kappa), float(tol), int(maxiter), int(bool(eo)), int(mode),
+                                 int(verbose), float(delta), int(bool(use_x0)), 0)
+
+    def cg_solve(self, b: np.ndarray, kappa, tol=1e-10, maxiter=20000, eo=True, mode=CG_DW,
+                 verbose=0, delta=0.0, x0=None, check=True):
+        """Solve D x = b from host arrays; returns (x, info dict, status)."""
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
+        p = self.params(kappa, tol, maxiter, eo, mode, verbose, delta, x0 is not None)
+        info = jqcd_solve_info()
+        st = jqcd_cg_solve(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(b), _host_ptr(x),
+                           ctypes.byref(info))
+        if check:
+            self.ctx.check(st, "jqcd_cg_solve")
+        return x, info.as_dict(), st
+
+    def cg_solve_dev(self, b_even, b_odd, x_even, x_odd, kappa, tol=1e-10, maxiter=20000, eo=True,
+                     mode=CG_DW, verbose=0, delta=0.0, use_x0=False, stream=None, check=True):
+        p = self.params(kappa, tol, maxiter, eo, mode, verbose, delta, use_x0)
+        info = jqcd_solve_info()
+        st = jqcd_cg_solve_dev(self.ctx.h, self.id, ctypes.byref(p), _dev_ptr(b_even),
+                               _dev_ptr(b_odd), _dev_ptr(x_even), _dev_ptr(x_odd),
+                               ctypes.byref(info), _stream_ptr(stream))
+        if check:
+            self.ctx.check(st, "jqcd_cg_solve_dev")
+        return info.as_dict(), st

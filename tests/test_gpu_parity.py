@@ -1,0 +1,227 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative 2-norm over the whole output field):
+  double-word and native FP64 applies: 1e-12;  FP32: 1e-5;
+  FP16 + per-site norm: 2e-3 (reported precision of the inner solver only).
+Solves: the oracle recomputes the CG system's residual from the GPU solution
+and it must be <= tol * (1 + 1e-6).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_03030_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 3: 1e-12, 1: 1e-5, 2: 2e-3}  # by precision code
+
+
+@pytest.fixture(scope="module")
+def jq():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_03030_gb300 import jqcd
+    ctx = jqcd.Context(0)
+    yield jqcd, ctx
+    ctx.close()
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def odd_mask(dims):
+    return oracle.parity_mask(dims)[None, :, :, :, :, None]
+
+
+def only_parity(dims, psi, parity):
+    m = odd_mask(dims)
+    return np.where(m if parity == 1 else ~m, psi, 0)
+
+
+LATTICES = [(2, 2, 2, 2), (4, 4, 4, 4), (6, 4, 2, 8), (6, 6, 6, 10), (8, 8, 8, 16)]
+PRECS = [0, 3, 1, 2]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (6, 4, 2, 8)])
+def test_pack_roundtrip(jq, dims, prec):
+    jqcd, ctx = jq
+    g = ctx.gauge_upload(dims, synth.gauge(dims, "unit"))
+    psi = synth.gaussian_spinor(dims, seed=3)
+    ev, od = g.pack(psi, prec)
+    back = g.unpack(ev, od, prec)
+    bound = {0: 1e-14, 3: 0.0, 1: 1e-7, 2: 1e-3}[prec]
+    assert rel(back, psi) <= bound
+    g.free()
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_hop_vs_oracle(jq, dims, prec, dagger):
+    jqcd, ctx = jq
+    import torch
+    U = synth.gauge(dims, "expi", eps=0.3, seed=11)
+    g = ctx.gauge_upload(dims, U, t_antiperiodic=True)
+    psi = synth.gaussian_spinor(dims, seed=12)
+    xs = synth.gaussian_spinor(dims, seed=13)
+    pe, po = g.pack(psi, prec)
+    xe, xo = g.pack(xs, prec)
+    norm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for p in (0, 1):
+        want_h = oracle.hop(dims, U, psi, dagger=bool(dagger), out_parity=p)
+        inp = po if p == 0 else pe
+        xin = xe if p == 0 else xo
+        out = g.empty(prec)
+        # plain hop with fused norm
+        g.dslash_eo(prec, p, dagger, inp, None, out, 0.0, 1.0, norm2=norm)
+        ev = out if p == 0 else g.empty(prec).zero_()
+        od = out if p == 1 else g.empty(prec).zero_()
+        got = only_parity(dims, g.unpack(ev, od, prec), p)
+        assert rel(got, want_h) <= TOL[prec], (p, rel(got, want_h))
+        n_want = np.linalg.norm(got) ** 2
+        assert abs(norm.item() - n_want) <= max(TOL[prec], 1e-12) * 10 * n_want
+        # fused axpy: out = a x + b H in
+        a, b = 0.7, -0.12
+        g.dslash_eo(prec, p, dagger, inp, xin, out, a, b)
+        got = only_parity(dims, g.unpack(ev, od, prec), p)
+        want = a * only_parity(dims, xs, p) + b * want_h
+        assert rel(got, want) <= TOL[prec], (p, rel(got, want))
+    g.free()
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 10)])
+@pytest.mark.parametrize("prec", PRECS)
+def test_mdagm_vs_oracle(jq, dims, prec):
+    jqcd, ctx = jq
+    import torch
+    U = synth.gauge(dims, "expi", eps=0.3, seed=21)
+    g = ctx.gauge_upload(dims, U)
+    v = only_parity(dims, synth.gaussian_spinor(dims, seed=22), 0)
+    ve, vo = g.pack(v, prec)
+    out = g.empty(prec)
+    norm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    k = 0.12
+    g.mdagm(prec, k, ve, out, norm2=norm)
+    got = only_parity(dims, g.unpack(out, vo, prec), 0)
+    want = oracle.normal_apply(dims, U, v, k, eo=True)
+    assert rel(got, want) <= TOL[prec]
+    mv = oracle.schur(dims, U, v, k)
+    assert abs(norm.item() - np.linalg.norm(mv) ** 2) <= max(TOL[prec], 1e-12) * 10 * np.linalg.norm(mv) ** 2
+    g.free()
+
+
+@pytest.mark.parametrize("prec", [0, 3, 1])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_dirac_apply_vs_oracle(jq, prec, dagger):
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, "haar", seed=1)
+    g = ctx.gauge_upload(dims, U)
+    psi = synth.gaussian_spinor(dims, seed=1)
+    ie, io = g.pack(psi, prec)
+    oe, oo = g.empty(prec), g.empty(prec)
+    g.dirac_apply(prec, 0.10, dagger, ie, io, oe, oo)
+    got = g.unpack(oe, oo, prec)
+    want = oracle.dirac(dims, U, psi, 0.10, dagger=bool(dagger))
+    assert rel(got, want) <= TOL[prec]
+    g.free()
+
+
+def system_residual(dims, U, b, x, kappa, eo):
+    """||rhs - A x|| / ||rhs|| of the CG system, recomputed by the oracle."""
+    if eo:
+        bhat = only_parity(dims, b, 0) + kappa * oracle.hop(dims, U, only_parity(dims, b, 1),
+                                                            out_parity=0)
+        rhs = oracle.schur(dims, U, bhat, kappa, dagger=True)
+        r = rhs - oracle.normal_apply(dims, U, only_parity(dims, x, 0), kappa, eo=True)
+    else:
+        rhs = oracle.dirac(dims, U, b, kappa, dagger=True)
+        r = rhs - oracle.normal_apply(dims, U, x, kappa, eo=False)
+    return np.linalg.norm(r) / np.linalg.norm(rhs)
+
+
+@pytest.mark.parametrize("eo", [False, True])
+def test_cg_config0_4x4(jq, eo):
+    """4^4, Haar links, kappa 0.10, antiperiodic time, Gaussian source, tol 1e-12."""
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, "haar", seed=1)
+    b = synth.gaussian_spinor(dims, seed=1)
+    g = ctx.gauge_upload(dims, U)
+    tol = 1e-12
+    x, info, st = g.cg_solve(b, 0.10, tol=tol, eo=eo, mode=jqcd.CG_DW)
+    assert st == 0 and info["iters"] > 0
+    res = system_residual(dims, U, b, x, 0.10, eo)
+    assert res <= tol * (1 + 1e-6), res
+    assert abs(info["true_rel_resid"] - res) <= 1e-2 * tol + 1e-14
+    full = rel(oracle.dirac(dims, U, x, 0.10), b)
+    assert abs(info["full_rel_resid"] - full) <= 1e-13
+    xo, *_ = oracle.solve(dims, U, b, 0.10, eo=eo, tol=1e-13)
+    assert rel(x, xo) < 1e-10
+    g.free()
+
+
+def test_cg_config1_16x4(jq):
+    """16^4, exp(i 0.3 H) links, kappa 0.12, even-odd, Gaussian source, tol 1e-10."""
+    jqcd, ctx = jq
+    dims = (16, 16, 16, 16)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=2)
+    b = synth.gaussian_spinor(dims, seed=3)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.CG_DW)
+    assert st == 0
+    res = system_residual(dims, U, b, x, 0.12, True)
+    assert res <= 1e-10 * (1 + 1e-6), res
+    g.free()
+
+
+def test_cg_zero_source_and_limits(jq):
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, "haar", seed=5)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(np.zeros(synth.spinor_shape(dims), complex), 0.1, tol=1e-10)
+    assert st == 0 and info["iters"] == 0 and not np.any(x)
+    b = synth.gaussian_spinor(dims, seed=6)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-14, maxiter=3, check=False)
+    assert st == jqcd.ENOCONV and info["iters"] >= 3
+    g.free()
+
+
+def test_errors(jq):
+    jqcd, ctx = jq
+    with pytest.raises(jqcd.JqcdError) as e:
+        ctx.gauge_upload((3, 4, 4, 4), np.zeros((4, 4, 4, 4, 3, 3, 3), complex))
+    assert e.value.status == jqcd.EINVAL
+    g = ctx.gauge_upload((2, 2, 2, 2), synth.gauge((2, 2, 2, 2), "unit"))
+    g.free()
+    with pytest.raises(jqcd.JqcdError) as e:
+        g2 = jqcd.Gauge(ctx, 999999, (2, 2, 2, 2), True)
+        g2.cg_solve(np.zeros(synth.spinor_shape((2, 2, 2, 2)), complex), 0.1)
+    assert e.value.status == jqcd.ENOTFOUND
+
+
+def test_hop_full_size_sampled(jq):
+    """24^3x48 (the bench lattice): double-word hop at sampled output sites
+    against the oracle's per-site hop."""
+    jqcd, ctx = jq
+    dims = (24, 24, 24, 48)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=7)
+    psi = synth.gaussian_spinor(dims, seed=8)
+    g = ctx.gauge_upload(dims, U)
+    pe, po = g.pack(psi, 0)
+    out_e, out_o = g.empty(0), g.empty(0)
+    g.dslash_eo(0, 0, 0, po, None, out_e)
+    g.dslash_eo(0, 1, 0, pe, None, out_o)
+    got = g.unpack(out_e, out_o, 0).reshape(4, -1, 3)
+    rng = np.random.default_rng(9)
+    V = int(np.prod(dims))
+    sites = np.unique(np.concatenate([rng.integers(0, V, 2000), [0, 1, V - 1, V - 2, V // 2]]))
+    want = oracle.hop_sites(dims, U, psi, sites)
+    got_s = np.transpose(got[:, sites, :], (1, 0, 2))
+    assert rel(got_s, want) <= 1e-12
+    g.free()
