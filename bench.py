@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the even-odd Wilson-Dirac CG hot path on GB300.
+
+One step = one complete FP64-class (double-word) even-odd CG solve of
+D x = b to a true relative residual of 1e-10 on a 24^3x48 lattice
+(links exp(i*0.3*H), kappa = 0.12, antiperiodic time, Gaussian source):
+source preparation, CG on Mhat^dag Mhat, reconstruction.  Gauge field and
+source are resident in HBM when the timed region starts.
+
+value = Dslash GB/s of the whole job: algorithmic bytes of every hop launch
+in the timed solves (1536 B per output site, +192 B when the hop also reads
+an axpy operand) divided by the wall time of the solves, summed over ranks.
+e2e   = the same quantity through jqcd_cg_solve with host buffers in pinned
+memory (copy of b in, copy of x out, inside the timed region).
+roofline = the double-word hop kernel timed alone on the same lattice.
+cpu_baseline / --impl reference = the FP64 CPU oracle on host cores.
+
+Multi-GPU (torchrun): each rank solves its own replica (independent problems,
+weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (24, 24, 24, 48)
+KAPPA = 0.12
+EPS = 0.3
+TOL = 1e-10
+METRIC = "Dslash GB/s vs HBM peak; CG s to 1e-10 mixed vs FP64; serve p50/p99"
+HOP_BYTES = {"dw": 1536, "f64": 1536, "f32": 576, "f16n": 488}  # per output site
+AXPY_BYTES = {"dw": 192, "f64": 192, "f32": 96, "f16n": 52}
+HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "fields.cuh", "dw.cuh", "lattice.cuh", "reduce.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="jqcd", choices=["jqcd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def vol(dims):
+    v = 1
+    for d in dims:
+        v *= d
+    return v
+
+
+def sample_description(iters):
+    return (f"oracle textbook CG on {DIMS[0]}^3x{DIMS[3]}, {iters} iteration(s) "
+            f"({iters + 2} applications of Mhat^dag Mhat incl. start and true residual)")
+
+
+def time_oracle_cg(U, b, iters):
+    """Oracle CG run for `iters` iterations; returns (GB/s of hop bytes, seconds, threads)."""
+    import numpy as np
+    import oracle
+    rhs = oracle.zero_parity(DIMS, b, 1)
+    t0 = time.perf_counter()
+    oracle.cg(DIMS, U, rhs, KAPPA, eo=True, tol=1e-30, maxiter=iters)
+    dt = time.perf_counter() - t0
+    vh = vol(DIMS) // 2
+    hop_bytes = (iters + 2) * vh * (4 * 1536 + 2 * 192)
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    del np
+    return hop_bytes / dt / 1e9, dt, threads
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in HOP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2409_03030_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the double-word hop from the committed ncu
+    summary, or None when the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "hop_dw_24x24x24x48.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_rank):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [v for v in vis.split(",") if v.strip()]
+        self.idx = ids[local_rank] if local_rank < len(ids) else str(local_rank)
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.idx, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2409_03030_gb300 import synth
+    U = synth.gauge(DIMS, "expi", eps=EPS, seed=1)
+    b = synth.gaussian_spinor(DIMS, seed=2)
+    iters = 1
+    for _ in range(args.warmup):
+        time_oracle_cg(U, b, iters)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, threads = time_oracle_cg(U, b, iters)
+        vals.append(v)
+        times.append(dt)
+    total = sum(times)
+    value = sum(v * t for v, t in zip(vals, times)) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": threads,
+                         "kind": "oracle", "sample": sample_description(iters)},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    del oracle
+
+
+def workload_config():
+    return {"workload": "even-odd Wilson-Dirac CG to 1e-10 true residual, 24^3x48, "
+                        "FP64-class double-word arithmetic",
+            "lattice": list(DIMS), "kappa": KAPPA, "links": f"exp(i*{EPS}*H), seeded",
+            "source": "Gaussian, seeded", "tol": TOL, "boundary": "periodic xyz, antiperiodic t",
+            "l2": "inputs larger than L2 (double-word gauge field 382 MB)",
+            "parallelism": "replicas"}
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    from paper_2409_03030_gb300 import jqcd, synth
+
+    vh = vol(DIMS) // 2
+    U = synth.gauge(DIMS, "expi", eps=EPS, seed=1)
+    b = synth.gaussian_spinor(DIMS, seed=2 + rank)
+    ctx = jqcd.Context(local)
+    g = ctx.gauge_upload(DIMS, U)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        be, bo = g.pack(b, jqcd.PREC_DW, stream=stream)
+        xe, xo = g.empty(jqcd.PREC_DW), g.empty(jqcd.PREC_DW)
+    stream.synchronize()
+
+    def solve():
+        info, st = g.cg_solve_dev(be, bo, xe, xo, KAPPA, tol=TOL, eo=True, mode=jqcd.CG_DW,
+                                  stream=stream)
+        return info
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        solve()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = jqcd.jqcd_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = [solve() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = jqcd.jqcd_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    hop_bytes = sum(i["hop_bytes"] for i in infos)
+    ms_max, bytes_sum = ms, hop_bytes
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = t.item()
+        t = torch.tensor([hop_bytes], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        bytes_sum = t.item()
+    value = bytes_sum / (ms_max * 1e-3) / 1e9
+    dw_s = ms / args.steps * 1e-3
+
+    # end to end through the host-buffer C ABI call, pinned host memory
+    shape = b.shape
+    b_pin = torch.empty(shape, dtype=torch.complex128, pin_memory=True)
+    b_pin.numpy()[...] = b
+    x_pin = torch.zeros(shape, dtype=torch.complex128, pin_memory=True)
+    bn, xn = b_pin.numpy(), x_pin.numpy()
+    p = g.params(KAPPA, TOL, 20000, True, jqcd.CG_DW)
+    import ctypes
+    info = jqcd.jqcd_solve_info()
+    bptr = bn.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    xptr = xn.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(2):
+        ctx.check(jqcd.jqcd_cg_solve(ctx.h, g.id, ctypes.byref(p), bptr, xptr, ctypes.byref(info)),
+                  "cg_solve")
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_bytes = 0.0
+    for _ in range(e2e_steps):
+        ctx.check(jqcd.jqcd_cg_solve(ctx.h, g.id, ctypes.byref(p), bptr, xptr, ctypes.byref(info)),
+                  "cg_solve")
+        e2e_bytes += info.hop_bytes
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s, e2e_bytes], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
+        e2e_s = t[0].item()
+        tb = torch.tensor([e2e_bytes], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tb)
+        e2e_bytes = tb.item()
+    e2e_value = e2e_bytes / e2e_s / 1e9
+
+    # dominant kernel alone: double-word hop, plus the other precisions
+    def time_hop(prec, n=40):
+        with torch.cuda.stream(stream):
+            pe, po = g.pack(b, prec, stream=stream)
+            out = g.empty(prec)
+        for _ in range(5):
+            g.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
+        stream.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(n):
+            g.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
+        a1.record(stream)
+        stream.synchronize()
+        return a0.elapsed_time(a1) / n
+
+    hop_ms = {name: time_hop(code) for name, code in
+              [("dw", jqcd.PREC_DW), ("f64", jqcd.PREC_F64), ("f32", jqcd.PREC_F32),
+               ("f16n", jqcd.PREC_F16N)]}
+    hbm, peak_kind = peaks()
+    dw_achieved = vh * HOP_BYTES["dw"] / (hop_ms["dw"] * 1e-3) / 1e9
+    traffic = profiled_traffic()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        _, dt1, _ = time_oracle_cg(U, b, 1)  # calibrate: ~10 s sample
+        iters = int(min(30, max(1, round(10.0 / max(dt1 / 3.0, 1e-3)) - 2)))
+        v, dt, threads = time_oracle_cg(U, b, iters)
+        cpu = {"value": round(v, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": sample_description(iters) + f", {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32x2 (double-word, FP64-class)", "data": "synthetic",
+            "config": workload_config(),
+            "roofline": {"bound": "hbm", "achieved": round(dw_achieved, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(dw_achieved / hbm, 4),
+                         "traffic": traffic, "kernel": "hop_kernel<PREC_DW> (plain hop)",
+                         "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
+                    "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cg": {"dw_s": round(dw_s, 5), "dw_iters": infos[-1]["iters"],
+                   "dw_true_rel_resid": infos[-1]["true_rel_resid"],
+                   "dw_full_rel_resid": infos[-1]["full_rel_resid"]},
+            "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
+                           for k, v in hop_ms.items()},
+        }
+        print(json.dumps(line), flush=True)
+    g.free()
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    del np
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

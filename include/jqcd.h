@@ -96,6 +96,10 @@ typedef struct {
 
 JQCD_API int32_t jqcd_abi_version(void);
 
+/* Number of CUDA kernel launches the library has issued in this process
+ * (all contexts).  Used to count the kernels inside a timed region. */
+JQCD_API uint64_t jqcd_kernel_launches(void);
+
 /* Create a context on CUDA device `device` (makes it current for the calling
  * thread).  *out receives the context; release it with jqcd_finalize. */
 JQCD_API jqcd_status jqcd_init(int device, jqcd_ctx **out);

@@ -2,6 +2,7 @@
 // applications and the conjugate-gradient drivers.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -16,6 +17,11 @@
 #include "solver.h"
 
 using namespace jqcd;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}
+void jqcd::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 struct jqcd_ctx {
   int device = 0;
@@ -94,6 +100,8 @@ bool valid_prec(int32_t p) { return p >= 0 && p <= 3; }
 extern "C" {
 
 int32_t jqcd_abi_version(void) { return JQCD_ABI_VERSION; }
+
+uint64_t jqcd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 jqcd_status jqcd_init(int device, jqcd_ctx **out) {
   if (!out) return JQCD_EINVAL;

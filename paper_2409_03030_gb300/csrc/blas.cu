@@ -172,18 +172,22 @@ __global__ void cg_start_kernel(const double *partials, int n, SolverScalars *S,
 }
 
 cudaError_t launch_finalize_sum(const double *partials, int n, double *out, cudaStream_t s) {
+  note_launch();
   finalize_sum_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, out);
   return cudaGetLastError();
 }
 cudaError_t launch_dw_copy(float4 *dst, const float4 *src, int64_t n, cudaStream_t s) {
+  note_launch();
   dw_copy_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(dst, src, n);
   return cudaGetLastError();
 }
 cudaError_t launch_dw_zero(float4 *dst, int64_t n, cudaStream_t s) {
+  note_launch();
   dw_zero_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(dst, n);
   return cudaGetLastError();
 }
 cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s) {
+  note_launch();
   dw_add_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(y, x, n);
   return cudaGetLastError();
 }
@@ -193,29 +197,35 @@ cudaError_t launch_dw_norm2(const float4 *a, int64_t n, double *partials, cudaSt
 }
 cudaError_t launch_dw_xmy_norm(float4 *r, const float4 *b, const float4 *y, int64_t n,
                                double *partials, cudaStream_t s) {
+  note_launch();
   dw_xmy_norm_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(r, b, y, n, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const float4 *Ap, int64_t n,
                                 const SolverScalars *S, double *partials, cudaStream_t s) {
+  note_launch();
   dw_cg_update_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(x, r, p, Ap, n, S, partials);
   return cudaGetLastError();
 }
 cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
                            cudaStream_t s) {
+  note_launch();
   dw_xpay_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(p, r, n, S);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_alpha(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
+  note_launch();
   cg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
+  note_launch();
   cg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
   return cudaGetLastError();
 }
 cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
                             int max_iters, cudaStream_t s) {
+  note_launch();
   cg_start_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S, tol2, max_iters);
   return cudaGetLastError();
 }

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
 template <int PREC, bool DAG, bool AXPY, bool NORM>
 static cudaError_t launch_hop_t(const HopParams &P, cudaStream_t s) {
   const unsigned blocks = hop_blocks(P.g.vh);
+  note_launch();
   hop_kernel<PREC, DAG, AXPY, NORM><<<blocks, kHopThreads, 0, s>>>(P);
   return cudaGetLastError();
 }

@@ -7,6 +7,9 @@
 
 namespace jqcd {
 
+// Process-wide count of kernel launches issued by the library.
+void note_launch();
+
 constexpr int kHopThreads = 128;
 inline unsigned hop_blocks(int64_t vh) { return (unsigned)((vh + kHopThreads - 1) / kHopThreads); }
 

@@ -153,6 +153,7 @@ __global__ void spinor_unpack_kernel(Geom g, int prec, const void *even, const v
 cudaError_t launch_gauge_pack(const Geom &g, const double *canon, void *dw, void *f64, void *f32,
                               cudaStream_t s) {
   const int64_t n = 8 * g.vh;
+  note_launch();
   gauge_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
       g, canon, reinterpret_cast<float4 *>(dw), reinterpret_cast<double2 *>(f64),
       reinterpret_cast<float4 *>(f32));
@@ -162,6 +163,7 @@ cudaError_t launch_gauge_pack(const Geom &g, const double *canon, void *dw, void
 cudaError_t launch_spinor_pack(const Geom &g, int prec, const double *canon, void *even, void *odd,
                                cudaStream_t s) {
   const int64_t n = 2 * g.vh;
+  note_launch();
   spinor_pack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, prec, canon, even, odd);
   return cudaGetLastError();
 }
@@ -169,6 +171,7 @@ cudaError_t launch_spinor_pack(const Geom &g, int prec, const double *canon, voi
 cudaError_t launch_spinor_unpack(const Geom &g, int prec, const void *even, const void *odd,
                                  double *canon, cudaStream_t s) {
   const int64_t n = 2 * g.vh;
+  note_launch();
   spinor_unpack_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, prec, even, odd, canon);
   return cudaGetLastError();
 }

@@ -1,0 +1,57 @@
+"""Time the even-odd hop kernel alone: python -m paper_2409_03030_gb300.hopbench.
+
+Prints one JSON line with the mean launch time (CUDA events on the launching
+stream, after warm-up) and the algorithmic bandwidth (bytes per output site:
+double-word/FP64 1536, FP32 576, FP16+norm 488, plus one spinor when the
+axpy operand is read)."""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import jqcd, synth
+
+HOP_BYTES = {"dw": (1536, 192), "f64": (1536, 192), "f32": (576, 96), "f16n": (488, 52)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=[24, 24, 24, 48])
+    ap.add_argument("--prec", default="dw", choices=sorted(HOP_BYTES))
+    ap.add_argument("--iters", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--axpy", action="store_true")
+    ap.add_argument("--dagger", action="store_true")
+    a = ap.parse_args()
+    dims = tuple(a.dims)
+    prec = jqcd.PRECS[a.prec]
+    ctx = jqcd.Context(0)
+    g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=0.3, seed=1))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        pe, po = g.pack(synth.gaussian_spinor(dims, seed=2), prec, stream=stream)
+        out = g.empty(prec)
+    x = pe if a.axpy else None
+    for _ in range(a.warmup):
+        g.dslash_eo(prec, 0, int(a.dagger), po, x, out, 1.0, -0.12, stream=stream)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.iters):
+        g.dslash_eo(prec, 0, int(a.dagger), po, x, out, 1.0, -0.12, stream=stream)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1) / a.iters
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    per_site = HOP_BYTES[a.prec][0] + (HOP_BYTES[a.prec][1] if a.axpy else 0)
+    print(json.dumps({"dims": dims, "prec": a.prec, "axpy": a.axpy, "dagger": a.dagger,
+                      "us_per_launch": round(ms * 1e3, 2), "bytes_per_launch": vh * per_site,
+                      "gbs": round(vh * per_site / (ms * 1e-3) / 1e9, 1)}))
+    g.free()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()

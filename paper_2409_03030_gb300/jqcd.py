@@ -59,6 +59,7 @@ _st = ctypes.c_int32
 _u64 = ctypes.c_uint64
 _SIGNATURES = {
     "jqcd_abi_version": (ctypes.c_int32, []),
+    "jqcd_kernel_launches": (ctypes.c_uint64, []),
     "jqcd_init": (_st, [ctypes.c_int, ctypes.POINTER(_vp)]),
     "jqcd_finalize": (_st, [_vp]),
     "jqcd_last_error": (ctypes.c_char_p, [_vp]),
