@@ -145,6 +145,30 @@ JQCD_API jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t pr
                            int32_t dagger, const void *in, const void *x, void *out, double a,
                            double b, double *norm2_dev, void *stream);
 
+/* Same operation as jqcd_dslash_eo, for callers that must not have the
+ * library allocate device memory during the call.  This entry point has no
+ * counterpart in the paper; it exists for users such as a solve server that
+ * budgets every byte of HBM up front, or code that overlaps work on several
+ * streams and cannot afford the device-wide synchronisation that cudaMalloc
+ * and cudaFree may cause.  jqcd_dslash_eo allocates its norm scratch on first
+ * use; this variant instead uses one fixed array of
+ * JQCD_NOALLOC_MAX_SITES_PER_PARITY / 128 doubles (128 KiB) compiled into the
+ * library, present on every device that loads the library until the process
+ * exits.  Lattices with more than JQCD_NOALLOC_MAX_SITES_PER_PARITY sites per
+ * parity are rejected with JQCD_EINVAL.
+ * The first call on a device that asks for a norm looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.
+ * All calls share the one array and each call overwrites what it reads, so
+ * nothing needs clearing, but calls whose work overlaps on the GPU (other
+ * streams, other host threads) race on it: serialise them.
+ * Arguments, layouts and results are those of jqcd_dslash_eo. */
+#define JQCD_NOALLOC_MAX_SITES_PER_PARITY (16384 * 128)
+JQCD_API jqcd_status jqcd_dslash_eo_noalloc(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
+                                            int32_t out_parity, int32_t dagger, const void *in,
+                                            const void *x, void *out, double a, double b,
+                                            double *norm2_dev, void *stream);
+
 /* out = Mhat' Mhat in on the even sites, Mhat = 1 - kappa^2 H_eo H_oe (the
  * even-odd form of DdagD_operator, paper "Definition of Dirac operators").
  * in, out: even-parity device buffers of `prec`, out must not alias in.

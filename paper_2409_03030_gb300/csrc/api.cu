@@ -341,3 +341,65 @@ jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of jqcd_dslash_eo (declared in jqcd.h).
+//
+// jqcd_dslash_eo allocates its reduction scratch from the device heap the
+// first time a norm is requested.  This variant keeps that scratch -- one
+// double per 128-site block of the hop -- in a fixed array compiled into the
+// library instead, so the call itself never allocates.  The array lives in
+// every device that loads the library until the process exits.
+#include <mutex>
+
+namespace {
+constexpr int kNoAllocMaxBlocks = JQCD_NOALLOC_MAX_SITES_PER_PARITY / kHopThreads;
+static_assert(JQCD_NOALLOC_MAX_SITES_PER_PARITY % kHopThreads == 0, "limit must be whole blocks");
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocMaxBlocks];
+
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device `dev`, looked up
+// once per device (the host-side name of the array is not a device address).
+cudaError_t noalloc_scratch(int dev, double **out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+}  // namespace
+
+extern "C" jqcd_status jqcd_dslash_eo_noalloc(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
+                                              int32_t out_parity, int32_t dagger, const void *in,
+                                              const void *x, void *out, double a, double b,
+                                              double *norm2_dev, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in || !out || in == out || (out_parity != 0 && out_parity != 1) || !valid_prec(prec))
+    return fail(ctx, JQCD_EINVAL, "dslash_eo_noalloc: bad argument");
+  if (G->g.vh > (int64_t)JQCD_NOALLOC_MAX_SITES_PER_PARITY)
+    return fail(ctx, JQCD_EINVAL,
+                "dslash_eo_noalloc: %lld sites per parity exceed the fixed scratch limit of %d",
+                (long long)G->g.vh, JQCD_NOALLOC_MAX_SITES_PER_PARITY);
+  if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+    return fail(ctx, JQCD_EINVAL, "dslash_eo_noalloc: device index %d not supported", ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  double *scratch = nullptr;
+  if (norm2_dev) CK(noalloc_scratch(ctx->device, &scratch), "cudaGetSymbolAddress(noalloc scratch)");
+  // Every partial the finalize step reads is written by the hop launch of this
+  // same call, so nothing in the scratch has to be cleared first.
+  HopParams P = G->hop_params(prec, out_parity, in, x, out, a, b, scratch);
+  CK(launch_hop(prec, P, dagger != 0, x != nullptr, norm2_dev != nullptr, s), "hop launch");
+  if (norm2_dev) CK(launch_finalize_sum(scratch, (int)hop_blocks(G->g.vh), norm2_dev, s), "norm");
+  return JQCD_OK;
+}

@@ -72,6 +72,8 @@ _SIGNATURES = {
     "jqcd_spinor_unpack": (_st, [_vp, _u64, ctypes.c_int32, _vp, _vp, _dp, _vp]),
     "jqcd_dslash_eo": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp, _vp,
                              _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
+    "jqcd_dslash_eo_noalloc": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp, _vp]),
     "jqcd_mdagm": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_double, _vp, _vp, _vp, _vp]),
     "jqcd_dirac_apply": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, _vp,
                                _vp, _vp, _vp, _vp]),
@@ -220,6 +222,15 @@ class Gauge:
                                       _dev_ptr(inp), _dev_ptr(x), _dev_ptr(out), float(a),
                                       float(b), _dev_ptr(norm2), _stream_ptr(stream)),
                        "jqcd_dslash_eo")
+
+    def dslash_eo_noalloc(self, prec, out_parity, dagger, inp, x, out, a=0.0, b=1.0, norm2=None,
+                          stream=None):
+        """jqcd_dslash_eo_noalloc: the hop without any allocation inside the call."""
+        self.ctx.check(jqcd_dslash_eo_noalloc(self.ctx.h, self.id, int(prec), int(out_parity),
+                                              int(dagger), _dev_ptr(inp), _dev_ptr(x),
+                                              _dev_ptr(out), float(a), float(b), _dev_ptr(norm2),
+                                              _stream_ptr(stream)),
+                       "jqcd_dslash_eo_noalloc")
 
     def mdagm(self, prec, kappa, inp, out, norm2=None, stream=None):
         self.ctx.check(jqcd_mdagm(self.ctx.h, self.id, int(prec), float(kappa), _dev_ptr(inp),
