@@ -160,10 +160,176 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-word hop: one runtime loop over the eight hops.  The body (spinor
+// load, projection, link load, compensated mat-vec, reconstruction) exists
+// once in the instruction stream; the direction only selects a small
+// projection/reconstruction case and the neighbour.  A fully unrolled
+// double-word body is ~10k instructions per site and does not fit the
+// instruction caches.  Forward/backward and dagger signs ride on the FMAs of
+// the error-free additions (dw_add_sgn), so they cost nothing.
+
+// h = a + sg * phi * b with phi = 1 (I = false) or i (I = true).
+template <bool I> __device__ __forceinline__ cw cadd_ph(const cw &a, const cw &b, float sg) {
+  if (I) return cw{dw_add_sgn(a.re, b.im, -sg), dw_add_sgn(a.im, b.re, sg)};
+  return cw{dw_add_sgn(a.re, b.re, sg), dw_add_sgn(a.im, b.im, sg)};
+}
+// acc += sg * phi * r
+template <bool I> __device__ __forceinline__ void cacc_ph(cw &acc, const cw &r, float sg) {
+  if (I) { acc.re = dw_add_sgn(acc.re, r.im, -sg); acc.im = dw_add_sgn(acc.im, r.re, sg); }
+  else { acc.re = dw_add_sgn(acc.re, r.re, sg); acc.im = dw_add_sgn(acc.im, r.im, sg); }
+}
+
+// (1 + S gamma_mu) psi, rows 0 and 1, DeGrand-Rossi basis (see hop.cuh).
+template <int MU> __device__ __forceinline__ void project_dw(const cw (&psi)[4][3], cw (&h)[2][3], float S) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) { h[0][c] = cadd_ph<true>(psi[0][c], psi[3][c], S);   h[1][c] = cadd_ph<true>(psi[1][c], psi[2][c], S); }
+    if (MU == 1) { h[0][c] = cadd_ph<false>(psi[0][c], psi[3][c], -S); h[1][c] = cadd_ph<false>(psi[1][c], psi[2][c], S); }
+    if (MU == 2) { h[0][c] = cadd_ph<true>(psi[0][c], psi[2][c], S);   h[1][c] = cadd_ph<true>(psi[1][c], psi[3][c], -S); }
+    if (MU == 3) { h[0][c] = cadd_ph<false>(psi[0][c], psi[2][c], S);  h[1][c] = cadd_ph<false>(psi[1][c], psi[3][c], S); }
+  }
+}
+
+template <int MU> __device__ __forceinline__ void reconstruct_dw(const cw (&r)[2][3], cw (&acc)[4][3], float S) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    cacc(acc[0][c], r[0][c]);
+    cacc(acc[1][c], r[1][c]);
+    if (MU == 0) { cacc_ph<true>(acc[2][c], r[1][c], -S);  cacc_ph<true>(acc[3][c], r[0][c], -S); }
+    if (MU == 1) { cacc_ph<false>(acc[2][c], r[1][c], S);  cacc_ph<false>(acc[3][c], r[0][c], -S); }
+    if (MU == 2) { cacc_ph<true>(acc[2][c], r[0][c], -S);  cacc_ph<true>(acc[3][c], r[1][c], S); }
+    if (MU == 3) { cacc_ph<false>(acc[2][c], r[0][c], S);  cacc_ph<false>(acc[3][c], r[1][c], S); }
+  }
+}
+
+template <bool DAG, bool AXPY, bool NORM>
+__global__ void __launch_bounds__(kHopThreads) hop_dw_kernel(const HopParams P) {
+  typedef PT<PREC_DW> T;
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const Geom &g = P.g;
+  const int64_t vh = g.vh;
+  dwacc nrm{0.f, 0.f};
+  if (idx < vh) {
+    int x, y, z, t;
+    cb_coords(g, idx, P.out_parity, x, y, z, t);
+    cw acc[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[a][c] = T::zero();
+    const float4 *in = reinterpret_cast<const float4 *>(P.in);
+    const float4 *gauge = reinterpret_cast<const float4 *>(P.gauge);
+    const int p = P.out_parity;
+#pragma unroll 1
+    for (int d = 0; d < 8; ++d) {
+      const int mu = d >> 1;
+      const bool bwd = (d & 1) != 0;
+      int xn = x, yn = y, zn = z, tn = t;
+      bool neg = false;
+      if (!bwd) {
+        switch (mu) {
+          case 0: xn = (x + 1 == g.nx) ? 0 : x + 1; break;
+          case 1: yn = (y + 1 == g.ny) ? 0 : y + 1; break;
+          case 2: zn = (z + 1 == g.nz) ? 0 : z + 1; break;
+          default:
+            if (t + 1 == g.nt) { tn = 0; neg = g.tanti != 0; } else tn = t + 1;
+        }
+      } else {
+        switch (mu) {
+          case 0: xn = (x == 0) ? g.nx - 1 : x - 1; break;
+          case 1: yn = (y == 0) ? g.ny - 1 : y - 1; break;
+          case 2: zn = (z == 0) ? g.nz - 1 : z - 1; break;
+          default:
+            if (t == 0) { tn = g.nt - 1; neg = g.tanti != 0; } else tn = t - 1;
+        }
+      }
+      const int64_t nb = cb_index(g, xn, yn, zn, tn);
+      cw psi[4][3];
+      T::load_spinor(in, vh, nb, psi);
+      // forward hops use (1 - gamma_mu), backward (1 + gamma_mu); dagger swaps
+      const float S = (bwd != DAG) ? 1.f : -1.f;
+      cw h[2][3];
+      switch (mu) {
+        case 0: project_dw<0>(psi, h, S); break;
+        case 1: project_dw<1>(psi, h, S); break;
+        case 2: project_dw<2>(psi, h, S); break;
+        default: project_dw<3>(psi, h, S);
+      }
+      if (neg) T::negate_if(h, true);
+      // forward: U_mu(x) from this parity; backward: U_mu(x-mu)^dag from the
+      // other parity, loaded transposed with the imaginary parts negated
+      const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
+      const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
+      const float cs = bwd ? -1.f : 1.f;
+      cw u[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const float4 v = __ldcs(L + (int64_t)(a * sa + b * sb) * vh);
+          u[a][b] = cw{dw_make(v.x, v.y), dw_make(cs * v.z, cs * v.w)};
+        }
+      cw r[2][3];
+      matvec2<false>(u, h, r);
+      switch (mu) {
+        case 0: reconstruct_dw<0>(r, acc, S); break;
+        case 1: reconstruct_dw<1>(r, acc, S); break;
+        case 2: reconstruct_dw<2>(r, acc, S); break;
+        default: reconstruct_dw<3>(r, acc, S);
+      }
+    }
+    const dw b = T::scalar(P.b, P.b_split);
+    cw o[4][3];
+    if (AXPY) {
+      const dw a = T::scalar(P.a, P.a_split);
+      cw xs[4][3];
+      T::load_spinor(P.x, vh, idx, xs);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::axpby(a, xs[s][c], b, acc[s][c]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::scale(b, acc[s][c]);
+    }
+    T::store_spinor(P.out, vh, idx, o);
+    if (NORM) nrm = site_norm2<PREC_DW>(o);
+  }
+  if (NORM) {
+    const double s = block_sum_dw(nrm);
+    if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+  }
+}
+
+template <bool DAG, bool AXPY, bool NORM>
+static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
+  note_launch();
+  hop_dw_kernel<DAG, AXPY, NORM><<<hop_blocks(P.g.vh), kHopThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_hop_dw(const HopParams &P, bool dag, bool axpy, bool norm, cudaStream_t s) {
+  const int key = (dag ? 4 : 0) | (axpy ? 2 : 0) | (norm ? 1 : 0);
+  switch (key) {
+    case 0: return launch_hop_dw_t<false, false, false>(P, s);
+    case 1: return launch_hop_dw_t<false, false, true>(P, s);
+    case 2: return launch_hop_dw_t<false, true, false>(P, s);
+    case 3: return launch_hop_dw_t<false, true, true>(P, s);
+    case 4: return launch_hop_dw_t<true, false, false>(P, s);
+    case 5: return launch_hop_dw_t<true, false, true>(P, s);
+    case 6: return launch_hop_dw_t<true, true, false>(P, s);
+    default: return launch_hop_dw_t<true, true, true>(P, s);
+  }
+}
+
 cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool norm,
                        cudaStream_t s) {
   switch (prec) {
-    case PREC_DW: return launch_hop_p<PREC_DW>(P, dag, axpy, norm, s);
+    case PREC_DW: return launch_hop_dw(P, dag, axpy, norm, s);
     case PREC_F64: return launch_hop_p<PREC_F64>(P, dag, axpy, norm, s);
     case PREC_F32: return launch_hop_p<PREC_F32>(P, dag, axpy, norm, s);
     case PREC_F16N: return launch_hop_p<PREC_F16N>(P, dag, axpy, norm, s);

@@ -102,6 +102,18 @@ __device__ __forceinline__ void dw_accum(dw &x, dw v) {
   x.l = __fadd_rn(__fadd_rn(x.l, v.l), e);
 }
 
+// a + s*b for s = +1 or -1, unnormalised.  The sign rides on FMAs, which are
+// exact here (s*b is exact), so TwoSum keeps its error-free property.
+__device__ __forceinline__ dw dw_add_sgn(dw a, dw b, float s) {
+  const float sum = __fmaf_rn(s, b.h, a.h);
+  const float bb = __fsub_rn(sum, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(sum, bb)), __fmaf_rn(s, b.h, -bb));
+  return dw_make(sum, __fadd_rn(__fmaf_rn(s, b.l, a.l), e));
+}
+
+// x += s*v for s = +1 or -1 (running sum, unnormalised).
+__device__ __forceinline__ void dw_accum_sgn(dw &x, dw v, float s) { x = dw_add_sgn(x, v, s); }
+
 // Square-accumulate a*a into (s, c) (for norms).
 __device__ __forceinline__ void acc_sq(dwacc &A, dw a) { acc_mad(A, a, a); }
 
