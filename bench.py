@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="jqcd", choices=["jqcd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the 32^3x64 mixed-vs-double-word CG comparison")
     return ap.parse_args()
 
 
@@ -332,6 +334,48 @@ def run_gpu(args):
     dw_achieved = vh * HOP_BYTES["dw"] / (hop_ms["dw"] * 1e-3) / 1e9
     traffic = profiled_traffic()
 
+    # CG to 1e-10: double-word vs mixed precision, on the workload lattice and
+    # on the 32^3x64 configuration (exp(i 0.4 H) links, kappa 0.122)
+    def time_solves(gg, be_, bo_, xe_, xo_, kappa, mode, n):
+        gg.cg_solve_dev(be_, bo_, xe_, xo_, kappa, tol=TOL, eo=True, mode=mode, stream=stream)
+        t = []
+        info = None
+        for _ in range(n):
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            info, _ = gg.cg_solve_dev(be_, bo_, xe_, xo_, kappa, tol=TOL, eo=True, mode=mode,
+                                      stream=stream)
+            a1.record(stream)
+            stream.synchronize()
+            t.append(a0.elapsed_time(a1) * 1e-3)
+        return statistics.median(t), info
+
+    def cg_table(gg, be_, bo_, kappa, n):
+        xe_, xo_ = gg.empty(jqcd.PREC_DW), gg.empty(jqcd.PREC_DW)
+        out = {}
+        for name, mode in [("dw", jqcd.CG_DW), ("mixed_f32", jqcd.CG_MIXED_F32),
+                           ("mixed_f16", jqcd.CG_MIXED_F16)]:
+            t, info = time_solves(gg, be_, bo_, xe_, xo_, kappa, mode, n)
+            out[name] = {"s": round(t, 5), "iters": info["iters"],
+                         "reliable_updates": info["reliable_updates"],
+                         "true_rel_resid": info["true_rel_resid"],
+                         "full_rel_resid": info["full_rel_resid"]}
+        out["speedup_mixed_f16_vs_dw"] = round(out["dw"]["s"] / out["mixed_f16"]["s"], 3)
+        out["speedup_mixed_f32_vs_dw"] = round(out["dw"]["s"] / out["mixed_f32"]["s"], 3)
+        return out
+
+    cg_work = cg_table(g, be, bo, KAPPA, 3)
+    cg_c2 = None
+    if not args.no_config2:
+        d2 = (32, 32, 32, 64)
+        g2 = ctx.gauge_upload(d2, synth.gauge(d2, "expi", eps=0.4, seed=11))
+        with torch.cuda.stream(stream):
+            b2e, b2o = g2.pack(synth.gaussian_spinor(d2, seed=12), jqcd.PREC_DW, stream=stream)
+        stream.synchronize()
+        cg_c2 = cg_table(g2, b2e, b2o, 0.122, 3)
+        cg_c2["workload"] = "32^3x64, exp(i*0.4*H) links, kappa 0.122, even-odd, tol 1e-10"
+        g2.free()
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         _, dt1, _ = time_oracle_cg(U, b, 1)  # calibrate: ~10 s sample
@@ -358,7 +402,8 @@ def run_gpu(args):
             "clocks": clocks,
             "cg": {"dw_s": round(dw_s, 5), "dw_iters": infos[-1]["iters"],
                    "dw_true_rel_resid": infos[-1]["true_rel_resid"],
-                   "dw_full_rel_resid": infos[-1]["full_rel_resid"]},
+                   "dw_full_rel_resid": infos[-1]["full_rel_resid"],
+                   "modes_24x24x24x48": cg_work, "modes_32x32x32x64": cg_c2},
             "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
                            for k, v in hop_ms.items()},
         }

@@ -199,7 +199,7 @@ typedef struct {
   int32_t eo;        /* 1: even-odd preconditioned, 0: CG on D'D, whole lattice */
   int32_t mode;      /* JQCD_CG_* */
   int32_t verbose;   /* 0 quiet; >= 3 prints residuals to stderr (paper verbose_level) */
-  double delta;      /* mixed modes: reliable-update threshold, 0 -> 0.1 */
+  double delta;      /* mixed modes: reliable-update threshold, 0 -> 0.01 */
   int32_t use_x0;    /* 1: x holds the start vector on entry; 0: start from 0 */
   int32_t reserved;
 } jqcd_solve_params;

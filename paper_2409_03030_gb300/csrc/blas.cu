@@ -72,7 +72,7 @@ __global__ void dw_xmy_norm_kernel(float4 *__restrict__ r, const float4 *__restr
 __global__ void dw_cg_update_kernel(float4 *__restrict__ x, float4 *__restrict__ r,
                                     const float4 *__restrict__ p, const float4 *__restrict__ Ap,
                                     int64_t n, const SolverScalars *S, double *partials) {
-  if (S->done) return;
+  if (S->halt) return;
   const dw al = dw_make(S->alpha_dw.x, S->alpha_dw.y);
   const dw mal = dw_neg(al);
   dwacc A{0.f, 0.f};
@@ -93,7 +93,7 @@ __global__ void dw_cg_update_kernel(float4 *__restrict__ x, float4 *__restrict__
 
 __global__ void dw_xpay_kernel(float4 *__restrict__ p, const float4 *__restrict__ r, int64_t n,
                                const SolverScalars *S) {
-  if (S->done) return;
+  if (S->halt) return;
   const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     float4 pv = p[i], rv = r[i];
@@ -121,12 +121,13 @@ __global__ void finalize_sum_kernel(const double *partials, int n, double *out) 
 }
 
 __global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S) {
-  if (S->done) return;
+  if (S->halt) return;
   const double pAp = sum_partials(partials, n);
   if (threadIdx.x == 0) {
     S->pAp = pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {  // breakdown: A not positive or NaN
       S->done = 2;
+      S->halt = 1;
       return;
     }
     const double a = S->rr / pAp;
@@ -139,18 +140,19 @@ __global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S)
 }
 
 __global__ void cg_beta_kernel(const double *partials, int n, SolverScalars *S) {
-  if (S->done) return;
+  if (S->halt) return;
   const double rr_new = sum_partials(partials, n);
   if (threadIdx.x == 0) {
     S->rr_new = rr_new;
     S->iters += 1;
-    if (!isfinite(rr_new)) { S->done = 2; return; }
+    if (!isfinite(rr_new)) { S->done = 2; S->halt = 1; return; }
     if (rr_new <= S->stop_rr) {
       S->rr = rr_new;
       S->done = 1;
+      S->halt = 1;
       return;
     }
-    if (S->iters >= S->max_iters) S->done = 3;
+    if (S->iters >= S->max_iters) { S->done = 3; S->halt = 1; }
     const double b = rr_new / S->rr;
     S->beta = b;
     S->beta_dw = split_d(b);
@@ -160,13 +162,17 @@ __global__ void cg_beta_kernel(const double *partials, int n, SolverScalars *S) 
 }
 
 __global__ void cg_start_kernel(const double *partials, int n, SolverScalars *S, double tol2,
-                                int max_iters) {
+                                int max_iters, double delta2) {
   const double rr = sum_partials(partials, n);
   if (threadIdx.x == 0) {
     S->rr = rr;
+    S->true_rr = rr;  // the start residual is computed from x, not recursively
     S->stop_rr = tol2 * S->rhs2;
     S->max_iters = max_iters;
+    S->delta2 = delta2;
     S->done = rr <= S->stop_rr ? 1 : (S->iters >= max_iters ? 3 : 0);
+    S->halt = S->done != 0;
+    S->need_update = 0;
     S->rr_max = rr;
   }
 }
@@ -224,9 +230,9 @@ cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cuda
   return cudaGetLastError();
 }
 cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
-                            int max_iters, cudaStream_t s) {
+                            int max_iters, double delta2, cudaStream_t s) {
   note_launch();
-  cg_start_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S, tol2, max_iters);
+  cg_start_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S, tol2, max_iters, delta2);
   return cudaGetLastError();
 }
 

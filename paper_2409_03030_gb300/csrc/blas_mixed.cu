@@ -1,0 +1,216 @@
+// Vector and scalar kernels of mixed-precision CG with reliable updates.
+//
+// The inner CG runs on the even-parity Schur system in low precision: the
+// operator and the search direction p (and A p) in FP32 or FP16 with a
+// per-site norm, the iterate x_s and residual r_s in FP32.  Whenever the
+// inner residual has dropped by a factor delta since the last update (or the
+// inner loop thinks it has converged), the host folds x_s into the
+// double-word solution x, recomputes r = rhs - A x in double-word arithmetic,
+// and restarts the inner residual from it while keeping the search direction
+// (reliable updates; Sleijpen and van der Vorst 1996).  Every decision is
+// taken on the device in single-block kernels; the host only polls.
+#include <cuda_runtime.h>
+
+#include "fields.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace jqcd {
+
+// FP32 spinor chunks of one site <-> registers
+__device__ __forceinline__ void load_f32(const float4 *base, int64_t vh, int64_t i, cf (&s)[4][3]) {
+  PT<PREC_F32>::load_spinor(base, vh, i, s);
+}
+__device__ __forceinline__ void store_f32(float4 *base, int64_t vh, int64_t i, const cf (&s)[4][3]) {
+  PT<PREC_F32>::store_spinor(base, vh, i, s);
+}
+
+template <int PREC>
+__global__ void mixed_update_kernel(float4 *__restrict__ xs, float4 *__restrict__ rs,
+                                    const void *__restrict__ p, const void *__restrict__ Ap,
+                                    int64_t vh, const SolverScalars *S, double *partials) {
+  if (S->halt) return;
+  const float a = S->alpha_f;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float n2 = 0.f;
+  if (i < vh) {
+    cf pv[4][3], av[4][3], xv[4][3], rv[4][3];
+    PT<PREC>::load_spinor(p, vh, i, pv);
+    PT<PREC>::load_spinor(Ap, vh, i, av);
+    load_f32(xs, vh, i, xv);
+    load_f32(rs, vh, i, rv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      cf &x = xv[k / 3][k % 3], &r = rv[k / 3][k % 3];
+      const cf pp = pv[k / 3][k % 3], aa = av[k / 3][k % 3];
+      x.re = fmaf(a, pp.re, x.re);
+      x.im = fmaf(a, pp.im, x.im);
+      r.re = fmaf(-a, aa.re, r.re);
+      r.im = fmaf(-a, aa.im, r.im);
+      n2 = fmaf(r.re, r.re, fmaf(r.im, r.im, n2));
+    }
+    store_f32(xs, vh, i, xv);
+    store_f32(rs, vh, i, rv);
+  }
+  const double s = block_sum_f(n2);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <int PREC>
+__global__ void mixed_xpay_kernel(void *__restrict__ p, const float4 *__restrict__ rs, int64_t vh,
+                                  const SolverScalars *S) {
+  if (S->halt) return;
+  const float b = S->beta_f;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vh) return;
+  cf pv[4][3], rv[4][3];
+  PT<PREC>::load_spinor(p, vh, i, pv);
+  load_f32(rs, vh, i, rv);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cf &q = pv[k / 3][k % 3];
+    const cf r = rv[k / 3][k % 3];
+    q.re = fmaf(b, q.re, r.re);
+    q.im = fmaf(b, q.im, r.im);
+  }
+  PT<PREC>::store_spinor(p, vh, i, pv);
+}
+
+template <int PREC>
+__global__ void mixed_copy_kernel(void *__restrict__ p, const float4 *__restrict__ rs, int64_t vh) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= vh) return;
+  cf rv[4][3];
+  load_f32(rs, vh, i, rv);
+  PT<PREC>::store_spinor(p, vh, i, rv);
+}
+
+// FP32 chunk j of a site holds complex components 2j and 2j+1; double-word
+// chunk k holds component k.  One thread per (site, FP32 chunk).
+__global__ void dw_to_f32_kernel(float4 *__restrict__ rs, const float4 *__restrict__ r, int64_t vh) {
+  const int64_t n = 6 * vh;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = q / vh, i = q % vh;
+    const float4 a = r[(2 * j) * vh + i], b = r[(2 * j + 1) * vh + i];
+    rs[q] = make_float4(a.x, a.z, b.x, b.z);  // normalised pairs: hi = nearest float
+  }
+}
+
+__global__ void dw_add_f32_kernel(float4 *__restrict__ x, float4 *__restrict__ xs, int64_t vh) {
+  const int64_t n = 6 * vh;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = q / vh, i = q % vh;
+    const float4 s = xs[q];
+    float4 *xa = x + (2 * j) * vh + i, *xb = x + (2 * j + 1) * vh + i;
+    float4 a = *xa, b = *xb;
+    dw ar = dw_add(dw_make(a.x, a.y), dw_make(s.x, 0.f));
+    dw ai = dw_add(dw_make(a.z, a.w), dw_make(s.y, 0.f));
+    dw br = dw_add(dw_make(b.x, b.y), dw_make(s.z, 0.f));
+    dw bi = dw_add(dw_make(b.z, b.w), dw_make(s.w, 0.f));
+    *xa = make_float4(ar.h, ar.l, ai.h, ai.l);
+    *xb = make_float4(br.h, br.l, bi.h, bi.l);
+    xs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+__device__ __forceinline__ double sum_partials_m(const double *partials, int n) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+  return block_sum_d(v);
+}
+
+__global__ void mixed_beta_kernel(const double *partials, int n, SolverScalars *S) {
+  if (S->halt) return;
+  const double rr_new = sum_partials_m(partials, n);
+  if (threadIdx.x == 0) {
+    S->rr_new = rr_new;
+    S->iters += 1;
+    if (!isfinite(rr_new)) { S->done = 2; S->halt = 1; return; }
+    if (rr_new <= S->stop_rr || rr_new < S->delta2 * S->rr_max || S->iters >= S->max_iters) {
+      S->need_update = 1;  // the host runs the double-word update next
+      S->halt = 1;
+      return;
+    }
+    const double b = rr_new / S->rr;
+    S->beta = b;
+    S->beta_f = (float)b;
+    S->rr = rr_new;
+    if (rr_new > S->rr_max) S->rr_max = rr_new;
+  }
+}
+
+__global__ void mixed_after_update_kernel(const double *partials, int n, SolverScalars *S) {
+  const double rr_true = sum_partials_m(partials, n);
+  if (threadIdx.x == 0) {
+    S->reliable_updates += 1;
+    S->need_update = 0;
+    S->true_rr = rr_true;
+    if (!isfinite(rr_true)) { S->done = 2; S->halt = 1; return; }
+    if (rr_true <= S->stop_rr) { S->rr = rr_true; S->done = 1; S->halt = 1; return; }
+    if (S->iters >= S->max_iters) { S->rr = rr_true; S->done = 3; S->halt = 1; return; }
+    const double b = rr_true / S->rr;
+    S->beta = b;
+    S->beta_f = (float)b;
+    S->rr = rr_true;
+    S->rr_max = rr_true;
+    S->halt = 0;
+  }
+}
+
+static unsigned site_blocks(int64_t vh) { return (unsigned)((vh + kBlasThreads - 1) / kBlasThreads); }
+
+cudaError_t launch_mixed_update(int hop_prec, float4 *xs, float4 *rs, const void *p, const void *Ap,
+                                int64_t vh, const SolverScalars *S, double *partials, cudaStream_t s) {
+  note_launch();
+  if (hop_prec == PREC_F16N)
+    mixed_update_kernel<PREC_F16N><<<site_blocks(vh), kBlasThreads, 0, s>>>(xs, rs, p, Ap, vh, S, partials);
+  else
+    mixed_update_kernel<PREC_F32><<<site_blocks(vh), kBlasThreads, 0, s>>>(xs, rs, p, Ap, vh, S, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_xpay(int hop_prec, void *p, const float4 *rs, int64_t vh,
+                              const SolverScalars *S, cudaStream_t s) {
+  note_launch();
+  if (hop_prec == PREC_F16N)
+    mixed_xpay_kernel<PREC_F16N><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh, S);
+  else
+    mixed_xpay_kernel<PREC_F32><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_copy(int hop_prec, void *p, const float4 *rs, int64_t vh, cudaStream_t s) {
+  note_launch();
+  if (hop_prec == PREC_F16N)
+    mixed_copy_kernel<PREC_F16N><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh);
+  else
+    mixed_copy_kernel<PREC_F32><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dw_to_f32(float4 *rs, const float4 *r, int64_t vh, cudaStream_t s) {
+  note_launch();
+  dw_to_f32_kernel<<<blas_blocks(6 * vh), kBlasThreads, 0, s>>>(rs, r, vh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dw_add_f32(float4 *x, float4 *xs, int64_t vh, cudaStream_t s) {
+  note_launch();
+  dw_add_f32_kernel<<<blas_blocks(6 * vh), kBlasThreads, 0, s>>>(x, xs, vh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
+  note_launch();
+  mixed_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_after_update(const double *partials, int n, SolverScalars *S,
+                                      cudaStream_t s) {
+  note_launch();
+  mixed_after_update_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
+  return cudaGetLastError();
+}
+
+}  // namespace jqcd

@@ -161,9 +161,9 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
 }
 
 // ---------------------------------------------------------------------------
-// Double-word hop: one runtime loop over the eight hops.  The body (spinor
-// load, projection, link load, compensated mat-vec, reconstruction) exists
-// once in the instruction stream; the direction only selects a small
+// Double-word hop: one runtime loop over the eight hops.  The body
+// (projection, compensated mat-vec, reconstruction) exists once in the
+// instruction stream; the direction only selects a small
 // projection/reconstruction case and the neighbour.  A fully unrolled
 // double-word body is ~10k instructions per site and does not fit the
 // instruction caches.  Forward/backward and dagger signs ride on the FMAs of
@@ -203,9 +203,69 @@ template <int MU> __device__ __forceinline__ void reconstruct_dw(const cw (&r)[2
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-word hop with the operands of the next hop prefetched into shared
+// memory (cp.async, two stages), so each warp's memory latency overlaps its
+// own arithmetic instead of depending on other resident warps.
+constexpr int kDwStageChunks = 21;  // 12 spinor + 9 link chunks of 16 bytes
+constexpr size_t kDwStagedSmem = 2ull * kDwStageChunks * kHopThreads * 16;
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool keep_l1) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (keep_l1)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Neighbour of hop d (mu = d/2, backward when d is odd) and its boundary sign.
+__device__ __forceinline__ int64_t hop_neighbour(const Geom &g, int x, int y, int z, int t, int d,
+                                                 bool &neg) {
+  const int mu = d >> 1;
+  const bool bwd = (d & 1) != 0;
+  neg = false;
+  if (!bwd) {
+    switch (mu) {
+      case 0: x = (x + 1 == g.nx) ? 0 : x + 1; break;
+      case 1: y = (y + 1 == g.ny) ? 0 : y + 1; break;
+      case 2: z = (z + 1 == g.nz) ? 0 : z + 1; break;
+      default: if (t + 1 == g.nt) { t = 0; neg = g.tanti != 0; } else t = t + 1;
+    }
+  } else {
+    switch (mu) {
+      case 0: x = (x == 0) ? g.nx - 1 : x - 1; break;
+      case 1: y = (y == 0) ? g.ny - 1 : y - 1; break;
+      case 2: z = (z == 0) ? g.nz - 1 : z - 1; break;
+      default: if (t == 0) { t = g.nt - 1; neg = g.tanti != 0; } else t = t - 1;
+    }
+  }
+  return cb_index(g, x, y, z, t);
+}
+
+// Issue the copies of hop d's neighbour spinor and link (in [a][b] order of
+// the matrix W the hop multiplies) into one stage, chunk-major [k][thread].
+__device__ __forceinline__ void stage_hop(float4 *st, const float4 *in, const float4 *gauge,
+                                          int64_t vh, int p, int64_t idx, int d, int64_t nb) {
+  const int mu = d >> 1;
+  const bool bwd = (d & 1) != 0;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) cp_async16(st + k * kHopThreads + tid, in + k * vh + nb, true);
+  const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
+  const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      cp_async16(st + (12 + 3 * a + b) * kHopThreads + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
+}
+
 template <bool DAG, bool AXPY, bool NORM>
-__global__ void __launch_bounds__(kHopThreads) hop_dw_kernel(const HopParams P) {
+__global__ void __launch_bounds__(kHopThreads) hop_dw_staged_kernel(const HopParams P) {
   typedef PT<PREC_DW> T;
+  extern __shared__ float4 dsm[];
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const Geom &g = P.g;
@@ -222,33 +282,29 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_kernel(const HopParams P) 
     const float4 *in = reinterpret_cast<const float4 *>(P.in);
     const float4 *gauge = reinterpret_cast<const float4 *>(P.gauge);
     const int p = P.out_parity;
+    const int tid = threadIdx.x;
+    bool neg_next;
+    int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
+    stage_hop(dsm, in, gauge, vh, p, idx, 0, nb);
+    cp_async_commit();
 #pragma unroll 1
     for (int d = 0; d < 8; ++d) {
+      const bool neg = neg_next;
+      if (d < 7) {
+        nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
+        stage_hop(dsm + ((d + 1) & 1) * kDwStageChunks * kHopThreads, in, gauge, vh, p, idx, d + 1, nb);
+      }
+      cp_async_commit();
+      cp_async_wait1();  // this thread's copies of hop d have landed
+      const float4 *st = dsm + (d & 1) * kDwStageChunks * kHopThreads + tid;
       const int mu = d >> 1;
       const bool bwd = (d & 1) != 0;
-      int xn = x, yn = y, zn = z, tn = t;
-      bool neg = false;
-      if (!bwd) {
-        switch (mu) {
-          case 0: xn = (x + 1 == g.nx) ? 0 : x + 1; break;
-          case 1: yn = (y + 1 == g.ny) ? 0 : y + 1; break;
-          case 2: zn = (z + 1 == g.nz) ? 0 : z + 1; break;
-          default:
-            if (t + 1 == g.nt) { tn = 0; neg = g.tanti != 0; } else tn = t + 1;
-        }
-      } else {
-        switch (mu) {
-          case 0: xn = (x == 0) ? g.nx - 1 : x - 1; break;
-          case 1: yn = (y == 0) ? g.ny - 1 : y - 1; break;
-          case 2: zn = (z == 0) ? g.nz - 1 : z - 1; break;
-          default:
-            if (t == 0) { tn = g.nt - 1; neg = g.tanti != 0; } else tn = t - 1;
-        }
-      }
-      const int64_t nb = cb_index(g, xn, yn, zn, tn);
       cw psi[4][3];
-      T::load_spinor(in, vh, nb, psi);
-      // forward hops use (1 - gamma_mu), backward (1 + gamma_mu); dagger swaps
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float4 v = st[k * kHopThreads];
+        psi[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(v.z, v.w)};
+      }
       const float S = (bwd != DAG) ? 1.f : -1.f;
       cw h[2][3];
       switch (mu) {
@@ -258,19 +314,13 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_kernel(const HopParams P) 
         default: project_dw<3>(psi, h, S);
       }
       if (neg) T::negate_if(h, true);
-      // forward: U_mu(x) from this parity; backward: U_mu(x-mu)^dag from the
-      // other parity, loaded transposed with the imaginary parts negated
-      const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-      const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
       const float cs = bwd ? -1.f : 1.f;
       cw u[3][3];
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const float4 v = __ldcs(L + (int64_t)(a * sa + b * sb) * vh);
-          u[a][b] = cw{dw_make(v.x, v.y), dw_make(cs * v.z, cs * v.w)};
-        }
+      for (int k = 0; k < 9; ++k) {
+        const float4 v = st[(12 + k) * kHopThreads];
+        u[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(cs * v.z, cs * v.w)};
+      }
       cw r[2][3];
       matvec2<false>(u, h, r);
       switch (mu) {
@@ -308,7 +358,15 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_kernel(const HopParams P) 
 template <bool DAG, bool AXPY, bool NORM>
 static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
   note_launch();
-  hop_dw_kernel<DAG, AXPY, NORM><<<hop_blocks(P.g.vh), kHopThreads, 0, s>>>(P);
+  static bool configured = false;  // one attribute call per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(hop_dw_staged_kernel<DAG, AXPY, NORM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDwStagedSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  hop_dw_staged_kernel<DAG, AXPY, NORM><<<hop_blocks(P.g.vh), kHopThreads, kDwStagedSmem, s>>>(P);
   return cudaGetLastError();
 }
 

@@ -67,6 +67,9 @@ struct SolverScalars {
   int iters;
   int need_update;  // mixed: reliable update requested
   int max_iters;
+  int halt;         // loop kernels return at once while nonzero (done or need_update)
+  int reliable_updates;
+  int pad0, pad1;
 };
 
 // sum of partials[0..n) in a fixed order -> *out
@@ -88,12 +91,34 @@ cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverSc
 // y += x
 cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s);
 
+// ---- mixed precision (inner CG in FP32 or FP16+norm, even parity) ----------
+// x_s (FP32) += alpha p; r_s (FP32) -= alpha Ap; partials ||r_s||^2 (guarded by S->halt)
+cudaError_t launch_mixed_update(int hop_prec, float4 *xs, float4 *rs, const void *p, const void *Ap,
+                                int64_t vh, const SolverScalars *S, double *partials, cudaStream_t s);
+// p = r_s + beta p in the hop precision (guarded)
+cudaError_t launch_mixed_xpay(int hop_prec, void *p, const float4 *rs, int64_t vh,
+                              const SolverScalars *S, cudaStream_t s);
+// p = r_s converted to the hop precision
+cudaError_t launch_mixed_copy(int hop_prec, void *p, const float4 *rs, int64_t vh, cudaStream_t s);
+// r_s = FP32(r) for a double-word r of vh sites
+cudaError_t launch_dw_to_f32(float4 *rs, const float4 *r, int64_t vh, cudaStream_t s);
+// x += x_s (double-word += FP32), then x_s = 0
+cudaError_t launch_dw_add_f32(float4 *x, float4 *xs, int64_t vh, cudaStream_t s);
+// inner step: rr_new = sum; iters++; request a reliable update when
+// rr_new <= stop, rr_new < delta^2 rr_max or the iteration cap is reached;
+// otherwise beta = rr_new / rr
+cudaError_t launch_mixed_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s);
+// after x += x_s and r = rhs - A x: rr_true = sum; done when rr_true <= stop
+// (or cap reached); otherwise beta = rr_true / rr and the inner loop resumes
+cudaError_t launch_mixed_after_update(const double *partials, int n, SolverScalars *S,
+                                      cudaStream_t s);
+
 // CG scalar steps (single block): alpha = rr / sum(partials)
 cudaError_t launch_cg_alpha(const double *partials, int n, SolverScalars *S, cudaStream_t s);
 // rr_new = sum(partials); iters++; done when rr_new <= stop_rr; beta = rr_new/rr
 cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s);
 // S->rr = sum(partials) and reset the loop state (start or restart of CG)
 cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
-                            int max_iters, cudaStream_t s);
+                            int max_iters, double delta2, cudaStream_t s);
 
 }  // namespace jqcd

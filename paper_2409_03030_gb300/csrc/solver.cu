@@ -79,6 +79,19 @@ cudaError_t GaugeEntry::ensure_solver() {
   return e;
 }
 
+cudaError_t GaugeEntry::ensure_mixed(int hop_prec) {
+  const int k = hop_prec == PREC_F16N ? 1 : 0;
+  const size_t f32 = spinor_parity_bytes(PREC_F32, g.vh);
+  const size_t hb = spinor_parity_bytes(hop_prec, g.vh);
+  cudaError_t e = cudaSuccess;
+  if (!mx) e = alloc(&mx, f32);
+  if (e == cudaSuccess && !mr) e = alloc(&mr, f32);
+  void **vs[] = {&mp[k], &mAp[k], &mw[k], &mt[k]};
+  for (void **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc(v, hb);
+  return e;
+}
+
 const void *GaugeEntry::gauge_for(int prec) const {
   switch (prec) {
     case PREC_DW: return gauge_dw;
@@ -177,13 +190,36 @@ struct DwSystem {
 
 }  // namespace
 
-static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+static unsigned site_blocks_host(int64_t vh) {
+  return (unsigned)((vh + kBlasThreads - 1) / kBlasThreads);
+}
+
+// Bytes per output site of one hop in precision `prec` (+ the axpy operand).
+static double hop_site_bytes(int prec, bool axpy) {
+  switch (prec) {
+    case PREC_F32: return 576.0 + (axpy ? 96.0 : 0.0);
+    case PREC_F16N: return 488.0 + (axpy ? 52.0 : 0.0);
+    default: return 1536.0 + (axpy ? 192.0 : 0.0);
+  }
+}
+
+// Conjugate gradient on the normal equations.  mode JQCD_CG_DW: every vector
+// and operator in double-word precision.  Mixed modes: inner CG in FP32 or
+// FP16+norm on the even-odd system, reliable updates in double-word.
+static jqcd_status solve_cg(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
                             jqcd_solve_info *info, std::string *msg) {
   const bool eo = P.eo != 0;
+  const bool mixed = P.mode == JQCD_CG_MIXED_F32 || P.mode == JQCD_CG_MIXED_F16;
+  const int hp = P.mode == JQCD_CG_MIXED_F16 ? PREC_F16N : PREC_F32;
+  const int mk = hp == PREC_F16N ? 1 : 0;  // index of the hop-precision vectors
   DwSystem A{G, P.kappa, eo, s, (eo ? 12 : 24) * G.g.vh, (eo ? 1 : 2) * (int)hop_blocks(G.g.vh)};
   const int nblas = (int)blas_blocks(A.n);
   const double tol2 = P.tol * P.tol;
+  const double delta = P.delta > 0.0 ? P.delta : 0.01;
+  const int64_t vh = G.g.vh;
   SolverScalars *S = G.S;
+  double low_bytes = 0.0;
+  long long low_hops = 0;
 #define CKS(call)                                              \
   do {                                                         \
     cudaError_t e_ = (call);                                   \
@@ -192,12 +228,13 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
       return e_ == cudaErrorMemoryAllocation ? JQCD_ENOMEM : JQCD_ECUDA; \
     }                                                          \
   } while (0)
+  if (mixed) CKS(G.ensure_mixed(hp));
 
   CKS(cudaEventRecord(G.ev0, s));
   CKS(cudaMemsetAsync(S, 0, sizeof(SolverScalars), s));
   // ||b||^2 of D x = b
-  CKS(launch_dw_norm2(G.vb, 24 * G.g.vh, G.partials, s));
-  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * G.g.vh), &S->b2, s));
+  CKS(launch_dw_norm2(G.vb, 24 * vh, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * vh), &S->b2, s));
   // right-hand side of the CG system
   if (eo) {
     // bhat_e = b_e + kappa H_eo b_o  (into vw even)
@@ -223,12 +260,19 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
     CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
     CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
   } else {
-    CKS(launch_dw_zero(G.vsol, 24 * G.g.vh, s));
+    CKS(launch_dw_zero(G.vsol, 24 * vh, s));
     CKS(launch_dw_copy(G.vr, G.vrhs, A.n, s));
     CKS(launch_dw_norm2(G.vr, A.n, G.partials, s));
   }
-  CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, s));
-  CKS(launch_dw_copy(G.vp, G.vr, A.n, s));
+  CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, delta * delta, s));
+  auto start_direction = [&]() -> cudaError_t {
+    if (!mixed) return launch_dw_copy(G.vp, G.vr, A.n, s);
+    cudaError_t e = launch_dw_to_f32((float4 *)G.mr, G.vr, vh, s);
+    if (!e) e = cudaMemsetAsync(G.mx, 0, spinor_parity_bytes(PREC_F32, vh), s);
+    if (!e) e = launch_mixed_copy(hp, G.mp[mk], (const float4 *)G.mr, vh, s);
+    return e;
+  };
+  CKS(start_direction());
 
   int restarts = 0;
   jqcd_status st = JQCD_OK;
@@ -236,30 +280,56 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
     // main loop: poll the device scalars every kCheckEvery iterations
     for (;;) {
       for (int k = 0; k < kCheckEvery; ++k) {
-        CKS(A.apply(G.vp, G.vAp, G.partials, &S->done));
-        CKS(launch_cg_alpha(G.partials, A.n_hop_partials, S, s));
-        CKS(launch_dw_cg_update(G.vsol, G.vr, G.vp, G.vAp, A.n, S, G.partials, s));
-        CKS(launch_cg_beta(G.partials, nblas, S, s));
-        CKS(launch_dw_xpay(G.vp, G.vr, A.n, S, s));
+        if (!mixed) {
+          CKS(A.apply(G.vp, G.vAp, G.partials, &S->halt));
+          CKS(launch_cg_alpha(G.partials, A.n_hop_partials, S, s));
+          CKS(launch_dw_cg_update(G.vsol, G.vr, G.vp, G.vAp, A.n, S, G.partials, s));
+          CKS(launch_cg_beta(G.partials, nblas, S, s));
+          CKS(launch_dw_xpay(G.vp, G.vr, A.n, S, s));
+        } else {
+          CKS(apply_mdagm(G, hp, P.kappa, G.mp[mk], G.mAp[mk], G.mt[mk], G.mw[mk], G.partials,
+                          &S->halt, s));
+          CKS(launch_cg_alpha(G.partials, (int)hop_blocks(vh), S, s));
+          CKS(launch_mixed_update(hp, (float4 *)G.mx, (float4 *)G.mr, G.mp[mk], G.mAp[mk], vh, S,
+                                  G.partials, s));
+          CKS(launch_mixed_beta(G.partials, (int)site_blocks_host(vh), S, s));
+          CKS(launch_mixed_xpay(hp, G.mp[mk], (const float4 *)G.mr, vh, S, s));
+        }
       }
       CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
       CKS(cudaStreamSynchronize(s));
+      if (mixed && G.S_host->need_update && !G.S_host->done) {
+        // reliable update: x += x_s; r = rhs - A x in double-word; resume
+        CKS(launch_dw_add_f32(G.vsol, (float4 *)G.mx, vh, s));
+        CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
+        CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
+        CKS(launch_mixed_after_update(G.partials, nblas, S, s));
+        CKS(launch_dw_to_f32((float4 *)G.mr, G.vr, vh, s));
+        CKS(launch_mixed_xpay(hp, G.mp[mk], (const float4 *)G.mr, vh, S, s));
+        CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+        CKS(cudaStreamSynchronize(s));
+      }
       if (P.verbose >= 3)
-        fprintf(stderr, "jqcd cg: iter %d  |r|/|rhs| = %.3e\n", G.S_host->iters,
-                G.S_host->rhs2 > 0 ? std::sqrt(G.S_host->rr / G.S_host->rhs2) : 0.0);
-      if (G.S_host->done || G.S_host->iters >= P.maxiter) break;
+        fprintf(stderr, "jqcd cg: iter %d  |r|/|rhs| = %.3e  reliable updates %d\n",
+                G.S_host->iters,
+                G.S_host->rhs2 > 0 ? std::sqrt(G.S_host->rr / G.S_host->rhs2) : 0.0,
+                G.S_host->reliable_updates);
+      if (G.S_host->done) break;
+      if (!mixed && G.S_host->iters >= P.maxiter) break;
     }
     if (G.S_host->done == 2) {
       *msg = "CG breakdown (<p,Ap> <= 0 or not finite)";
       st = JQCD_EBREAKDOWN;
       break;
     }
-    // true residual of the CG system
-    CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
-    CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
-    CKS(launch_finalize_sum(G.partials, nblas, &S->true_rr, s));
-    CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
-    CKS(cudaStreamSynchronize(s));
+    if (!mixed) {
+      // true residual of the CG system (the mixed loop ends on one)
+      CKS(A.apply(G.vsol, G.vAp, nullptr, nullptr));
+      CKS(launch_dw_xmy_norm(G.vr, G.vrhs, G.vAp, A.n, G.partials, s));
+      CKS(launch_finalize_sum(G.partials, nblas, &S->true_rr, s));
+      CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+      CKS(cudaStreamSynchronize(s));
+    }
     const double rhs2 = G.S_host->rhs2;
     const bool ok = G.S_host->true_rr <= tol2 * rhs2;
     if (ok) break;
@@ -269,8 +339,8 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
       break;
     }
     ++restarts;  // restart from x with the recomputed residual
-    CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, s));
-    CKS(launch_dw_copy(G.vp, G.vr, A.n, s));
+    CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, delta * delta, s));
+    CKS(start_direction());
   }
   // even-odd reconstruction x_o = b_o + kappa H_oe x_e
   if (eo) {
@@ -282,8 +352,8 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
   CKS(cudaEventRecord(G.ev1, s));
   // ||b - D x||^2 (not part of the timed solve)
   CKS(apply_dirac_dw(G, P.kappa, false, G.vsol, G.vw, nullptr, nullptr, s));
-  CKS(launch_dw_xmy_norm(G.vAp, G.vb, G.vw, 24 * G.g.vh, G.partials, s));
-  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * G.g.vh), &S->full_rr, s));
+  CKS(launch_dw_xmy_norm(G.vAp, G.vb, G.vw, 24 * vh, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * vh), &S->full_rr, s));
   CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
   CKS(cudaStreamSynchronize(s));
   float ms = 0.f;
@@ -291,14 +361,20 @@ static jqcd_status solve_dw(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
   const SolverScalars &H = *G.S_host;
   info->iters = H.iters;
   info->restarts = restarts;
-  info->reliable_updates = 0;
+  info->reliable_updates = H.reliable_updates;
   info->true_rel_resid = H.rhs2 > 0 ? std::sqrt(H.true_rr / H.rhs2) : 0.0;
   info->full_rel_resid = H.b2 > 0 ? std::sqrt(H.full_rr / H.b2) : 0.0;
   info->gpu_seconds = ms * 1e-3;
-  // loop hops: four per completed iteration
-  for (int i = 0; i < H.iters; ++i) A.count(eo ? 2 : 0, eo ? 2 : 4);
-  info->hop_count = (double)A.hops;
-  info->hop_bytes = A.hop_bytes;
+  if (!mixed) {
+    // loop hops: four per completed iteration
+    for (int i = 0; i < H.iters; ++i) A.count(eo ? 2 : 0, eo ? 2 : 4);
+  } else {
+    low_hops = 4LL * H.iters;
+    low_bytes = (double)vh * H.iters * 2.0 * (hop_site_bytes(hp, false) + hop_site_bytes(hp, true));
+    // double-word applications of A in the reliable updates (counted by apply)
+  }
+  info->hop_count = (double)(A.hops + low_hops);
+  info->hop_bytes = A.hop_bytes + low_bytes;
   return st;
 #undef CKS
 }
@@ -310,7 +386,18 @@ jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream
     return JQCD_EINVAL;
   }
   switch (P.mode) {
-    case JQCD_CG_DW: return solve_dw(G, P, s, info, msg);
+    case JQCD_CG_DW: return solve_cg(G, P, s, info, msg);
+    case JQCD_CG_MIXED_F32:
+    case JQCD_CG_MIXED_F16:
+      if (!P.eo) {
+        *msg = "mixed-precision modes solve the even-odd system only (eo = 1)";
+        return JQCD_EINVAL;
+      }
+      if (!(P.delta >= 0.0 && P.delta < 1.0)) {
+        *msg = "delta must lie in [0, 1)";
+        return JQCD_EINVAL;
+      }
+      return solve_cg(G, P, s, info, msg);
     default:
       *msg = "solver mode not available";
       return JQCD_EINVAL;

@@ -225,3 +225,49 @@ def test_hop_full_size_sampled(jq):
     got_s = np.transpose(got[:, sites, :], (1, 0, 2))
     assert rel(got_s, want) <= 1e-12
     g.free()
+
+
+@pytest.mark.parametrize("mode", ["mixed_f32", "mixed_f16"])
+def test_mixed_cg_16x4(jq, mode):
+    """Mixed-precision CG (FP32 or FP16+norm inner, double-word reliable
+    updates) reaches the requested true residual of the even-odd system, and
+    agrees with the double-word solve within the conditioning bound."""
+    jqcd, ctx = jq
+    dims = (16, 16, 16, 16)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=2)
+    b = synth.gaussian_spinor(dims, seed=3)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.MODES[mode])
+    assert st == 0 and info["reliable_updates"] >= 1
+    res = system_residual(dims, U, b, x, 0.12, True)
+    assert res <= 1e-10 * (1 + 1e-6), res
+    assert abs(info["true_rel_resid"] - res) <= 1e-2 * 1e-10 + 1e-14
+    xd, info_d, st_d = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.CG_DW)
+    assert rel(x, xd) < 1e-7
+    g.free()
+
+
+def test_mixed_cg_config2_32x64(jq):
+    """32^3x64, exp(i 0.4 H) links, kappa 0.122: FP16+norm mixed CG to 1e-10.
+    Full size: the oracle recomputes the CG system's residual from the GPU
+    solution (one Mhat^dag Mhat application in FP64)."""
+    jqcd, ctx = jq
+    dims = (32, 32, 32, 64)
+    U = synth.gauge(dims, "expi", eps=0.4, seed=4)
+    b = synth.gaussian_spinor(dims, seed=5)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.122, tol=1e-10, eo=True, mode=jqcd.CG_MIXED_F16)
+    assert st == 0
+    res = system_residual(dims, U, b, x, 0.122, True)
+    assert res <= 1e-10 * (1 + 1e-6), res
+    g.free()
+
+
+def test_mixed_rejects_whole_lattice(jq):
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    g = ctx.gauge_upload(dims, synth.gauge(dims, "haar", seed=1))
+    x, info, st = g.cg_solve(synth.gaussian_spinor(dims, seed=1), 0.1, eo=False,
+                             mode=jqcd.CG_MIXED_F32, check=False)
+    assert st == jqcd.EINVAL
+    g.free()
