@@ -39,7 +39,8 @@ TOL = 1e-10
 METRIC = "Dslash GB/s vs HBM peak; CG s to 1e-10 mixed vs FP64; serve p50/p99"
 HOP_BYTES = {"dw": 1536, "f64": 1536, "f32": 576, "f16n": 488}  # per output site
 AXPY_BYTES = {"dw": 192, "f64": 192, "f32": 96, "f16n": 52}
-HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "fields.cuh", "dw.cuh", "lattice.cuh", "reduce.cuh"]
+HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "hop_dw.cuh", "fields.cuh", "dw.cuh", "lattice.cuh",
+                      "reduce.cuh"]
 
 
 def parse():

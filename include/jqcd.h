@@ -235,6 +235,20 @@ JQCD_API jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const j
                               const void *b_even, const void *b_odd, void *x_even, void *x_odd,
                               jqcd_solve_info *info, void *stream);
 
+/* Solve n systems D_i x_i = b_i together (batched mixed-precision CG):
+ * every solve advances one iteration per pass of persistent kernels that
+ * walk all active solves at once; solves on the same gauge field share each
+ * link load (multi right-hand-side hops); one iteration is captured in a
+ * CUDA graph and replayed; sites per tile and grid size are autotuned per
+ * batch shape.  Each solve has its own kappa, tol and maxiter (params[i]);
+ * all must use the same mixed mode (JQCD_CG_MIXED_F32 or _F16) and eo = 1.
+ * b[i], x[i]: host canonical spinors of solve i's lattice (b copied, x
+ * written before return).  infos: NULL or n entries.  Returns JQCD_OK when
+ * every solve converged, else the first failing status (all infos filled). */
+JQCD_API jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_ids,
+                                         const jqcd_solve_params *params, const double *const *b,
+                                         double *const *x, jqcd_solve_info *infos);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,7 +11,9 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <vector>
 
+#include "batch_engine.h"
 #include "jqcd.h"
 #include "kernels.h"
 #include "solver.h"
@@ -21,7 +23,7 @@ using namespace jqcd;
 namespace {
 std::atomic<uint64_t> g_launches{0};
 }
-void jqcd::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void jqcd::note_launch(int64_t n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 struct jqcd_ctx {
   int device = 0;
@@ -31,6 +33,7 @@ struct jqcd_ctx {
   std::string err;
   uint64_t next_id = 1;
   std::map<uint64_t, std::unique_ptr<GaugeEntry>> gauges;
+  std::unique_ptr<BatchEngine> engine[2];  // batched solves: FP32 and FP16 inner precision
 };
 
 namespace {
@@ -126,6 +129,8 @@ jqcd_status jqcd_finalize(jqcd_ctx *ctx) {
   if (!ctx) return JQCD_EINVAL;
   cudaSetDevice(ctx->device);
   if (!ctx->poisoned) cudaStreamSynchronize(ctx->stream);
+  ctx->engine[0].reset();
+  ctx->engine[1].reset();
   ctx->gauges.clear();
   if (ctx->stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
@@ -337,6 +342,54 @@ jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve
   inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (info) *info = inf;
   if (st != JQCD_OK) return fail(ctx, st, "cg_solve_dev: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+
+jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_ids,
+                                const jqcd_solve_params *params, const double *const *b,
+                                double *const *x, jqcd_solve_info *infos) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  if (n < 1 || !gauge_ids || !params || !b || !x) return fail(ctx, JQCD_EINVAL, "cg_solve_batch: bad argument");
+  const int32_t mode = params[0].mode;
+  if (mode != JQCD_CG_MIXED_F32 && mode != JQCD_CG_MIXED_F16)
+    return fail(ctx, JQCD_EINVAL, "cg_solve_batch: mode must be JQCD_CG_MIXED_F32 or JQCD_CG_MIXED_F16");
+  std::vector<GaugeEntry *> G(n);
+  for (int i = 0; i < n; ++i) {
+    const jqcd_solve_params &P = params[i];
+    if (P.mode != mode || !P.eo || !(P.tol > 0.0) || P.maxiter < 1 || !(P.kappa >= 0.0) ||
+        !(P.delta >= 0.0 && P.delta < 1.0) || !b[i] || !x[i])
+      return fail(ctx, JQCD_EINVAL, "cg_solve_batch: solve %d: bad parameters (one mixed mode for "
+                  "all, eo = 1, tol > 0, maxiter >= 1)", i);
+    G[i] = find_gauge(ctx, gauge_ids[i]);
+    if (!G[i]) return fail(ctx, JQCD_ENOTFOUND, "cg_solve_batch: solve %d: unknown gauge id", i);
+    if (G[i]->g.vh >= ((int64_t)1 << 31)) return fail(ctx, JQCD_EINVAL, "lattice too large for batching");
+  }
+  const int hp = mode == JQCD_CG_MIXED_F16 ? PREC_F16N : PREC_F32;
+  std::unique_ptr<BatchEngine> &E = ctx->engine[hp == PREC_F16N ? 1 : 0];
+  if (!E || E->max_slots() < n) {
+    E.reset(new BatchEngine(hp, n, ctx->stream, ctx->sm_count));
+    CK(E->init(), "batch engine init");
+  }
+  for (int i = 0; i < n; ++i) CK(E->admit(i, G[i], params[i], b[i]), "batch admit");
+  CK(E->autotune(), "batch autotune");
+  int left = n;
+  std::vector<int> done;
+  jqcd_status worst = JQCD_OK;
+  while (left > 0) {
+    CK(E->run(8), "batch iterations");
+    done.clear();
+    CK(E->poll(&done), "batch poll");
+    for (int i : done) {
+      jqcd_solve_info inf;
+      CK(E->collect(i, x[i], &inf), "batch collect");
+      if (infos) infos[i] = inf;
+      if (inf.status != JQCD_OK && worst == JQCD_OK) worst = inf.status;
+      --left;
+    }
+  }
+  if (worst != JQCD_OK) return fail(ctx, worst, "cg_solve_batch: a solve did not converge");
   return JQCD_OK;
 }
 

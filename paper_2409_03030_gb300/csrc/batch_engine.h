@@ -1,0 +1,101 @@
+// Host side of the batched mixed-precision CG engine (kernels in batch.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batch.h"
+#include "jqcd.h"
+#include "solver.h"
+
+namespace jqcd {
+
+// Device buffers of one slot, sized for `vh_cap` sites per parity.
+struct SlotBuffers {
+  int64_t vh_cap = 0;
+  int hp = -1;
+  void *p = nullptr, *Ap = nullptr, *w = nullptr, *t = nullptr;
+  float4 *xs = nullptr, *rs = nullptr;
+  float4 *b = nullptr, *x = nullptr, *r = nullptr, *rhs = nullptr, *wdw = nullptr, *Adw = nullptr,
+         *tdw = nullptr;
+  double *part = nullptr;
+  size_t bytes = 0;
+  std::vector<void *> allocs;
+  ~SlotBuffers();
+  void release();
+  cudaError_t ensure(int64_t vh, int hp);
+  static size_t footprint(int64_t vh, int hp);
+  static int64_t n_part(int64_t vh);
+};
+
+struct SlotHost {
+  int state = 0;  // 0 free, 1 iterating, 2 converged or stopped, waiting for collect
+  GaugeEntry *G = nullptr;
+  jqcd_solve_params P{};
+  SlotBuffers buf;
+  double t_admit = 0.0, t_done = 0.0;  // seconds on the engine's host clock
+};
+
+class BatchEngine {
+ public:
+  BatchEngine(int hp, int max_slots, cudaStream_t s, int sm_count);
+  ~BatchEngine();
+  cudaError_t init();
+  int hop_prec() const { return hp_; }
+  int max_slots() const { return (int)slots_.size(); }
+  int free_slot() const;
+  int running() const;
+  // Prepare slot `slot` for D x = b (b: host canonical spinor).  Even-odd
+  // source, normal-equation right-hand side, start residual; the slot joins
+  // the next iteration.
+  cudaError_t admit(int slot, GaugeEntry *G, const jqcd_solve_params &P, const double *b_host);
+  // Run `iters` iterations of every running slot (graph replays).
+  cudaError_t run(int iters);
+  // Copy the device scalars; slots that finished move to state 2.
+  cudaError_t poll(std::vector<int> *finished);
+  // Reconstruct x_o, compute ||b - D x||, copy x to the host, fill info and
+  // free the slot.
+  cudaError_t collect(int slot, double *x_host, jqcd_solve_info *info);
+  // Choose sites per tile and grid size for the current active set.
+  cudaError_t autotune();
+  const SolverScalars &scalars(int slot) const { return h_S_[slot]; }
+  double now() const;
+  int tile_sites() const { return tile_sites_; }
+  int grid() const { return grid_; }
+  cudaStream_t stream() const { return s_; }
+
+ private:
+  cudaError_t rebuild();
+  cudaError_t ensure_canon(int64_t vh);
+  cudaError_t ensure_graph();
+  std::string tune_key() const;
+
+  int hp_;
+  int sm_count_;
+  cudaStream_t s_;
+  std::vector<SlotHost> slots_;
+  std::vector<SlotDev> h_slots_;
+  SlotDev *d_slots_ = nullptr;
+  SolverScalars *d_S_ = nullptr;
+  SolverScalars *h_S_ = nullptr;  // pinned
+  GroupDev *d_groups_ = nullptr;
+  int2 *d_tiles_ = nullptr;
+  int *d_ntiles_ = nullptr;
+  int *d_any_update_ = nullptr;
+  int max_groups_ = 0;
+  int64_t max_tiles_ = 0;
+  double *canon_ = nullptr;
+  int64_t canon_vh_ = 0;
+  int tile_sites_ = 128;
+  int grid_ = 0;
+  bool dirty_ = true;
+  cudaGraphExec_t graph_ = nullptr;
+  int graph_ts_ = 0, graph_grid_ = 0;
+  int64_t graph_kernels_ = 0;
+  std::map<std::string, std::pair<int, int>> tuned_;
+  double t0_ = 0.0;
+};
+
+}  // namespace jqcd

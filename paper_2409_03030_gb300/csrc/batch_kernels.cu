@@ -1,0 +1,498 @@
+// Kernels of the batched mixed-precision CG (see batch.h).
+//
+// Tile kernels are persistent: block b handles tiles b, b + gridDim.x, ...
+// of the device tile list; a tile is tile_sites consecutive sites (one per
+// thread) of one group of right-hand sides sharing a gauge field.  Per-slot
+// kernels run one block per slot.  Every skip condition below depends only on
+// values all threads of a block read alike, so block reductions stay
+// convergent.
+#include <cuda_runtime.h>
+
+#include "batch.h"
+#include "hop_dw.cuh"
+#include "reduce.cuh"
+
+namespace jqcd {
+
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
+  return A.slots[si].active && !A.S[si].halt;
+}
+
+// One of the eight hops of the low-precision operator for one site, the link
+// (rows 0 and 1) taken from the tile's shared-memory stage.
+template <int PREC, int MU, bool BWD, bool DAG>
+__device__ __forceinline__ void lp_dir(const void *in, int64_t vh, int32_t nb, bool neg,
+                                       const float4 *lsm, int tid, int bd, cf (&acc)[4][3]) {
+  constexpr int S = (BWD != DAG) ? 1 : -1;
+  constexpr int D = 2 * MU + (BWD ? 1 : 0);
+  cf psi[4][3], h[2][3], r[2][3], u[3][3];
+  PT<PREC>::load_spinor(in, vh, nb, psi);
+  project<MU, S>(psi, h);
+  PT<PREC>::negate_if(h, neg);
+  PT<PREC>::link_from_chunks(lsm[(D * 3 + 0) * bd + tid], lsm[(D * 3 + 1) * bd + tid],
+                             lsm[(D * 3 + 2) * bd + tid], u);
+  matvec2<BWD>(u, h, r);
+  reconstruct<MU, S>(r, acc);
+}
+
+// STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t (norm);  2: t = H^dag_oe w;
+// STAGE 3: Ap = w - kappa^2 H^dag_eo t.  Links staged once per tile.
+template <int PREC, int STAGE>
+__global__ void __launch_bounds__(256) batch_lp_hop_kernel(const BatchArgs A) {
+  extern __shared__ float4 lsm[];  // [8 hops][3 chunks][blockDim.x]
+  constexpr bool DAG = STAGE >= 2;
+  constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
+  constexpr bool AXPY = STAGE == 1 || STAGE == 3;
+  constexpr bool NORM = STAGE == 1;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T = A.tiles[ti];
+    const GroupDev *G = A.groups + T.x;
+    const int ns = G->nslots;
+    bool any = false;
+    for (int s = 0; s < ns; ++s) any |= slot_running(A, G->slot[s]);
+    if (!any) continue;
+    const Geom g = G->g;
+    const int64_t idx = (int64_t)T.y * bd + tid;
+    const bool on = idx < g.vh;
+    int32_t nb[8];
+    unsigned negm = 0;
+    if (on) {
+      int x, y, z, t;
+      cb_coords(g, idx, OUTP, x, y, z, t);
+#pragma unroll
+      for (int d = 0; d < 8; ++d) {
+        bool ng;
+        nb[d] = (int32_t)hop_neighbour(g, x, y, z, t, d, ng);
+        negm |= (ng ? 1u : 0u) << d;
+        const int mu = d >> 1;
+        const bool bwd = (d & 1) != 0;
+        const float4 *L = G->gauge_f32 + (size_t)(((bwd ? 1 - OUTP : OUTP) * 4 + mu) * 3) * g.vh +
+                          (bwd ? (int64_t)nb[d] : idx);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cp_async16(lsm + (d * 3 + j) * bd + tid, L + j * g.vh, false);
+      }
+      cp_async_commit();
+      cp_async_wait0();  // this thread's links have landed (no other thread reads them)
+    }
+    for (int s = 0; s < ns; ++s) {
+      const int si = G->slot[s];
+      if (!slot_running(A, si)) continue;
+      const SlotDev &Sl = A.slots[si];
+      const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
+      const void *xv = STAGE == 1 ? Sl.p : Sl.w;
+      void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
+      float n2 = 0.f;
+      if (on) {
+        cf acc[4][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) acc[a][c] = cf{0.f, 0.f};
+        const int64_t vh = g.vh;
+        lp_dir<PREC, 0, false, DAG>(in, vh, nb[0], negm & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 0, true, DAG>(in, vh, nb[1], (negm >> 1) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 1, false, DAG>(in, vh, nb[2], (negm >> 2) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 1, true, DAG>(in, vh, nb[3], (negm >> 3) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 2, false, DAG>(in, vh, nb[4], (negm >> 4) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 2, true, DAG>(in, vh, nb[5], (negm >> 5) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 3, false, DAG>(in, vh, nb[6], (negm >> 6) & 1u, lsm, tid, bd, acc);
+        lp_dir<PREC, 3, true, DAG>(in, vh, nb[7], (negm >> 7) & 1u, lsm, tid, bd, acc);
+        cf o[4][3];
+        if (AXPY) {
+          cf xs[4][3];
+          PT<PREC>::load_spinor(xv, vh, idx, xs);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[a][c] = PT<PREC>::axpby(1.f, xs[a][c], Sl.k2, acc[a][c]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[a][c] = acc[a][c];
+        }
+        PT<PREC>::store_spinor(out, vh, idx, o);
+        if (NORM) {
+#pragma unroll
+          for (int k = 0; k < 12; ++k)
+            n2 = fmaf(o[k / 3][k % 3].re, o[k / 3][k % 3].re, fmaf(o[k / 3][k % 3].im, o[k / 3][k % 3].im, n2));
+        }
+      }
+      if (NORM) {
+        const double sum = block_sum_f(n2);
+        if (tid == 0) Sl.part[T.y] = sum;
+      }
+    }
+  }
+}
+
+// x_s += alpha p; r_s -= alpha Ap; partial ||r_s||^2
+template <int PREC>
+__global__ void __launch_bounds__(256) batch_update_kernel(const BatchArgs A) {
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T = A.tiles[ti];
+    const GroupDev *G = A.groups + T.x;
+    const int64_t vh = G->g.vh;
+    const int64_t i = (int64_t)T.y * bd + tid;
+    for (int s = 0; s < G->nslots; ++s) {
+      const int si = G->slot[s];
+      if (!slot_running(A, si)) continue;
+      const SlotDev &Sl = A.slots[si];
+      const float a = A.S[si].alpha_f;
+      float n2 = 0.f;
+      if (i < vh) {
+        cf pv[4][3], av[4][3], xv[4][3], rv[4][3];
+        PT<PREC>::load_spinor(Sl.p, vh, i, pv);
+        PT<PREC>::load_spinor(Sl.Ap, vh, i, av);
+        PT<PREC_F32>::load_spinor(Sl.xs, vh, i, xv);
+        PT<PREC_F32>::load_spinor(Sl.rs, vh, i, rv);
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          cf &x = xv[k / 3][k % 3], &r = rv[k / 3][k % 3];
+          const cf pp = pv[k / 3][k % 3], aa = av[k / 3][k % 3];
+          x.re = fmaf(a, pp.re, x.re);
+          x.im = fmaf(a, pp.im, x.im);
+          r.re = fmaf(-a, aa.re, r.re);
+          r.im = fmaf(-a, aa.im, r.im);
+          n2 = fmaf(r.re, r.re, fmaf(r.im, r.im, n2));
+        }
+        PT<PREC_F32>::store_spinor(Sl.xs, vh, i, xv);
+        PT<PREC_F32>::store_spinor(Sl.rs, vh, i, rv);
+      }
+      const double sum = block_sum_f(n2);
+      if (tid == 0) Sl.part[T.y] = sum;
+    }
+  }
+}
+
+// p = r_s + beta p for running slots (CONVERT = false) or, after a reliable
+// update, r_s = FP32(r) and then p = r_s + beta p (CONVERT = true).
+template <int PREC, bool CONVERT>
+__global__ void __launch_bounds__(256) batch_xpay_kernel(const BatchArgs A) {
+  if (CONVERT && *A.any_update == 0) return;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T = A.tiles[ti];
+    const GroupDev *G = A.groups + T.x;
+    const int64_t vh = G->g.vh;
+    const int64_t i = (int64_t)T.y * bd + tid;
+    if (i >= vh) continue;
+    for (int s = 0; s < G->nslots; ++s) {
+      const int si = G->slot[s];
+      const SlotDev &Sl = A.slots[si];
+      if (CONVERT) {
+        if (!Sl.active || A.S[si].need_update != 2) continue;
+      } else if (!slot_running(A, si)) {
+        continue;
+      }
+      const float b = A.S[si].beta_f;
+      cf rv[4][3], pv[4][3];
+      if (CONVERT) {
+        const float4 *r = Sl.r + i;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const float4 v = r[k * vh];
+          rv[k / 3][k % 3] = cf{v.x, v.z};  // normalised pairs: hi = nearest float
+        }
+        PT<PREC_F32>::store_spinor(Sl.rs, vh, i, rv);
+      } else {
+        PT<PREC_F32>::load_spinor(Sl.rs, vh, i, rv);
+      }
+      PT<PREC>::load_spinor(Sl.p, vh, i, pv);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        cf &q = pv[k / 3][k % 3];
+        q.re = fmaf(b, q.re, rv[k / 3][k % 3].re);
+        q.im = fmaf(b, q.im, rv[k / 3][k % 3].im);
+      }
+      PT<PREC>::store_spinor(Sl.p, vh, i, pv);
+    }
+  }
+}
+
+// ---- reliable updates (slots with need_update == 1) ---------------------------
+
+// x_e += x_s; x_s = 0
+__global__ void __launch_bounds__(256) batch_dw_add_kernel(const BatchArgs A) {
+  if (*A.any_update == 0) return;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T = A.tiles[ti];
+    const GroupDev *G = A.groups + T.x;
+    const int64_t vh = G->g.vh;
+    const int64_t i = (int64_t)T.y * bd + tid;
+    if (i >= vh) continue;
+    for (int s = 0; s < G->nslots; ++s) {
+      const int si = G->slot[s];
+      const SlotDev &Sl = A.slots[si];
+      if (!Sl.active || A.S[si].need_update != 1) continue;
+      cf xv[4][3];
+      PT<PREC_F32>::load_spinor(Sl.xs, vh, i, xv);
+      float4 *x = Sl.x + i;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float4 v = x[k * vh];
+        const dw re = dw_add(dw_make(v.x, v.y), dw_make(xv[k / 3][k % 3].re, 0.f));
+        const dw im = dw_add(dw_make(v.z, v.w), dw_make(xv[k / 3][k % 3].im, 0.f));
+        x[k * vh] = make_float4(re.h, re.l, im.h, im.l);
+      }
+      float4 *xs = Sl.xs + i;
+#pragma unroll
+      for (int j = 0; j < 6; ++j) xs[j * vh] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+}
+
+// Double-word Mhat^dag Mhat x in four stages (as the low-precision stages, on
+// x, tdw, wdw, Adw).
+template <int STAGE>
+__global__ void __launch_bounds__(256) batch_dw_hop_kernel(const BatchArgs A) {
+  if (*A.any_update == 0) return;
+  typedef PT<PREC_DW> T;
+  constexpr bool DAG = STAGE >= 2;
+  constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
+  constexpr bool AXPY = STAGE == 1 || STAGE == 3;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T2 = A.tiles[ti];
+    const GroupDev *G = A.groups + T2.x;
+    const Geom g = G->g;
+    const int64_t i = (int64_t)T2.y * bd + tid;
+    if (i >= g.vh) continue;
+    for (int s = 0; s < G->nslots; ++s) {
+      const int si = G->slot[s];
+      const SlotDev &Sl = A.slots[si];
+      if (!Sl.active || A.S[si].need_update != 1) continue;
+      const float4 *in = STAGE == 0 ? Sl.x : (STAGE == 2 ? Sl.wdw : Sl.tdw);
+      const float4 *xv = STAGE == 1 ? Sl.x : Sl.wdw;
+      float4 *out = STAGE == 0 || STAGE == 2 ? Sl.tdw : (STAGE == 1 ? Sl.wdw : Sl.Adw);
+      cw acc[4][3];
+      dw_hop_site<DAG>(in, G->gauge_dw, g, OUTP, i, acc);
+      cw o[4][3];
+      const dw k2 = dw_make(Sl.k2_dw.x, Sl.k2_dw.y);
+      if (AXPY) {
+        cw xs[4][3];
+        T::load_spinor(xv, g.vh, i, xs);
+        const dw one = dw_make(1.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) o[a][c] = T::axpby(one, xs[a][c], k2, acc[a][c]);
+      } else {
+        const dw one = dw_make(1.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) o[a][c] = T::scale(one, acc[a][c]);
+      }
+      T::store_spinor(out, g.vh, i, o);
+    }
+  }
+}
+
+// r = rhs - Adw, partial ||r||^2
+__global__ void __launch_bounds__(256) batch_dw_resid_kernel(const BatchArgs A) {
+  if (*A.any_update == 0) return;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int nt = *A.ntiles;
+  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
+    const int2 T = A.tiles[ti];
+    const GroupDev *G = A.groups + T.x;
+    const int64_t vh = G->g.vh;
+    const int64_t i = (int64_t)T.y * bd + tid;
+    for (int s = 0; s < G->nslots; ++s) {
+      const int si = G->slot[s];
+      const SlotDev &Sl = A.slots[si];
+      if (!Sl.active || A.S[si].need_update != 1) continue;
+      dwacc n2{0.f, 0.f};
+      if (i < vh) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) {
+          const float4 bv = Sl.rhs[k * vh + i], yv = Sl.Adw[k * vh + i];
+          const dw re = dw_add(dw_make(bv.x, bv.y), dw_make(-yv.x, -yv.y));
+          const dw im = dw_add(dw_make(bv.z, bv.w), dw_make(-yv.z, -yv.w));
+          Sl.r[k * vh + i] = make_float4(re.h, re.l, im.h, im.l);
+          acc_sq(n2, re);
+          acc_sq(n2, im);
+        }
+      }
+      const double sum = block_sum_dw(n2);
+      if (tid == 0) Sl.part[T.y] = sum;
+    }
+  }
+}
+
+// ---- per-slot scalar steps (one block per slot) --------------------------------
+__device__ __forceinline__ double slot_sum(const SlotDev &Sl) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < Sl.nblocks; i += blockDim.x) v += Sl.part[i];
+  return block_sum_d(v);
+}
+
+__global__ void batch_alpha_kernel(const BatchArgs A) {
+  const int si = blockIdx.x;
+  if (si >= A.nslots || !slot_running(A, si)) return;
+  const double pAp = slot_sum(A.slots[si]);
+  if (threadIdx.x == 0) {
+    SolverScalars *S = A.S + si;
+    S->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) { S->done = 2; S->halt = 1; return; }
+    const double a = S->rr / pAp;
+    S->alpha = a;
+    S->alpha_f = (float)a;
+  }
+}
+
+__global__ void batch_beta_kernel(const BatchArgs A) {
+  const int si = blockIdx.x;
+  if (si >= A.nslots || !slot_running(A, si)) return;
+  const double rr_new = slot_sum(A.slots[si]);
+  if (threadIdx.x == 0) {
+    SolverScalars *S = A.S + si;
+    S->rr_new = rr_new;
+    S->iters += 1;
+    if (!isfinite(rr_new)) { S->done = 2; S->halt = 1; return; }
+    if (rr_new <= S->stop_rr || rr_new < S->delta2 * S->rr_max || S->iters >= S->max_iters) {
+      S->need_update = 1;
+      S->halt = 1;
+      *A.any_update = 1;
+      return;
+    }
+    const double b = rr_new / S->rr;
+    S->beta = b;
+    S->beta_f = (float)b;
+    S->rr = rr_new;
+    if (rr_new > S->rr_max) S->rr_max = rr_new;
+  }
+}
+
+__global__ void batch_after_update_kernel(const BatchArgs A) {
+  if (*A.any_update == 0) return;
+  const int si = blockIdx.x;
+  if (si >= A.nslots || !A.slots[si].active || A.S[si].need_update != 1) return;
+  const double rr_true = slot_sum(A.slots[si]);
+  if (threadIdx.x == 0) {
+    SolverScalars *S = A.S + si;
+    S->reliable_updates += 1;
+    S->true_rr = rr_true;
+    S->need_update = 0;
+    if (!isfinite(rr_true)) { S->done = 2; return; }
+    if (rr_true <= S->stop_rr) { S->rr = rr_true; S->done = 1; return; }
+    if (S->iters >= S->max_iters) { S->rr = rr_true; S->done = 3; return; }
+    const double b = rr_true / S->rr;
+    S->beta = b;
+    S->beta_f = (float)b;
+    S->rr = rr_true;
+    S->rr_max = rr_true;
+    S->need_update = 2;  // convert the residual, then resume
+  }
+}
+
+__global__ void batch_resume_kernel(const BatchArgs A) {
+  const int si = blockIdx.x;
+  if (si < A.nslots && threadIdx.x == 0 && A.slots[si].active && A.S[si].need_update == 2) {
+    A.S[si].need_update = 0;
+    A.S[si].halt = 0;
+  }
+  if (si == 0 && threadIdx.x == 0) *A.any_update = 0;
+}
+
+// ---- launchers -------------------------------------------------------------------
+template <int PREC>
+static cudaError_t configure_prec() {
+  const int mx = 24 * 256 * 16;
+  cudaError_t e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 0>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return e;
+}
+
+cudaError_t batch_configure() {
+  cudaError_t e = configure_prec<PREC_F32>();
+  return e ? e : configure_prec<PREC_F16N>();
+}
+
+template <int PREC>
+static cudaError_t lp_apply(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)24 * ts * 16;
+  note_launch();
+  batch_lp_hop_kernel<PREC, 0><<<grid, ts, smem, s>>>(A);
+  note_launch();
+  batch_lp_hop_kernel<PREC, 1><<<grid, ts, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t lp_apply_dag(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
+  const size_t smem = (size_t)24 * ts * 16;
+  note_launch();
+  batch_lp_hop_kernel<PREC, 2><<<grid, ts, smem, s>>>(A);
+  note_launch();
+  batch_lp_hop_kernel<PREC, 3><<<grid, ts, smem, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t iteration(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
+  cudaError_t e = lp_apply<PREC>(A, ts, grid, s);
+  if (e) return e;
+  note_launch();
+  batch_alpha_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
+  if ((e = lp_apply_dag<PREC>(A, ts, grid, s))) return e;
+  note_launch();
+  batch_update_kernel<PREC><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_beta_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
+  note_launch();
+  batch_xpay_kernel<PREC, false><<<grid, ts, 0, s>>>(A);
+  // reliable updates of the slots that asked for one (no-ops otherwise)
+  note_launch();
+  batch_dw_add_kernel<<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_dw_hop_kernel<0><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_dw_hop_kernel<1><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_dw_hop_kernel<2><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_dw_hop_kernel<3><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_dw_resid_kernel<<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_after_update_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
+  note_launch();
+  batch_xpay_kernel<PREC, true><<<grid, ts, 0, s>>>(A);
+  note_launch();
+  batch_resume_kernel<<<A.nslots, 32, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_iteration(const BatchArgs &A, int hp, int tile_sites, int grid,
+                                   cudaStream_t s) {
+  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1) return cudaErrorInvalidValue;
+  return hp == PREC_F16N ? iteration<PREC_F16N>(A, tile_sites, grid, s)
+                         : iteration<PREC_F32>(A, tile_sites, grid, s);
+}
+
+cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int tile_sites, int grid,
+                                  cudaStream_t s) {
+  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1) return cudaErrorInvalidValue;
+  cudaError_t e = hp == PREC_F16N ? lp_apply<PREC_F16N>(A, tile_sites, grid, s)
+                                  : lp_apply<PREC_F32>(A, tile_sites, grid, s);
+  if (e) return e;
+  return hp == PREC_F16N ? lp_apply_dag<PREC_F16N>(A, tile_sites, grid, s)
+                         : lp_apply_dag<PREC_F32>(A, tile_sites, grid, s);
+}
+
+}  // namespace jqcd

@@ -130,7 +130,18 @@ struct PT_F32Links {
     u[0][0] = cf{c0.x, c0.y}; u[0][1] = cf{c0.z, c0.w};
     u[0][2] = cf{c1.x, c1.y}; u[1][0] = cf{c1.z, c1.w};
     u[1][1] = cf{c2.x, c2.y}; u[1][2] = cf{c2.z, c2.w};
-    // row 2 = conj(row0 x row1)
+    reconstruct_row2(u);
+  }
+  // rows 0 and 1 from three 16-byte chunks (U00,U01) (U02,U10) (U11,U12)
+  __device__ static __forceinline__ void link_from_chunks(float4 c0, float4 c1, float4 c2,
+                                                          cf (&u)[3][3]) {
+    u[0][0] = cf{c0.x, c0.y}; u[0][1] = cf{c0.z, c0.w};
+    u[0][2] = cf{c1.x, c1.y}; u[1][0] = cf{c1.z, c1.w};
+    u[1][1] = cf{c2.x, c2.y}; u[1][2] = cf{c2.z, c2.w};
+    reconstruct_row2(u);
+  }
+  // row 2 = conj(row0 x row1), exact for SU(3)
+  __device__ static __forceinline__ void reconstruct_row2(cf (&u)[3][3]) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int c1i = (c + 1) % 3, c2i = (c + 2) % 3;
@@ -210,7 +221,11 @@ template <> struct PT<PREC_F16N> : PT_F32Links {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(s[k / 3][k % 3].re), fabsf(s[k / 3][k % 3].im)));
-    const float inv = m > 0.f ? 1.f / m : 0.f;
+    // A site whose largest component is below 1e-30 is stored as exact zeros:
+    // 1/m would overflow for denormal m (point sources reach such values at
+    // the edge of their support).  NaN is kept so breakdowns stay visible.
+    if (m < 1e-30f) m = 0.f;
+    const float inv = m > 0.f ? 1.f / m : (m == 0.f ? 0.f : m);
     uint4 *p = reinterpret_cast<uint4 *>(base) + i;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {

@@ -7,8 +7,9 @@
 
 namespace jqcd {
 
-// Process-wide count of kernel launches issued by the library.
-void note_launch();
+// Process-wide count of kernel launches issued by the library (n may be
+// negative to take back launches recorded into a graph that is replayed).
+void note_launch(int64_t n = 1);
 
 constexpr int kHopThreads = 128;
 inline unsigned hop_blocks(int64_t vh) { return (unsigned)((vh + kHopThreads - 1) / kHopThreads); }

@@ -79,6 +79,9 @@ _SIGNATURES = {
                                _vp, _vp, _vp, _vp]),
     "jqcd_cg_solve": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _dp, _dp,
                             ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_cg_solve_batch": (_st, [_vp, ctypes.c_int32, ctypes.POINTER(_u64),
+                                  ctypes.POINTER(jqcd_solve_params), ctypes.POINTER(_dp),
+                                  ctypes.POINTER(_dp), ctypes.POINTER(jqcd_solve_info)]),
     "jqcd_cg_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(jqcd_solve_info), _vp]),
 }
@@ -168,6 +171,26 @@ class Context:
         if st not in (OK, PENDING):
             raise JqcdError(st, f"{what}: {jqcd_last_error(self.h).decode()}")
         return st
+
+    def cg_solve_batch(self, gauges, bs, kappas, tols, mode=CG_MIXED_F16, maxiter=20000,
+                       delta=0.0, check=True):
+        """jqcd_cg_solve_batch: solve D_i x_i = b_i for all i together.
+        gauges: list of Gauge; bs: host spinors; kappas, tols: per solve.
+        Returns (list of x, list of info dicts, status)."""
+        n = len(bs)
+        bs = [np.ascontiguousarray(b, dtype=np.complex128) for b in bs]
+        xs = [np.zeros_like(b) for b in bs]
+        ids = (ctypes.c_uint64 * n)(*[g.id for g in gauges])
+        params = (jqcd_solve_params * n)(*[
+            Gauge.params(kappas[i], tols[i], maxiter, True, mode, 0, delta, False)
+            for i in range(n)])
+        bp = (_dp * n)(*[_host_ptr(b) for b in bs])
+        xp = (_dp * n)(*[_host_ptr(x) for x in xs])
+        infos = (jqcd_solve_info * n)()
+        st = jqcd_cg_solve_batch(self.h, n, ids, params, bp, xp, infos)
+        if check:
+            self.check(st, "jqcd_cg_solve_batch")
+        return xs, [i.as_dict() for i in infos], st
 
     # ---- gauge fields -----------------------------------------------------
     def gauge_upload(self, dims, links: np.ndarray, t_antiperiodic=True) -> "Gauge":

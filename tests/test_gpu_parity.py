@@ -271,3 +271,18 @@ def test_mixed_rejects_whole_lattice(jq):
                              mode=jqcd.CG_MIXED_F32, check=False)
     assert st == jqcd.EINVAL
     g.free()
+
+
+@pytest.mark.parametrize("mode", ["mixed_f16", "mixed_f32", "dw"])
+def test_point_source_solve(jq, mode):
+    """Point source (spin 2, colour 1 at the origin): the solution's support
+    spreads one site per hop and its edge reaches denormal magnitudes."""
+    jqcd, ctx = jq
+    dims = (8, 8, 8, 16)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=9)
+    b = synth.point_source(dims, 2, 1)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.MODES[mode])
+    assert st == 0
+    assert system_residual(dims, U, b, x, 0.12, True) <= 1e-10 * (1 + 1e-6)
+    g.free()
