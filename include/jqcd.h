@@ -45,7 +45,8 @@
  * Ownership: the library never frees caller memory.  Host inputs are copied
  * during the call; device buffers passed to kernel-level calls stay owned by
  * the caller and must stay valid until the work on `stream` has completed.
- * Threading: one caller thread per context.
+ * Threading: one caller thread per context, except jqcd_serve_submit and
+ * jqcd_serve_poll, which may be called from any thread while a server runs.
  */
 #ifndef JQCD_H
 #define JQCD_H
@@ -248,6 +249,50 @@ JQCD_API jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const j
 JQCD_API jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_ids,
                                          const jqcd_solve_params *params, const double *const *b,
                                          double *const *x, jqcd_solve_info *infos);
+
+/* ---- serving: continuous batching of solves -------------------------------
+ * A scheduler thread owned by the context admits queued solve requests as
+ * engine slots and device memory free up, advances every admitted solve
+ * together (the batched engine of jqcd_cg_solve_batch), and completes each
+ * request as soon as it converges.  Requests that arrive while others run
+ * join at the next iteration boundary.  Admission is first come, first
+ * served, by HBM footprint: a request is admitted when a slot is free and the
+ * device memory held by all slot buffers, plus what this request adds, stays
+ * within hbm_budget_bytes (resident gauge fields are not counted).
+ * This mode of operation has no counterpart in the paper; it serves the
+ * paper's solves (solve_DinvX! with per-request kappa and eps_CG). */
+typedef struct {
+  uint64_t gauge_id;         /* resident gauge field (jqcd_gauge_upload) */
+  jqcd_solve_params params;  /* kappa, tol, maxiter; mode must match the server's; eo = 1 */
+  const double *b;           /* host canonical source, read during admission */
+  double *x;                 /* host canonical solution, written before completion */
+} jqcd_request;              /* b and x must stay valid until the request has completed */
+
+typedef struct {
+  int64_t completed;      /* requests finished */
+  int64_t rejected;       /* requests whose footprint exceeds the budget */
+  double p50_s, p99_s;    /* latency percentiles, submit -> completion */
+  double mean_s;
+  double solves_per_s;    /* completed / (last completion - first submit) */
+  double wall_s;
+  double peak_hbm_bytes;  /* peak device bytes held by solve slots */
+  int32_t peak_active;    /* largest number of solves iterating together */
+  int32_t reserved;
+} jqcd_serve_stats;
+
+/* Start the scheduler thread.  max_slots: solves iterating together (>= 1);
+ * max_queue: waiting requests before submit returns JQCD_EBUSY (0 = unbounded);
+ * mode: JQCD_CG_MIXED_F16 or JQCD_CG_MIXED_F32.  One server per context. */
+JQCD_API jqcd_status jqcd_serve_start(jqcd_ctx *ctx, size_t hbm_budget_bytes, int32_t max_slots,
+                                      int32_t max_queue, int32_t mode);
+/* Queue a request; *ticket identifies it.  Thread-safe.  JQCD_EBUSY when the
+ * queue is full, JQCD_ENOTFOUND for an unknown gauge id. */
+JQCD_API jqcd_status jqcd_serve_submit(jqcd_ctx *ctx, const jqcd_request *req, uint64_t *ticket);
+/* JQCD_PENDING while queued or running; otherwise the request's final status
+ * (info filled, x written) and the ticket is released.  Thread-safe. */
+JQCD_API jqcd_status jqcd_serve_poll(jqcd_ctx *ctx, uint64_t ticket, jqcd_solve_info *info);
+/* Wait for every submitted request to finish, stop the thread, report stats. */
+JQCD_API jqcd_status jqcd_serve_stop(jqcd_ctx *ctx, jqcd_serve_stats *stats);
 
 #ifdef __cplusplus
 }

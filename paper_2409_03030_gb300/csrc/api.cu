@@ -13,9 +13,12 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include "batch_engine.h"
 #include "jqcd.h"
 #include "kernels.h"
+#include "serve.h"
 #include "solver.h"
 
 using namespace jqcd;
@@ -34,6 +37,9 @@ struct jqcd_ctx {
   uint64_t next_id = 1;
   std::map<uint64_t, std::unique_ptr<GaugeEntry>> gauges;
   std::unique_ptr<BatchEngine> engine[2];  // batched solves: FP32 and FP16 inner precision
+  Server *server = nullptr;                // continuous-batching solve server
+  int server_mode = 0;
+  std::mutex gauges_mu;                    // gauge map vs. serve_submit from other threads
 };
 
 namespace {
@@ -128,6 +134,11 @@ jqcd_status jqcd_init(int device, jqcd_ctx **out) {
 jqcd_status jqcd_finalize(jqcd_ctx *ctx) {
   if (!ctx) return JQCD_EINVAL;
   cudaSetDevice(ctx->device);
+  if (ctx->server) {
+    std::string err;
+    serve_destroy(ctx->server, nullptr, &err);
+    ctx->server = nullptr;
+  }
   if (!ctx->poisoned) cudaStreamSynchronize(ctx->stream);
   ctx->engine[0].reset();
   ctx->engine[1].reset();
@@ -164,6 +175,7 @@ jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const doub
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   cudaFree(canon);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "gauge upload");
+  std::lock_guard<std::mutex> lk(ctx->gauges_mu);
   const uint64_t id = ctx->next_id++;
   ctx->gauges[id] = std::move(G);
   *gauge_id = id;
@@ -172,7 +184,10 @@ jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const doub
 
 jqcd_status jqcd_gauge_free(jqcd_ctx *ctx, uint64_t gauge_id) {
   if (!ctx) return JQCD_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->gauges_mu);
   auto it = ctx->gauges.find(gauge_id);
+  if (it != ctx->gauges.end() && ctx->server && serve_uses_gauge(ctx->server, it->second.get()))
+    return fail(ctx, JQCD_EBUSY, "gauge %llu has requests in flight", (unsigned long long)gauge_id);
   if (it == ctx->gauges.end()) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id %llu",
                                            (unsigned long long)gauge_id);
   cudaSetDevice(ctx->device);
@@ -390,6 +405,58 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
     }
   }
   if (worst != JQCD_OK) return fail(ctx, worst, "cg_solve_batch: a solve did not converge");
+  return JQCD_OK;
+}
+
+
+jqcd_status jqcd_serve_start(jqcd_ctx *ctx, size_t hbm_budget_bytes, int32_t max_slots,
+                             int32_t max_queue, int32_t mode) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  if (ctx->server) return fail(ctx, JQCD_EBUSY, "a server is already running on this context");
+  if (max_slots < 1 || max_queue < 0 || (mode != JQCD_CG_MIXED_F16 && mode != JQCD_CG_MIXED_F32))
+    return fail(ctx, JQCD_EINVAL, "serve_start: max_slots >= 1, max_queue >= 0, mixed mode");
+  std::string err;
+  Server *S = serve_create(ctx->device, ctx->sm_count, mode == JQCD_CG_MIXED_F16 ? PREC_F16N : PREC_F32,
+                           hbm_budget_bytes, max_slots, max_queue, &err);
+  if (!S) return fail(ctx, JQCD_ECUDA, "serve_start: %s", err.c_str());
+  ctx->server = S;
+  ctx->server_mode = mode;
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_serve_submit(jqcd_ctx *ctx, const jqcd_request *req, uint64_t *ticket) {
+  if (!ctx || !req || !ticket || !req->b || !req->x) return JQCD_EINVAL;
+  if (!ctx->server) return JQCD_EINVAL;
+  const jqcd_solve_params &P = req->params;
+  if (P.mode != ctx->server_mode || !P.eo || !(P.tol > 0.0) || P.maxiter < 1 ||
+      !(P.kappa >= 0.0) || !(P.delta >= 0.0 && P.delta < 1.0))
+    return JQCD_EINVAL;
+  GaugeEntry *G;
+  {
+    std::lock_guard<std::mutex> lk(ctx->gauges_mu);
+    G = find_gauge(ctx, req->gauge_id);
+  }
+  if (!G) return JQCD_ENOTFOUND;
+  if (G->g.vh >= ((int64_t)1 << 31)) return JQCD_EINVAL;
+  return serve_submit(ctx->server, G, *req, ticket);
+}
+
+jqcd_status jqcd_serve_poll(jqcd_ctx *ctx, uint64_t ticket, jqcd_solve_info *info) {
+  if (!ctx || !ctx->server) return JQCD_EINVAL;
+  return serve_poll(ctx->server, ticket, info, true);
+}
+
+jqcd_status jqcd_serve_stop(jqcd_ctx *ctx, jqcd_serve_stats *stats) {
+  if (!ctx) return JQCD_EINVAL;
+  if (!ctx->server) return fail(ctx, JQCD_EINVAL, "no server running");
+  std::string err;
+  jqcd_status st = serve_destroy(ctx->server, stats, &err);
+  ctx->server = nullptr;
+  if (st != JQCD_OK) {
+    ctx->poisoned = true;
+    return fail(ctx, st, "serve: %s", err.c_str());
+  }
   return JQCD_OK;
 }
 

@@ -111,6 +111,38 @@ int BatchEngine::free_slot() const {
   return -1;
 }
 
+int BatchEngine::pick_slot(int64_t vh, int64_t *extra) const {
+  const size_t need = SlotBuffers::footprint(vh, hp_);
+  int best = -1, empty = -1, largest = -1;
+  for (size_t i = 0; i < slots_.size(); ++i) {
+    const SlotHost &S = slots_[i];
+    if (S.state != 0) continue;
+    if (S.buf.vh_cap >= vh && S.buf.hp == hp_) {
+      if (best < 0 || S.buf.bytes < slots_[best].buf.bytes) best = (int)i;
+    } else if (S.buf.vh_cap == 0) {
+      if (empty < 0) empty = (int)i;
+    } else if (largest < 0 || S.buf.bytes > slots_[largest].buf.bytes) {
+      largest = (int)i;
+    }
+  }
+  if (best >= 0) { *extra = 0; return best; }
+  if (empty >= 0) { *extra = (int64_t)need; return empty; }
+  if (largest >= 0) { *extra = (int64_t)need - (int64_t)slots_[largest].buf.bytes; return largest; }
+  *extra = 0;
+  return -1;
+}
+
+void BatchEngine::release_idle(int keep) {
+  for (size_t i = 0; i < slots_.size(); ++i)
+    if ((int)i != keep && slots_[i].state == 0 && slots_[i].buf.vh_cap > 0) slots_[i].buf.release();
+}
+
+size_t BatchEngine::allocated_bytes() const {
+  size_t b = 0;
+  for (const SlotHost &S : slots_) b += S.buf.bytes;
+  return b;
+}
+
 int BatchEngine::running() const {
   int r = 0;
   for (const SlotHost &s : slots_) r += s.state == 1;

@@ -61,6 +61,14 @@ class BatchEngine {
   // Choose sites per tile and grid size for the current active set.
   cudaError_t autotune();
   const SolverScalars &scalars(int slot) const { return h_S_[slot]; }
+  // Free slot for a lattice of vh sites: best fit among free slots whose
+  // buffers already suffice (extra = 0), else an unused slot or the largest
+  // free one (extra = bytes the admission will add).  -1 if none is free.
+  int pick_slot(int64_t vh, int64_t *extra_bytes) const;
+  // Device bytes held by all slot buffers.
+  size_t allocated_bytes() const;
+  // Free the buffers of every idle slot except `keep`.
+  void release_idle(int keep);
   double now() const;
   int tile_sites() const { return tile_sites_; }
   int grid() const { return grid_; }

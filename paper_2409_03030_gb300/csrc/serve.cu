@@ -1,0 +1,286 @@
+// Solve server: continuous batching of CG solves on one GPU.
+//
+// jqcd_serve_submit queues a request (thread-safe, never blocks on the GPU).
+// One scheduler thread owns a BatchEngine on its own stream and loops:
+//   admit queued requests while a slot is free and the device memory the
+//   request needs (its slot buffers) fits the byte budget -> advance every
+//   admitted solve together by a few batched iterations -> collect the solves
+//   that finished (x written to the caller's buffer, latency recorded).
+// Requests that arrive while others iterate join at the next iteration
+// boundary; their work shares the same kernel launches (and, on the same
+// gauge field, the same link loads).  Admission is FIFO: a request that does
+// not fit waits until earlier ones finish.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "batch_engine.h"
+#include "serve.h"
+
+namespace jqcd {
+
+namespace {
+double wall() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+constexpr int kItersPerStep = 8;
+}  // namespace
+
+struct ServeTicket {
+  jqcd_request req;
+  GaugeEntry *G = nullptr;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  int state = 0;  // 0 queued, 1 running, 2 finished
+  jqcd_status status = JQCD_PENDING;
+  jqcd_solve_info info{};
+  size_t footprint = 0;
+  int slot = -1;
+};
+
+struct Server {
+  int device = 0;
+  int sm_count = 152;
+  int hp = PREC_F16N;
+  size_t budget = 0;
+  int max_queue = 0;
+  cudaStream_t stream = nullptr;
+  std::unique_ptr<BatchEngine> engine;
+  std::thread thread;
+  std::mutex mu;
+  std::condition_variable cv;
+  bool stop = false;
+  double stop_deadline = 0.0;  // drain limit after stop (seconds on wall())
+  bool failed = false;
+  std::string error;
+  uint64_t next_ticket = 1;
+  std::deque<uint64_t> queue;                       // waiting tickets, FIFO
+  std::map<uint64_t, std::unique_ptr<ServeTicket>> tickets;
+  std::map<int, uint64_t> slot_ticket;              // engine slot -> ticket
+  size_t peak_alloc = 0;                            // peak device bytes of slot buffers
+  int peak_active = 0;
+  double t_first = 0.0, t_last = 0.0;
+  std::vector<double> latencies;
+  int64_t rejected = 0;
+
+  void loop();
+};
+
+void Server::loop() {
+  cudaSetDevice(device);
+  std::vector<int> finished;
+  for (;;) {
+    std::vector<std::pair<uint64_t, ServeTicket *>> admit;
+    {
+      std::unique_lock<std::mutex> lk(mu);
+      const bool idle = engine->running() == 0;
+      if (idle && queue.empty()) {
+        if (stop) return;
+        cv.wait_for(lk, std::chrono::milliseconds(2));
+        continue;
+      }
+      if (stop && wall() > stop_deadline) {  // drain took too long: give up
+        for (auto &kv : tickets)
+          if (kv.second->state != 2) {
+            kv.second->state = 2;
+            kv.second->status = JQCD_ETIMEOUT;
+          }
+        failed = true;
+        error = "requests still running at the stop deadline";
+        return;
+      }
+      // FIFO admission: a free slot and a device-memory budget that covers
+      // every slot buffer allocated so far plus what this request adds
+      int64_t planned = 0;
+      std::vector<int> taken;
+      while (!queue.empty() && (int)taken.size() < engine->max_slots()) {
+        ServeTicket *T = tickets[queue.front()].get();
+        if (T->footprint > budget) {  // can never fit
+          T->state = 2;
+          T->status = JQCD_ENOMEM;
+          T->t_done = wall();
+          ++rejected;
+          queue.pop_front();
+          continue;
+        }
+        int64_t extra = 0;
+        int slot = engine->pick_slot(T->G->g.vh, &extra);
+        if (slot >= 0 && std::find(taken.begin(), taken.end(), slot) != taken.end()) break;
+        if (slot < 0) break;
+        if ((int64_t)engine->allocated_bytes() + planned + extra > (int64_t)budget) {
+          // idle slots may be holding buffers from earlier, larger requests
+          engine->release_idle(slot);
+          slot = engine->pick_slot(T->G->g.vh, &extra);
+          if (slot < 0 || (int64_t)engine->allocated_bytes() + planned + extra > (int64_t)budget) break;
+        }
+        planned += extra;
+        taken.push_back(slot);
+        T->slot = slot;
+        admit.push_back({queue.front(), T});
+        queue.pop_front();
+        break;  // one admission per pass: pick_slot sees the new slot state next time
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    for (auto &a : admit) {
+      ServeTicket *T = a.second;
+      e = engine->admit(T->slot, T->G, T->req.params, T->req.b);
+      if (e) break;
+      std::lock_guard<std::mutex> lk(mu);
+      T->state = 1;
+      T->t_admit = wall();
+      slot_ticket[T->slot] = a.first;
+      peak_alloc = std::max(peak_alloc, engine->allocated_bytes());
+      peak_active = std::max(peak_active, (int)slot_ticket.size());
+    }
+    // keep admitting while requests fit before spending time on iterations
+    if (!e && !admit.empty()) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!queue.empty() && (int)slot_ticket.size() < engine->max_slots()) {
+        int64_t extra = 0;
+        const int slot = engine->pick_slot(tickets[queue.front()]->G->g.vh, &extra);
+        if (slot >= 0 && (int64_t)engine->allocated_bytes() + extra <= (int64_t)budget) continue;
+      }
+    }
+    if (!e && engine->running() > 0) e = engine->run(kItersPerStep);
+    finished.clear();
+    if (!e) e = engine->poll(&finished);
+    for (int slot : finished) {
+      if (e) break;
+      uint64_t id;
+      ServeTicket *T;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        id = slot_ticket[slot];
+        T = tickets[id].get();
+      }
+      jqcd_solve_info inf;
+      e = engine->collect(slot, T->req.x, &inf);
+      if (e) break;
+      std::lock_guard<std::mutex> lk(mu);
+      T->t_done = wall();
+      inf.seconds = T->t_done - T->t_submit;
+      T->info = inf;
+      T->status = inf.status;
+      T->state = 2;
+      slot_ticket.erase(slot);
+      latencies.push_back(T->t_done - T->t_submit);
+      t_last = T->t_done;
+    }
+    if (e) {
+      std::lock_guard<std::mutex> lk(mu);
+      failed = true;
+      error = cudaGetErrorString(e);
+      for (auto &kv : tickets)
+        if (kv.second->state != 2) {
+          kv.second->state = 2;
+          kv.second->status = JQCD_ECUDA;
+        }
+      return;
+    }
+  }
+}
+
+Server *serve_create(int device, int sm_count, int hp, size_t budget, int max_slots, int max_queue,
+                     std::string *err) {
+  std::unique_ptr<Server> S(new Server());
+  S->device = device;
+  S->sm_count = sm_count;
+  S->hp = hp;
+  S->budget = budget;
+  S->max_queue = max_queue;
+  cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e) { *err = cudaGetErrorString(e); return nullptr; }
+  S->engine.reset(new BatchEngine(hp, max_slots, S->stream, sm_count));
+  e = S->engine->init();
+  if (e) { *err = cudaGetErrorString(e); return nullptr; }
+  Server *raw = S.get();
+  S->thread = std::thread([raw] { raw->loop(); });
+  return S.release();
+}
+
+jqcd_status serve_submit(Server *S, GaugeEntry *G, const jqcd_request &r, uint64_t *ticket) {
+  std::unique_ptr<ServeTicket> T(new ServeTicket());
+  T->req = r;
+  T->G = G;
+  T->t_submit = wall();
+  T->footprint = SlotBuffers::footprint(G->g.vh, S->hp);
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->failed) return JQCD_ECUDA;
+  if (S->stop) return JQCD_EINVAL;
+  if (S->max_queue > 0 && (int)S->queue.size() >= S->max_queue) return JQCD_EBUSY;
+  const uint64_t id = S->next_ticket++;
+  if (S->t_first == 0.0) S->t_first = T->t_submit;
+  S->tickets[id] = std::move(T);
+  S->queue.push_back(id);
+  *ticket = id;
+  S->cv.notify_one();
+  return JQCD_OK;
+}
+
+jqcd_status serve_poll(Server *S, uint64_t ticket, jqcd_solve_info *info, bool forget) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->tickets.find(ticket);
+  if (it == S->tickets.end()) return JQCD_ENOTFOUND;
+  ServeTicket *T = it->second.get();
+  if (T->state != 2) return JQCD_PENDING;
+  if (info) *info = T->info;
+  const jqcd_status st = T->status;
+  if (forget) S->tickets.erase(it);
+  return st;
+}
+
+bool serve_uses_gauge(Server *S, const GaugeEntry *G) {
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (auto &kv : S->tickets)
+    if (kv.second->G == G && kv.second->state != 2) return true;
+  return false;
+}
+
+jqcd_status serve_destroy(Server *S, jqcd_serve_stats *stats, std::string *err) {
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->stop_deadline = wall() + 300.0;
+    S->cv.notify_one();
+  }
+  if (S->thread.joinable()) S->thread.join();
+  jqcd_status st = S->failed ? JQCD_ECUDA : JQCD_OK;
+  if (S->failed) *err = S->error;
+  if (stats) {
+    memset(stats, 0, sizeof *stats);
+    std::vector<double> l = S->latencies;
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double q) -> double {
+      if (l.empty()) return 0.0;
+      size_t k = (size_t)std::ceil(q * l.size()) - 1;
+      return l[std::min(k, l.size() - 1)];
+    };
+    stats->completed = (int64_t)l.size();
+    stats->rejected = S->rejected;
+    stats->p50_s = pct(0.50);
+    stats->p99_s = pct(0.99);
+    double sum = 0;
+    for (double v : l) sum += v;
+    stats->mean_s = l.empty() ? 0.0 : sum / l.size();
+    stats->wall_s = S->t_last > S->t_first ? S->t_last - S->t_first : 0.0;
+    stats->solves_per_s = stats->wall_s > 0 ? l.size() / stats->wall_s : 0.0;
+    stats->peak_hbm_bytes = (double)S->peak_alloc;
+    stats->peak_active = S->peak_active;
+  }
+  S->engine.reset();
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
+  return st;
+}
+
+}  // namespace jqcd

@@ -42,6 +42,22 @@ class jqcd_solve_params(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class jqcd_request(ctypes.Structure):
+    _fields_ = [("gauge_id", ctypes.c_uint64), ("params", jqcd_solve_params),
+                ("b", ctypes.POINTER(ctypes.c_double)), ("x", ctypes.POINTER(ctypes.c_double))]
+
+
+class jqcd_serve_stats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("wall_s", ctypes.c_double),
+                ("peak_hbm_bytes", ctypes.c_double), ("peak_active", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
 class jqcd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32),
                 ("restarts", ctypes.c_int32), ("status", ctypes.c_int32),
@@ -82,6 +98,11 @@ _SIGNATURES = {
     "jqcd_cg_solve_batch": (_st, [_vp, ctypes.c_int32, ctypes.POINTER(_u64),
                                   ctypes.POINTER(jqcd_solve_params), ctypes.POINTER(_dp),
                                   ctypes.POINTER(_dp), ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_serve_start": (_st, [_vp, ctypes.c_size_t, ctypes.c_int32, ctypes.c_int32,
+                               ctypes.c_int32]),
+    "jqcd_serve_submit": (_st, [_vp, ctypes.POINTER(jqcd_request), ctypes.POINTER(_u64)]),
+    "jqcd_serve_poll": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_serve_stop": (_st, [_vp, ctypes.POINTER(jqcd_serve_stats)]),
     "jqcd_cg_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(jqcd_solve_info), _vp]),
 }
@@ -191,6 +212,31 @@ class Context:
         if check:
             self.check(st, "jqcd_cg_solve_batch")
         return xs, [i.as_dict() for i in infos], st
+
+    # ---- serving ------------------------------------------------------------
+    def serve_start(self, hbm_budget_bytes, max_slots=32, max_queue=0, mode=CG_MIXED_F16):
+        self.check(jqcd_serve_start(self.h, int(hbm_budget_bytes), int(max_slots), int(max_queue),
+                                    int(mode)), "jqcd_serve_start")
+
+    def serve_submit(self, gauge, b, x, kappa, tol, maxiter=20000, mode=CG_MIXED_F16, delta=0.0):
+        """Queue a solve.  b, x: C-contiguous complex128 host arrays that must
+        stay alive (and x untouched) until poll reports completion.  Returns
+        (status, ticket); status is OK, EBUSY (queue full) or an error."""
+        req = jqcd_request(int(gauge.id), Gauge.params(kappa, tol, maxiter, True, mode, 0, delta),
+                           _host_ptr(b), _host_ptr(x))
+        t = ctypes.c_uint64(0)
+        st = jqcd_serve_submit(self.h, ctypes.byref(req), ctypes.byref(t))
+        return st, t.value
+
+    def serve_poll(self, ticket):
+        info = jqcd_solve_info()
+        st = jqcd_serve_poll(self.h, int(ticket), ctypes.byref(info))
+        return st, (info.as_dict() if st != PENDING else None)
+
+    def serve_stop(self):
+        stats = jqcd_serve_stats()
+        self.check(jqcd_serve_stop(self.h, ctypes.byref(stats)), "jqcd_serve_stop")
+        return stats.as_dict()
 
     # ---- gauge fields -----------------------------------------------------
     def gauge_upload(self, dims, links: np.ndarray, t_antiperiodic=True) -> "Gauge":

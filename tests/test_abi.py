@@ -56,7 +56,9 @@ def test_struct_layout_matches_c(tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(jqcd_lattice),'
                    ' sizeof(jqcd_solve_params), sizeof(jqcd_solve_info),'
                    ' offsetof(jqcd_solve_params, delta), offsetof(jqcd_solve_info, true_rel_resid),'
-                   ' offsetof(jqcd_solve_info, hop_count)); return 0;}\n')
+                   ' offsetof(jqcd_solve_info, hop_count)); printf("%zu %zu %zu\\n",'
+                   ' sizeof(jqcd_request), sizeof(jqcd_serve_stats), offsetof(jqcd_request, x));'
+                   ' return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
                     str(exe)], check=True)
@@ -64,7 +66,9 @@ def test_struct_layout_matches_c(tmp_path):
                                           check=True).stdout.split()]
     want = [ctypes.sizeof(jqcd.jqcd_lattice), ctypes.sizeof(jqcd.jqcd_solve_params),
             ctypes.sizeof(jqcd.jqcd_solve_info), jqcd.jqcd_solve_params.delta.offset,
-            jqcd.jqcd_solve_info.true_rel_resid.offset, jqcd.jqcd_solve_info.hop_count.offset]
+            jqcd.jqcd_solve_info.true_rel_resid.offset, jqcd.jqcd_solve_info.hop_count.offset,
+            ctypes.sizeof(jqcd.jqcd_request), ctypes.sizeof(jqcd.jqcd_serve_stats),
+            jqcd.jqcd_request.x.offset]
     assert got == want
 
 

@@ -1,0 +1,108 @@
+"""Solve server (continuous batching): requests of different lattices, kappa
+and tolerances arrive while others run; every result must equal the same
+solve run alone within the tolerance bound and pass the oracle's residual
+check.  Also: queue-full back-pressure and over-budget rejection."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_2409_03030_gb300 import synth
+from test_gpu_parity import rel, system_residual
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def jq():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_03030_gb300 import jqcd
+    ctx = jqcd.Context(0)
+    yield jqcd, ctx
+    ctx.close()
+
+
+def wait_all(ctx, jqcd, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for t in tickets:
+            if t in out:
+                continue
+            st, info = ctx.serve_poll(t)
+            if st != jqcd.PENDING:
+                out[t] = (st, info)
+        assert time.time() - t0 < timeout, "server did not finish"
+        time.sleep(0.001)
+    return out
+
+
+def test_serve_mix_equals_alone(jq):
+    jqcd, ctx = jq
+    lat = {"a": (8, 8, 8, 8), "b": (6, 6, 6, 10), "c": (16, 16, 16, 16)}
+    U = {k: synth.gauge(d, "expi", eps=0.3, seed=40 + i) for i, (k, d) in enumerate(lat.items())}
+    G = {k: ctx.gauge_upload(lat[k], U[k]) for k in lat}
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(12):
+        k = ["a", "b", "c"][i % 3]
+        b = synth.gaussian_spinor(lat[k], seed=500 + i)
+        reqs.append((k, b, float(rng.uniform(0.10, 0.122)), [1e-8, 1e-10, 1e-12][i % 3]))
+    ctx.serve_start(8 << 30, max_slots=6, mode=jqcd.CG_MIXED_F16)
+    xs, tickets = [], []
+    for i, (k, b, kap, tol) in enumerate(reqs):
+        x = np.zeros_like(b)
+        st, t = ctx.serve_submit(G[k], b, x, kap, tol, mode=jqcd.CG_MIXED_F16)
+        assert st == 0
+        xs.append(x)
+        tickets.append(t)
+        if i % 4 == 3:
+            time.sleep(0.005)  # later requests join while earlier ones iterate
+    res = wait_all(ctx, jqcd, tickets)
+    stats = ctx.serve_stop()
+    assert stats["completed"] == len(reqs) and stats["peak_active"] >= 2
+    for (k, b, kap, tol), x, t in zip(reqs, xs, tickets):
+        st, info = res[t]
+        assert st == 0 and info["true_rel_resid"] <= tol
+        assert system_residual(lat[k], U[k], b, x, kap, True) <= tol * (1 + 1e-6)
+        xa, ia, sa = G[k].cg_solve(b, kap, tol=tol, eo=True, mode=jqcd.CG_MIXED_F16)
+        assert rel(x, xa) <= 1e3 * tol
+    for g in G.values():
+        g.free()
+
+
+def test_serve_backpressure_and_budget(jq):
+    jqcd, ctx = jq
+    d = (16, 16, 16, 16)
+    g = ctx.gauge_upload(d, synth.gauge(d, "expi", eps=0.3, seed=60))
+    b = synth.gaussian_spinor(d, seed=61)
+    # budget below one slot: every request is rejected
+    ctx.serve_start(1 << 20, max_slots=2, mode=jqcd.CG_MIXED_F32)
+    x = np.zeros_like(b)
+    st, t = ctx.serve_submit(g, b, x, 0.12, 1e-10, mode=jqcd.CG_MIXED_F32)
+    assert st == 0
+    st, info = wait_all(ctx, jqcd, [t])[t]
+    assert st == jqcd.ENOMEM
+    assert ctx.serve_stop()["rejected"] == 1
+    # one slot, queue of one: rapid submissions hit EBUSY
+    ctx.serve_start(8 << 30, max_slots=1, max_queue=1, mode=jqcd.CG_MIXED_F32)
+    xs, tickets, busy = [], [], 0
+    for i in range(20):
+        x = np.zeros_like(b)
+        st, t = ctx.serve_submit(g, b, x, 0.12, 1e-12, mode=jqcd.CG_MIXED_F32)
+        if st == jqcd.EBUSY:
+            busy += 1
+        else:
+            assert st == 0
+            xs.append(x)
+            tickets.append(t)
+    assert busy > 0
+    # wrong mode and unknown gauge are refused at submission
+    st, _ = ctx.serve_submit(g, b, np.zeros_like(b), 0.12, 1e-10, mode=jqcd.CG_MIXED_F16)
+    assert st == jqcd.EINVAL
+    res = wait_all(ctx, jqcd, tickets)
+    assert all(v[0] == 0 for v in res.values())
+    ctx.serve_stop()
+    g.free()
