@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config2", action="store_true",
                     help="skip the 32^3x64 mixed-vs-double-word CG comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 24-solve batch")
+    ap.add_argument("--serve-requests", type=int, default=300,
+                    help="requests of the serving run (0 skips it)")
     return ap.parse_args()
 
 
@@ -217,6 +220,103 @@ def workload_config():
             "parallelism": "replicas"}
 
 
+def bench_batch(ctx, jqcd, synth, np):
+    """12 point sources on 24^3x48 + 12 Gaussian sources on 16^4 (kappa 0.12,
+    exp(i 0.3 H) links, tol 1e-10, FP16 inner): one jqcd_cg_solve_batch call
+    vs the same 24 solves one after another through jqcd_cg_solve."""
+    dA, dB = (24, 24, 24, 48), (16, 16, 16, 16)
+    gA = ctx.gauge_upload(dA, synth.gauge(dA, "expi", eps=EPS, seed=31))
+    gB = ctx.gauge_upload(dB, synth.gauge(dB, "expi", eps=EPS, seed=32))
+    bs = [synth.point_source(dA, s, c) for s in range(4) for c in range(3)]
+    bs += [synth.gaussian_spinor(dB, seed=100 + i) for i in range(12)]
+    gauges = [gA] * 12 + [gB] * 12
+    mode = jqcd.CG_MIXED_F16
+    ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode)  # warm-up + autotune
+    t0 = time.perf_counter()
+    xs, infos, st = ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode)
+    t_batch = time.perf_counter() - t0
+    gA.cg_solve(bs[0], KAPPA, tol=TOL, mode=mode)  # warm-up
+    t0 = time.perf_counter()
+    for g, b in zip(gauges, bs):
+        g.cg_solve(b, KAPPA, tol=TOL, mode=mode)
+    t_seq = time.perf_counter() - t0
+    out = {"workload": "12 point sources 24^3x48 + 12 Gaussian 16^4, kappa 0.12, tol 1e-10, "
+                       "mixed FP16, one batch (host buffers)",
+           "batch_s": round(t_batch, 4), "sequential_s": round(t_seq, 4),
+           "speedup": round(t_seq / t_batch, 3), "solves_per_s": round(24 / t_batch, 2),
+           "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
+           "iters": [infos[0]["iters"], infos[12]["iters"]], "status": st}
+    gA.free()
+    gB.free()
+    return out
+
+
+def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
+    """Poisson arrivals (seeded, mean `rate`/s) of solves with volume drawn from
+    {8^4, 16^4, 24^3x48, 32^3x64}, kappa ~ U[0.10, 0.122], tol in {1e-8,
+    1e-10, 1e-12}, Gaussian sources, gauge fields pre-generated (eps 0.3).
+    Latency = scheduled arrival -> completion seen by the client."""
+    vols = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)]
+    gauges = [ctx.gauge_upload(d, synth.gauge(d, "expi", eps=EPS, seed=70 + i))
+              for i, d in enumerate(vols)]
+    n_src, n_x = 3, 8
+    srcs = [[synth.gaussian_spinor(d, seed=800 + 10 * i + j) for j in range(n_src)]
+            for i, d in enumerate(vols)]
+    xpool = [[np.zeros(synth.spinor_shape(d), np.complex128) for _ in range(n_x)] for d in vols]
+    free = [list(range(n_x)) for _ in vols]
+    rng = np.random.default_rng(20261202)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    vol = rng.integers(0, 4, n_req)
+    kap = rng.uniform(0.10, 0.122, n_req)
+    tol = rng.choice([1e-8, 1e-10, 1e-12], n_req)
+    src = rng.integers(0, n_src, n_req)
+    mode = jqcd.CG_MIXED_F16
+    ctx.serve_start(64 << 30, max_slots=32, mode=mode)
+    inflight = {}  # ticket -> (request index, volume, x index)
+    lat, done, nxt, worst_res = [], 0, 0, 0.0
+    t0 = time.perf_counter()
+    while done < n_req:
+        now = time.perf_counter() - t0
+        while nxt < n_req and arrivals[nxt] <= now and free[vol[nxt]]:
+            v = int(vol[nxt])
+            xi = free[v].pop()
+            st, t = ctx.serve_submit(gauges[v], srcs[v][src[nxt]], xpool[v][xi], float(kap[nxt]),
+                                     float(tol[nxt]), mode=mode)
+            if st != 0:
+                raise RuntimeError(f"serve_submit status {st}")
+            inflight[t] = (nxt, v, xi)
+            nxt += 1
+        for t in list(inflight):
+            st, info = ctx.serve_poll(t)
+            if st == jqcd.PENDING:
+                continue
+            i, v, xi = inflight.pop(t)
+            if st != 0:
+                raise RuntimeError(f"request {i} finished with status {st}")
+            lat.append(time.perf_counter() - t0 - arrivals[i])
+            worst_res = max(worst_res, info["true_rel_resid"] / tol[i])
+            free[v].append(xi)
+            done += 1
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    stats = ctx.serve_stop()
+    lat = np.sort(np.array(lat))
+    out = {"workload": f"{n_req} Poisson requests at {rate}/s, volumes 8^4/16^4/24^3x48/32^3x64, "
+                       "kappa U[0.10,0.122], tol {1e-8,1e-10,1e-12}, mixed FP16, budget 64 GiB",
+           "p50_s": round(float(np.percentile(lat, 50)), 5),
+           "p99_s": round(float(np.percentile(lat, 99)), 5),
+           "mean_s": round(float(lat.mean()), 5),
+           "solves_per_s": round(n_req / wall, 2), "offered_per_s": rate,
+           "arrival_span_s": round(float(arrivals[-1]), 3), "wall_s": round(wall, 3),
+           "stable": bool(wall < arrivals[-1] + 2.0),
+           "server_p50_s": round(stats["p50_s"], 5), "server_p99_s": round(stats["p99_s"], 5),
+           "peak_active": stats["peak_active"], "peak_slot_bytes": stats["peak_hbm_bytes"],
+           "max_true_resid_over_tol": worst_res}
+    for g in gauges:
+        g.free()
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -377,6 +477,9 @@ def run_gpu(args):
         cg_c2["workload"] = "32^3x64, exp(i*0.4*H) links, kappa 0.122, even-odd, tol 1e-10"
         g2.free()
 
+    batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
+    serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         _, dt1, _ = time_oracle_cg(U, b, 1)  # calibrate: ~10 s sample
@@ -407,6 +510,8 @@ def run_gpu(args):
                    "modes_24x24x24x48": cg_work, "modes_32x32x32x64": cg_c2},
             "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
                            for k, v in hop_ms.items()},
+            "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     g.free()
