@@ -72,14 +72,30 @@ BatchEngine::BatchEngine(int hp, int max_slots, cudaStream_t s, int sm_count)
       h_slots_(max_slots) {
   memset(h_slots_.data(), 0, sizeof(SlotDev) * h_slots_.size());
   grid_ = sm_count_ * 4;
+  lp_grid_ = sm_count_ * 2;
   t0_ = now();
+}
+
+BatchArgs BatchEngine::args() const {
+  BatchArgs A;
+  A.slots = d_slots_;
+  A.S = d_S_;
+  A.groups = d_groups_;
+  A.tiles = d_tiles_;
+  A.ntiles = d_ntiles_;
+  A.lp_tiles = d_lp_tiles_;
+  A.n_lp_tiles = d_n_lp_tiles_;
+  A.any_update = d_any_update_;
+  A.nslots = (int)slots_.size();
+  return A;
 }
 
 BatchEngine::~BatchEngine() {
   cudaStreamSynchronize(s_);
   if (graph_) cudaGraphExecDestroy(graph_);
   for (void *p : {(void *)d_slots_, (void *)d_S_, (void *)d_groups_, (void *)d_tiles_,
-                  (void *)d_ntiles_, (void *)d_any_update_, (void *)canon_})
+                  (void *)d_ntiles_, (void *)d_lp_tiles_, (void *)d_n_lp_tiles_,
+                  (void *)d_any_update_, (void *)canon_})
     if (p) cudaFree(p);
   if (h_S_) cudaFreeHost(h_S_);
 }
@@ -96,6 +112,8 @@ cudaError_t BatchEngine::init() {
   if (!e) e = cudaMallocHost(&h_S_, sizeof(SolverScalars) * n);
   if (!e) e = cudaMalloc(&d_groups_, sizeof(GroupDev) * n);
   if (!e) e = cudaMalloc(&d_ntiles_, sizeof(int));
+  if (!e) e = cudaMalloc(&d_n_lp_tiles_, sizeof(int));
+  if (!e) e = cudaMemsetAsync(d_n_lp_tiles_, 0, sizeof(int), s_);
   if (!e) e = cudaMalloc(&d_any_update_, sizeof(int));
   if (!e) e = cudaMemsetAsync(d_S_, 0, sizeof(SolverScalars) * n, s_);
   if (!e) e = cudaMemsetAsync(d_ntiles_, 0, sizeof(int), s_);
@@ -229,6 +247,7 @@ cudaError_t BatchEngine::rebuild() {
       continue;
     }
     D.nblocks = (int)((D.g.vh + tile_sites_ - 1) / tile_sites_);
+    D.nblk_lp = (int)((D.g.vh + kLpThreads - 1) / kLpThreads);
     auto it = open.find(D.gauge_f32);
     if (it == open.end() || groups[it->second].nslots == kBatchMaxRhs) {
       GroupDev Gd;
@@ -243,10 +262,23 @@ cudaError_t BatchEngine::rebuild() {
     GroupDev &Gd = groups[it->second];
     Gd.slot[Gd.nslots++] = (int)i;
   }
-  std::vector<int2> tiles;
+  std::vector<int2> tiles, lp_tiles;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const int nbk = (int)((groups[gi].g.vh + tile_sites_ - 1) / tile_sites_);
     for (int j = 0; j < nbk; ++j) tiles.push_back(make_int2((int)gi, j));
+    groups[gi].tpb = 1;
+    const int nlp = (int)((groups[gi].g.vh + kLpThreads - 1) / kLpThreads);
+    for (int j = 0; j < nlp; ++j)
+      for (int r = 0; r < groups[gi].nslots; ++r) lp_tiles.push_back(make_int2((int)gi * 16 + r, j));
+  }
+  if ((int64_t)lp_tiles.size() > max_lp_tiles_) {
+    if (d_lp_tiles_) cudaFree(d_lp_tiles_);
+    d_lp_tiles_ = nullptr;
+    const int64_t cap = std::max<int64_t>((int64_t)lp_tiles.size() * 2, 1024);
+    cudaError_t e0 = cudaMalloc(&d_lp_tiles_, sizeof(int2) * cap);
+    if (e0) { max_lp_tiles_ = 0; return e0; }
+    max_lp_tiles_ = cap;
+    if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }  // pointer changed
   }
   cudaError_t e = cudaSuccess;
   if ((int64_t)tiles.size() > max_tiles_) {
@@ -267,6 +299,11 @@ cudaError_t BatchEngine::rebuild() {
   if (!e && ntiles)
     e = cudaMemcpyAsync(d_tiles_, tiles.data(), sizeof(int2) * tiles.size(), cudaMemcpyHostToDevice, s_);
   if (!e) e = cudaMemcpyAsync(d_ntiles_, &ntiles, sizeof(int), cudaMemcpyHostToDevice, s_);
+  const int n_lp = (int)lp_tiles.size();
+  if (!e && n_lp)
+    e = cudaMemcpyAsync(d_lp_tiles_, lp_tiles.data(), sizeof(int2) * lp_tiles.size(),
+                        cudaMemcpyHostToDevice, s_);
+  if (!e) e = cudaMemcpyAsync(d_n_lp_tiles_, &n_lp, sizeof(int), cudaMemcpyHostToDevice, s_);
   // pageable sources: make the copies complete before the vectors go away
   if (!e) e = cudaStreamSynchronize(s_);
   if (!e) dirty_ = false;
@@ -274,14 +311,16 @@ cudaError_t BatchEngine::rebuild() {
 }
 
 cudaError_t BatchEngine::ensure_graph() {
-  if (graph_ && graph_ts_ == tile_sites_ && graph_grid_ == grid_) return cudaSuccess;
+  if (graph_ && graph_ts_ == tile_sites_ && graph_grid_ == grid_ && graph_lp_grid_ == lp_grid_)
+    return cudaSuccess;
   if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }
-  BatchArgs A{d_slots_, d_S_, d_groups_, d_tiles_, d_ntiles_, d_any_update_, (int)slots_.size()};
+  const BatchArgs A = args();
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal);
   if (e) return e;
   const uint64_t before = jqcd_kernel_launches();
-  for (int k = 0; k < kGraphIters && !e; ++k) e = launch_batch_iteration(A, hp_, tile_sites_, grid_, s_);
+  for (int k = 0; k < kGraphIters && !e; ++k)
+    e = launch_batch_iteration(A, hp_, tile_sites_, grid_, lp_grid_, s_);
   graph_kernels_ = (int64_t)(jqcd_kernel_launches() - before);
   note_launch(-graph_kernels_);  // recorded, not run: counted at each replay instead
   cudaError_t e2 = cudaStreamEndCapture(s_, &g);
@@ -292,6 +331,7 @@ cudaError_t BatchEngine::ensure_graph() {
   if (e) { graph_ = nullptr; return e; }
   graph_ts_ = tile_sites_;
   graph_grid_ = grid_;
+  graph_lp_grid_ = lp_grid_;
   return cudaSuccess;
 }
 
@@ -397,46 +437,35 @@ cudaError_t BatchEngine::autotune() {
   const std::string key = tune_key();
   auto it = tuned_.find(key);
   if (it != tuned_.end()) {
-    if (tile_sites_ != it->second.first) dirty_ = true;
-    tile_sites_ = it->second.first;
-    grid_ = it->second.second;
+    lp_grid_ = it->second.first;
     return cudaSuccess;
   }
-  const int ts_cand[] = {64, 128, 256};
-  const int m_cand[] = {1, 2, 4, 8};
+  cudaError_t e = cudaSuccess;
+  if (dirty_ && (e = rebuild())) return e;
+  const int m_cand[] = {2, 4, 6, 8, 12};
   float best = 1e30f;
-  int best_ts = tile_sites_, best_grid = grid_;
+  int best_grid = lp_grid_;
   cudaEvent_t a, b;
-  cudaError_t e = cudaEventCreate(&a);
-  if (!e) e = cudaEventCreate(&b);
-  if (e) return e;
-  BatchArgs A{d_slots_, d_S_, d_groups_, d_tiles_, d_ntiles_, d_any_update_, (int)slots_.size()};
-  for (int ts : ts_cand) {
-    tile_sites_ = ts;
-    dirty_ = true;
-    if ((e = rebuild())) break;
-    A.tiles = d_tiles_;
-    for (int m : m_cand) {
-      const int grid = sm_count_ * m;
-      if ((e = launch_batch_lp_apply(A, hp_, ts, grid, s_))) break;  // warm-up
-      if ((e = cudaEventRecord(a, s_))) break;
-      for (int r = 0; r < 3 && !e; ++r) e = launch_batch_lp_apply(A, hp_, ts, grid, s_);
-      if (!e) e = cudaEventRecord(b, s_);
-      if (!e) e = cudaEventSynchronize(b);
-      float ms = 0.f;
-      if (!e) e = cudaEventElapsedTime(&ms, a, b);
-      if (e) break;
-      if (ms < best) { best = ms; best_ts = ts; best_grid = grid; }
-    }
+  if ((e = cudaEventCreate(&a))) return e;
+  if ((e = cudaEventCreate(&b))) { cudaEventDestroy(a); return e; }
+  const BatchArgs A = args();
+  for (int m : m_cand) {
+    const int grid = sm_count_ * m;
+    if ((e = launch_batch_lp_apply(A, hp_, grid, s_))) break;  // warm-up
+    if ((e = cudaEventRecord(a, s_))) break;
+    for (int r = 0; r < 3 && !e; ++r) e = launch_batch_lp_apply(A, hp_, grid, s_);
+    if (!e) e = cudaEventRecord(b, s_);
+    if (!e) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (!e) e = cudaEventElapsedTime(&ms, a, b);
     if (e) break;
+    if (ms < best) { best = ms; best_grid = grid; }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e) return e;
-  tile_sites_ = best_ts;
-  grid_ = best_grid;
-  tuned_[key] = {best_ts, best_grid};
-  dirty_ = true;
+  lp_grid_ = best_grid;
+  tuned_[key] = {best_grid, 0};
   return cudaSuccess;
 }
 

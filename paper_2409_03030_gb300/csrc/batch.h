@@ -35,6 +35,8 @@ struct SlotDev {
   double *part;             // partial sums, one per site block
   int active;               // 1 while the solve iterates
   int nblocks;              // site blocks of this lattice for the current tile size
+  int nblk_lp;              // kLpThreads-site blocks of this lattice (hop partials)
+  int pad;
 };
 
 struct GroupDev {
@@ -43,14 +45,17 @@ struct GroupDev {
   const float4 *gauge_dw;
   int nslots;
   int slot[kBatchMaxRhs];
+  int tpb;                  // reserved
 };
 
 struct BatchArgs {
   SlotDev *slots;
   SolverScalars *S;      // one per slot
   GroupDev *groups;
-  int2 *tiles;           // (group, site block)
+  int2 *tiles;           // (group, site block of tile_sites)
   const int *ntiles;
+  int2 *lp_tiles;        // (16 * group + slot in group, block of kLpThreads sites)
+  const int *n_lp_tiles;
   int *any_update;       // nonzero when some slot requested a reliable update
   int nslots;            // descriptors allocated (grid of per-slot kernels)
 };
@@ -58,12 +63,16 @@ struct BatchArgs {
 // Shared-memory limits of the batch kernels; call once before launching.
 cudaError_t batch_configure();
 
-// One CG iteration of every active slot (inner hop precision hp), launched
-// with a persistent grid of `grid` blocks of `tile_sites` threads.
+// Low-precision hop blocks: one thread per site, kLpThreads sites per item.
+constexpr int kLpThreads = 128;
+
+// One CG iteration of every active slot (inner hop precision hp): the
+// low-precision hops on a persistent grid of lp_grid blocks of kLpThreads
+// threads, the other tile kernels on `grid` blocks of `tile_sites` threads.
 cudaError_t launch_batch_iteration(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                   cudaStream_t s);
-// Only the four low-precision hops of one iteration (for the autotuner).
-cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                  cudaStream_t s);
+                                   int lp_grid, cudaStream_t s);
+// Only the four low-precision hops of one iteration (for the autotuner; the
+// last stage also updates x_s and r_s, so run it on a copy of the state).
+cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int lp_grid, cudaStream_t s);
 
 }  // namespace jqcd

@@ -72,10 +72,12 @@ class BatchEngine {
   double now() const;
   int tile_sites() const { return tile_sites_; }
   int grid() const { return grid_; }
+  int lp_grid() const { return lp_grid_; }
   cudaStream_t stream() const { return s_; }
 
  private:
   cudaError_t rebuild();
+  BatchArgs args() const;
   cudaError_t ensure_canon(int64_t vh);
   cudaError_t ensure_graph();
   std::string tune_key() const;
@@ -91,6 +93,10 @@ class BatchEngine {
   GroupDev *d_groups_ = nullptr;
   int2 *d_tiles_ = nullptr;
   int *d_ntiles_ = nullptr;
+  int2 *d_lp_tiles_ = nullptr;
+  int *d_n_lp_tiles_ = nullptr;
+  int64_t max_lp_tiles_ = 0;
+  int lp_grid_ = 0;
   int *d_any_update_ = nullptr;
   int max_groups_ = 0;
   int64_t max_tiles_ = 0;
@@ -100,7 +106,7 @@ class BatchEngine {
   int grid_ = 0;
   bool dirty_ = true;
   cudaGraphExec_t graph_ = nullptr;
-  int graph_ts_ = 0, graph_grid_ = 0;
+  int graph_ts_ = 0, graph_grid_ = 0, graph_lp_grid_ = 0;
   int64_t graph_kernels_ = 0;
   std::map<std::string, std::pair<int, int>> tuned_;
   double t0_ = 0.0;

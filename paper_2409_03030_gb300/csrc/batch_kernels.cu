@@ -20,101 +20,106 @@ __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
   return A.slots[si].active && !A.S[si].halt;
 }
 
-// One of the eight hops of the low-precision operator for one site, the link
-// (rows 0 and 1) taken from the tile's shared-memory stage.
+// One of the eight hops of the low-precision operator for one site; links
+// (rows 0 and 1) through the read-only path, where the blocks of the other
+// right-hand sides on the same sites, running alongside, find them.
 template <int PREC, int MU, bool BWD, bool DAG>
-__device__ __forceinline__ void lp_dir(const void *in, int64_t vh, int32_t nb, bool neg,
-                                       const float4 *lsm, int tid, int bd, cf (&acc)[4][3]) {
+__device__ __forceinline__ void lp_dir(const void *in, const float4 *gauge, int outp, int64_t vh,
+                                       int64_t idx, int64_t nb, bool neg, cf (&acc)[4][3]) {
   constexpr int S = (BWD != DAG) ? 1 : -1;
-  constexpr int D = 2 * MU + (BWD ? 1 : 0);
   cf psi[4][3], h[2][3], r[2][3], u[3][3];
   PT<PREC>::load_spinor(in, vh, nb, psi);
   project<MU, S>(psi, h);
   PT<PREC>::negate_if(h, neg);
-  PT<PREC>::link_from_chunks(lsm[(D * 3 + 0) * bd + tid], lsm[(D * 3 + 1) * bd + tid],
-                             lsm[(D * 3 + 2) * bd + tid], u);
+  const float4 *L = gauge + (size_t)(((BWD ? 1 - outp : outp) * 4 + MU) * 3) * vh + (BWD ? nb : idx);
+  PT<PREC>::link_from_chunks(__ldg(L), __ldg(L + vh), __ldg(L + 2 * vh), u);
   matvec2<BWD>(u, h, r);
   reconstruct<MU, S>(r, acc);
 }
 
-// STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t (norm);  2: t = H^dag_oe w;
-// STAGE 3: Ap = w - kappa^2 H^dag_eo t.  Links staged once per tile.
-template <int PREC, int STAGE>
-__global__ void __launch_bounds__(256) batch_lp_hop_kernel(const BatchArgs A) {
-  extern __shared__ float4 lsm[];  // [8 hops][3 chunks][blockDim.x]
+template <int PREC, int MU, bool DAG>
+__device__ __forceinline__ void lp_mu(const void *in, const float4 *gauge, int outp, const Geom &g,
+                                      int64_t idx, int x, int y, int z, int t, cf (&acc)[4][3]) {
+  bool nf, nbk;
+  const int64_t f = hop_neighbour(g, x, y, z, t, 2 * MU, nf);
+  const int64_t bk = hop_neighbour(g, x, y, z, t, 2 * MU + 1, nbk);
+  lp_dir<PREC, MU, false, DAG>(in, gauge, outp, g.vh, idx, f, nf, acc);
+  lp_dir<PREC, MU, true, DAG>(in, gauge, outp, g.vh, idx, bk, nbk, acc);
+}
+
+// Low-precision hop stages of the batched operator.  Work items are
+// (slot, block of 128 sites); consecutive items are the right-hand sides of
+// one group on the same sites, so their link loads meet in L1/L2.
+// STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t, ||w||^2;  2: t = H^dag_oe w;
+// STAGE 3: Ap = w - kappa^2 H^dag_eo t, then (UPDATE) x_s += alpha p,
+//          r_s -= alpha Ap, ||r_s||^2 without storing Ap.
+template <int PREC, int STAGE, bool UPDATE>
+__global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
   constexpr bool AXPY = STAGE == 1 || STAGE == 3;
-  constexpr bool NORM = STAGE == 1;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int nt = *A.ntiles;
-  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
-    const int2 T = A.tiles[ti];
-    const GroupDev *G = A.groups + T.x;
-    const int ns = G->nslots;
-    bool any = false;
-    for (int s = 0; s < ns; ++s) any |= slot_running(A, G->slot[s]);
-    if (!any) continue;
+  constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
+  const int n = *A.n_lp_tiles;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 W = A.lp_tiles[it];
+    const GroupDev *G = A.groups + (W.x >> 4);
+    const int si = G->slot[W.x & 15];
+    if (!slot_running(A, si)) continue;  // uniform over the block
+    const SlotDev &Sl = A.slots[si];
     const Geom g = G->g;
-    const int64_t idx = (int64_t)T.y * bd + tid;
+    const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
     const bool on = idx < g.vh;
-    int32_t nb[8];
-    unsigned negm = 0;
+    float n2 = 0.f;
     if (on) {
-      int x, y, z, t;
-      cb_coords(g, idx, OUTP, x, y, z, t);
-#pragma unroll
-      for (int d = 0; d < 8; ++d) {
-        bool ng;
-        nb[d] = (int32_t)hop_neighbour(g, x, y, z, t, d, ng);
-        negm |= (ng ? 1u : 0u) << d;
-        const int mu = d >> 1;
-        const bool bwd = (d & 1) != 0;
-        const float4 *L = G->gauge_f32 + (size_t)(((bwd ? 1 - OUTP : OUTP) * 4 + mu) * 3) * g.vh +
-                          (bwd ? (int64_t)nb[d] : idx);
-#pragma unroll
-        for (int j = 0; j < 3; ++j) cp_async16(lsm + (d * 3 + j) * bd + tid, L + j * g.vh, false);
-      }
-      cp_async_commit();
-      cp_async_wait0();  // this thread's links have landed (no other thread reads them)
-    }
-    for (int s = 0; s < ns; ++s) {
-      const int si = G->slot[s];
-      if (!slot_running(A, si)) continue;
-      const SlotDev &Sl = A.slots[si];
       const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
       const void *xv = STAGE == 1 ? Sl.p : Sl.w;
       void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
-      float n2 = 0.f;
-      if (on) {
-        cf acc[4][3];
+      int x, y, z, t;
+      cb_coords(g, idx, OUTP, x, y, z, t);
+      cf acc[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[a][c] = cf{0.f, 0.f};
+      const float4 *U = G->gauge_f32;
+      lp_mu<PREC, 0, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
+      lp_mu<PREC, 1, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
+      lp_mu<PREC, 2, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
+      lp_mu<PREC, 3, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
+      const int64_t vh = g.vh;
+      cf o[4][3];
+      if (AXPY) {
+        cf xs[4][3];
+        PT<PREC>::load_spinor(xv, vh, idx, xs);
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int c = 0; c < 3; ++c) acc[a][c] = cf{0.f, 0.f};
-        const int64_t vh = g.vh;
-        lp_dir<PREC, 0, false, DAG>(in, vh, nb[0], negm & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 0, true, DAG>(in, vh, nb[1], (negm >> 1) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 1, false, DAG>(in, vh, nb[2], (negm >> 2) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 1, true, DAG>(in, vh, nb[3], (negm >> 3) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 2, false, DAG>(in, vh, nb[4], (negm >> 4) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 2, true, DAG>(in, vh, nb[5], (negm >> 5) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 3, false, DAG>(in, vh, nb[6], (negm >> 6) & 1u, lsm, tid, bd, acc);
-        lp_dir<PREC, 3, true, DAG>(in, vh, nb[7], (negm >> 7) & 1u, lsm, tid, bd, acc);
-        cf o[4][3];
-        if (AXPY) {
-          cf xs[4][3];
-          PT<PREC>::load_spinor(xv, vh, idx, xs);
+          for (int c = 0; c < 3; ++c) o[a][c] = PT<PREC>::axpby(1.f, xs[a][c], Sl.k2, acc[a][c]);
+      } else {
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) o[a][c] = PT<PREC>::axpby(1.f, xs[a][c], Sl.k2, acc[a][c]);
-        } else {
+          for (int c = 0; c < 3; ++c) o[a][c] = acc[a][c];
+      }
+      if (STAGE == 3 && UPDATE) {
+        const float al = A.S[si].alpha_f;
+        cf pv[4][3], xv4[4][3], rv[4][3];
+        PT<PREC>::load_spinor(Sl.p, vh, idx, pv);
+        PT<PREC_F32>::load_spinor(Sl.xs, vh, idx, xv4);
+        PT<PREC_F32>::load_spinor(Sl.rs, vh, idx, rv);
 #pragma unroll
-          for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) o[a][c] = acc[a][c];
+        for (int k = 0; k < 12; ++k) {
+          cf &xq = xv4[k / 3][k % 3], &rq = rv[k / 3][k % 3];
+          const cf pp = pv[k / 3][k % 3], aa = o[k / 3][k % 3];
+          xq.re = fmaf(al, pp.re, xq.re);
+          xq.im = fmaf(al, pp.im, xq.im);
+          rq.re = fmaf(-al, aa.re, rq.re);
+          rq.im = fmaf(-al, aa.im, rq.im);
+          n2 = fmaf(rq.re, rq.re, fmaf(rq.im, rq.im, n2));
         }
+        PT<PREC_F32>::store_spinor(Sl.xs, vh, idx, xv4);
+        PT<PREC_F32>::store_spinor(Sl.rs, vh, idx, rv);
+      } else {
         PT<PREC>::store_spinor(out, vh, idx, o);
         if (NORM) {
 #pragma unroll
@@ -122,51 +127,10 @@ __global__ void __launch_bounds__(256) batch_lp_hop_kernel(const BatchArgs A) {
             n2 = fmaf(o[k / 3][k % 3].re, o[k / 3][k % 3].re, fmaf(o[k / 3][k % 3].im, o[k / 3][k % 3].im, n2));
         }
       }
-      if (NORM) {
-        const double sum = block_sum_f(n2);
-        if (tid == 0) Sl.part[T.y] = sum;
-      }
     }
-  }
-}
-
-// x_s += alpha p; r_s -= alpha Ap; partial ||r_s||^2
-template <int PREC>
-__global__ void __launch_bounds__(256) batch_update_kernel(const BatchArgs A) {
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int nt = *A.ntiles;
-  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
-    const int2 T = A.tiles[ti];
-    const GroupDev *G = A.groups + T.x;
-    const int64_t vh = G->g.vh;
-    const int64_t i = (int64_t)T.y * bd + tid;
-    for (int s = 0; s < G->nslots; ++s) {
-      const int si = G->slot[s];
-      if (!slot_running(A, si)) continue;
-      const SlotDev &Sl = A.slots[si];
-      const float a = A.S[si].alpha_f;
-      float n2 = 0.f;
-      if (i < vh) {
-        cf pv[4][3], av[4][3], xv[4][3], rv[4][3];
-        PT<PREC>::load_spinor(Sl.p, vh, i, pv);
-        PT<PREC>::load_spinor(Sl.Ap, vh, i, av);
-        PT<PREC_F32>::load_spinor(Sl.xs, vh, i, xv);
-        PT<PREC_F32>::load_spinor(Sl.rs, vh, i, rv);
-#pragma unroll
-        for (int k = 0; k < 12; ++k) {
-          cf &x = xv[k / 3][k % 3], &r = rv[k / 3][k % 3];
-          const cf pp = pv[k / 3][k % 3], aa = av[k / 3][k % 3];
-          x.re = fmaf(a, pp.re, x.re);
-          x.im = fmaf(a, pp.im, x.im);
-          r.re = fmaf(-a, aa.re, r.re);
-          r.im = fmaf(-a, aa.im, r.im);
-          n2 = fmaf(r.re, r.re, fmaf(r.im, r.im, n2));
-        }
-        PT<PREC_F32>::store_spinor(Sl.xs, vh, i, xv);
-        PT<PREC_F32>::store_spinor(Sl.rs, vh, i, rv);
-      }
+    if (NORM) {
       const double sum = block_sum_f(n2);
-      if (tid == 0) Sl.part[T.y] = sum;
+      if (threadIdx.x == 0) Sl.part[W.y] = sum;
     }
   }
 }
@@ -332,16 +296,16 @@ __global__ void __launch_bounds__(256) batch_dw_resid_kernel(const BatchArgs A) 
 }
 
 // ---- per-slot scalar steps (one block per slot) --------------------------------
-__device__ __forceinline__ double slot_sum(const SlotDev &Sl) {
+__device__ __forceinline__ double slot_sum(const SlotDev &Sl, int n) {
   double v = 0.0;
-  for (int i = threadIdx.x; i < Sl.nblocks; i += blockDim.x) v += Sl.part[i];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v += Sl.part[i];
   return block_sum_d(v);
 }
 
 __global__ void batch_alpha_kernel(const BatchArgs A) {
   const int si = blockIdx.x;
   if (si >= A.nslots || !slot_running(A, si)) return;
-  const double pAp = slot_sum(A.slots[si]);
+  const double pAp = slot_sum(A.slots[si], A.slots[si].nblk_lp);
   if (threadIdx.x == 0) {
     SolverScalars *S = A.S + si;
     S->pAp = pAp;
@@ -355,7 +319,7 @@ __global__ void batch_alpha_kernel(const BatchArgs A) {
 __global__ void batch_beta_kernel(const BatchArgs A) {
   const int si = blockIdx.x;
   if (si >= A.nslots || !slot_running(A, si)) return;
-  const double rr_new = slot_sum(A.slots[si]);
+  const double rr_new = slot_sum(A.slots[si], A.slots[si].nblk_lp);
   if (threadIdx.x == 0) {
     SolverScalars *S = A.S + si;
     S->rr_new = rr_new;
@@ -379,7 +343,7 @@ __global__ void batch_after_update_kernel(const BatchArgs A) {
   if (*A.any_update == 0) return;
   const int si = blockIdx.x;
   if (si >= A.nslots || !A.slots[si].active || A.S[si].need_update != 1) return;
-  const double rr_true = slot_sum(A.slots[si]);
+  const double rr_true = slot_sum(A.slots[si], A.slots[si].nblocks);
   if (threadIdx.x == 0) {
     SolverScalars *S = A.S + si;
     S->reliable_updates += 1;
@@ -407,51 +371,22 @@ __global__ void batch_resume_kernel(const BatchArgs A) {
 }
 
 // ---- launchers -------------------------------------------------------------------
-template <int PREC>
-static cudaError_t configure_prec() {
-  const int mx = 24 * 256 * 16;
-  cudaError_t e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 0>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  if (!e) e = cudaFuncSetAttribute(batch_lp_hop_kernel<PREC, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  return e;
-}
+cudaError_t batch_configure() { return cudaSuccess; }
 
-cudaError_t batch_configure() {
-  cudaError_t e = configure_prec<PREC_F32>();
-  return e ? e : configure_prec<PREC_F16N>();
+template <int PREC, int STAGE, bool UPDATE>
+static void lp_stage(const BatchArgs &A, int lp_grid, cudaStream_t s) {
+  note_launch();
+  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, 0, s>>>(A);
 }
 
 template <int PREC>
-static cudaError_t lp_apply(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)24 * ts * 16;
-  note_launch();
-  batch_lp_hop_kernel<PREC, 0><<<grid, ts, smem, s>>>(A);
-  note_launch();
-  batch_lp_hop_kernel<PREC, 1><<<grid, ts, smem, s>>>(A);
-  return cudaGetLastError();
-}
-
-template <int PREC>
-static cudaError_t lp_apply_dag(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
-  const size_t smem = (size_t)24 * ts * 16;
-  note_launch();
-  batch_lp_hop_kernel<PREC, 2><<<grid, ts, smem, s>>>(A);
-  note_launch();
-  batch_lp_hop_kernel<PREC, 3><<<grid, ts, smem, s>>>(A);
-  return cudaGetLastError();
-}
-
-template <int PREC>
-static cudaError_t iteration(const BatchArgs &A, int ts, int grid, cudaStream_t s) {
-  cudaError_t e = lp_apply<PREC>(A, ts, grid, s);
-  if (e) return e;
+static cudaError_t iteration(const BatchArgs &A, int ts, int grid, int lp_grid, cudaStream_t s) {
+  lp_stage<PREC, 0, false>(A, lp_grid, s);
+  lp_stage<PREC, 1, false>(A, lp_grid, s);
   note_launch();
   batch_alpha_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
-  if ((e = lp_apply_dag<PREC>(A, ts, grid, s))) return e;
-  note_launch();
-  batch_update_kernel<PREC><<<grid, ts, 0, s>>>(A);
+  lp_stage<PREC, 2, false>(A, lp_grid, s);
+  lp_stage<PREC, 3, true>(A, lp_grid, s);  // Ap and the x_s, r_s update
   note_launch();
   batch_beta_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
   note_launch();
@@ -479,20 +414,27 @@ static cudaError_t iteration(const BatchArgs &A, int ts, int grid, cudaStream_t 
 }
 
 cudaError_t launch_batch_iteration(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                   cudaStream_t s) {
-  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1) return cudaErrorInvalidValue;
-  return hp == PREC_F16N ? iteration<PREC_F16N>(A, tile_sites, grid, s)
-                         : iteration<PREC_F32>(A, tile_sites, grid, s);
+                                   int lp_grid, cudaStream_t s) {
+  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1 || lp_grid < 1)
+    return cudaErrorInvalidValue;
+  return hp == PREC_F16N ? iteration<PREC_F16N>(A, tile_sites, grid, lp_grid, s)
+                         : iteration<PREC_F32>(A, tile_sites, grid, lp_grid, s);
 }
 
-cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                  cudaStream_t s) {
-  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1) return cudaErrorInvalidValue;
-  cudaError_t e = hp == PREC_F16N ? lp_apply<PREC_F16N>(A, tile_sites, grid, s)
-                                  : lp_apply<PREC_F32>(A, tile_sites, grid, s);
-  if (e) return e;
-  return hp == PREC_F16N ? lp_apply_dag<PREC_F16N>(A, tile_sites, grid, s)
-                         : lp_apply_dag<PREC_F32>(A, tile_sites, grid, s);
+cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int lp_grid, cudaStream_t s) {
+  if (lp_grid < 1) return cudaErrorInvalidValue;
+  if (hp == PREC_F16N) {
+    lp_stage<PREC_F16N, 0, false>(A, lp_grid, s);
+    lp_stage<PREC_F16N, 1, false>(A, lp_grid, s);
+    lp_stage<PREC_F16N, 2, false>(A, lp_grid, s);
+    lp_stage<PREC_F16N, 3, false>(A, lp_grid, s);
+  } else {
+    lp_stage<PREC_F32, 0, false>(A, lp_grid, s);
+    lp_stage<PREC_F32, 1, false>(A, lp_grid, s);
+    lp_stage<PREC_F32, 2, false>(A, lp_grid, s);
+    lp_stage<PREC_F32, 3, false>(A, lp_grid, s);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace jqcd
