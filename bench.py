@@ -128,6 +128,43 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def reduce_over_ranks(max_values, sum_values, device):
+    """Across all ranks: elementwise max of max_values and sum of sum_values
+    (lists of floats).  One rank: returned unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(max_values), list(sum_values)
+    tm = torch.tensor(list(max_values), dtype=torch.float64, device=device)
+    ts = torch.tensor(list(sum_values), dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+    return tm.tolist(), ts.tolist()
+
+
+def parse_clock_lines(lines):
+    """nvidia-smi CSV rows (clocks.sm, clocks.max.sm, power, active mask,
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap)."""
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 8:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            mx.append(float(parts[1]))
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[4:8]):
+            if v.lower() == "active":
+                reasons.add(n)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+            "reasons": sorted(reasons)}
+
+
 class ClockSampler:
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -158,24 +195,7 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.splitlines():
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 8:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                mx.append(float(parts[1]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[4:8]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return parse_clock_lines(out.splitlines())
 
 
 def run_reference(args):
@@ -366,14 +386,7 @@ def run_gpu(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     hop_bytes = sum(i["hop_bytes"] for i in infos)
-    ms_max, bytes_sum = ms, hop_bytes
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = t.item()
-        t = torch.tensor([hop_bytes], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t)
-        bytes_sum = t.item()
+    (ms_max,), (bytes_sum,) = reduce_over_ranks([ms], [hop_bytes], "cuda")
     value = bytes_sum / (ms_max * 1e-3) / 1e9
     dw_s = ms / args.steps * 1e-3
 
@@ -403,13 +416,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s, e2e_bytes], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t[:1], op=torch.distributed.ReduceOp.MAX)
-        e2e_s = t[0].item()
-        tb = torch.tensor([e2e_bytes], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tb)
-        e2e_bytes = tb.item()
+    (e2e_s,), (e2e_bytes,) = reduce_over_ranks([e2e_s], [e2e_bytes], "cuda")
     e2e_value = e2e_bytes / e2e_s / 1e9
 
     # dominant kernel alone: double-word hop, plus the other precisions
