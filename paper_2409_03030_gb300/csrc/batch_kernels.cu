@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256) batch_xpay_kernel(const BatchArgs A) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
           const float4 v = r[k * vh];
-          rv[k / 3][k % 3] = cf{v.x, v.z};  // normalised pairs: hi = nearest float
+          rv[k / 3][k % 3] = cf{v.x, v.y};  // normalised pairs: hi = nearest float
         }
         PT<PREC_F32>::store_spinor(Sl.rs, vh, i, rv);
       } else {
@@ -203,10 +203,11 @@ __global__ void __launch_bounds__(256) batch_dw_add_kernel(const BatchArgs A) {
       float4 *x = Sl.x + i;
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const float4 v = x[k * vh];
-        const dw re = dw_add(dw_make(v.x, v.y), dw_make(xv[k / 3][k % 3].re, 0.f));
-        const dw im = dw_add(dw_make(v.z, v.w), dw_make(xv[k / 3][k % 3].im, 0.f));
-        x[k * vh] = make_float4(re.h, re.l, im.h, im.l);
+        dw re, im;
+        dwc_unpack(x[k * vh], re, im);
+        re = dw_add(re, dw_make(xv[k / 3][k % 3].re, 0.f));
+        im = dw_add(im, dw_make(xv[k / 3][k % 3].im, 0.f));
+        x[k * vh] = dwc_pack(re, im);
       }
       float4 *xs = Sl.xs + i;
 #pragma unroll
@@ -281,10 +282,12 @@ __global__ void __launch_bounds__(256) batch_dw_resid_kernel(const BatchArgs A) 
       if (i < vh) {
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
-          const float4 bv = Sl.rhs[k * vh + i], yv = Sl.Adw[k * vh + i];
-          const dw re = dw_add(dw_make(bv.x, bv.y), dw_make(-yv.x, -yv.y));
-          const dw im = dw_add(dw_make(bv.z, bv.w), dw_make(-yv.z, -yv.w));
-          Sl.r[k * vh + i] = make_float4(re.h, re.l, im.h, im.l);
+          dw br, bi, yr, yi;
+          dwc_unpack(Sl.rhs[k * vh + i], br, bi);
+          dwc_unpack(Sl.Adw[k * vh + i], yr, yi);
+          const dw re = dw_add(br, dw_neg(yr));
+          const dw im = dw_add(bi, dw_neg(yi));
+          Sl.r[k * vh + i] = dwc_pack(re, im);
           acc_sq(n2, re);
           acc_sq(n2, im);
         }

@@ -1,7 +1,7 @@
 // Vector kernels and the scalar steps of conjugate gradient.
 //
 // Double-word vectors are handled as flat arrays of float4 = one complex
-// double-word number (re.h, re.l, im.h, im.l).  Vector kernels use a fixed
+// double-word number (re.h, im.h, re.l, im.l).  Vector kernels use a fixed
 // grid with grid-stride loops, so the number of partial sums (and with it the
 // rounding of every reduction) depends only on the vector length.
 #include <cuda_runtime.h>
@@ -23,8 +23,10 @@ unsigned blas_blocks(int64_t n) {
 __device__ __forceinline__ dw lo_dw(float h, float l) { return dw_make(h, l); }
 
 __device__ __forceinline__ void accum_sq4(dwacc &A, float4 v) {
-  acc_sq(A, dw_make(v.x, v.y));
-  acc_sq(A, dw_make(v.z, v.w));
+  dw re, im;
+  dwc_unpack(v, re, im);
+  acc_sq(A, re);
+  acc_sq(A, im);
 }
 
 __global__ void dw_copy_kernel(float4 *__restrict__ d, const float4 *__restrict__ s, int64_t n) {
@@ -39,10 +41,10 @@ __global__ void dw_zero_kernel(float4 *__restrict__ d, int64_t n) {
 
 __global__ void dw_add_kernel(float4 *__restrict__ y, const float4 *__restrict__ x, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 a = y[i], b = x[i];
-    dw re = dw_add(dw_make(a.x, a.y), dw_make(b.x, b.y));
-    dw im = dw_add(dw_make(a.z, a.w), dw_make(b.z, b.w));
-    y[i] = make_float4(re.h, re.l, im.h, im.l);
+    dw ar, ai, br, bi;
+    dwc_unpack(y[i], ar, ai);
+    dwc_unpack(x[i], br, bi);
+    y[i] = dwc_pack(dw_add(ar, br), dw_add(ai, bi));
   }
 }
 
@@ -58,10 +60,12 @@ __global__ void dw_xmy_norm_kernel(float4 *__restrict__ r, const float4 *__restr
                                    const float4 *__restrict__ y, int64_t n, double *partials) {
   dwacc A{0.f, 0.f};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 bv = b[i], yv = y[i];
-    dw re = dw_add(dw_make(bv.x, bv.y), dw_make(-yv.x, -yv.y));
-    dw im = dw_add(dw_make(bv.z, bv.w), dw_make(-yv.z, -yv.w));
-    r[i] = make_float4(re.h, re.l, im.h, im.l);
+    dw br, bi, yr, yi;
+    dwc_unpack(b[i], br, bi);
+    dwc_unpack(y[i], yr, yi);
+    const dw re = dw_add(br, dw_neg(yr));
+    const dw im = dw_add(bi, dw_neg(yi));
+    r[i] = dwc_pack(re, im);
     acc_sq(A, re);
     acc_sq(A, im);
   }
@@ -77,13 +81,17 @@ __global__ void dw_cg_update_kernel(float4 *__restrict__ x, float4 *__restrict__
   const dw mal = dw_neg(al);
   dwacc A{0.f, 0.f};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 xv = x[i], pv = p[i], rv = r[i], av = Ap[i];
-    dw xr = dw_add(dw_make(xv.x, xv.y), dw_mul(al, dw_make(pv.x, pv.y)));
-    dw xi = dw_add(dw_make(xv.z, xv.w), dw_mul(al, dw_make(pv.z, pv.w)));
-    dw rr = dw_add(dw_make(rv.x, rv.y), dw_mul(mal, dw_make(av.x, av.y)));
-    dw ri = dw_add(dw_make(rv.z, rv.w), dw_mul(mal, dw_make(av.z, av.w)));
-    x[i] = make_float4(xr.h, xr.l, xi.h, xi.l);
-    r[i] = make_float4(rr.h, rr.l, ri.h, ri.l);
+    dw x_r, x_i, p_r, p_i, r_r, r_i, a_r, a_i;
+    dwc_unpack(x[i], x_r, x_i);
+    dwc_unpack(p[i], p_r, p_i);
+    dwc_unpack(r[i], r_r, r_i);
+    dwc_unpack(Ap[i], a_r, a_i);
+    const dw xr = dw_add(x_r, dw_mul(al, p_r));
+    const dw xi = dw_add(x_i, dw_mul(al, p_i));
+    const dw rr = dw_add(r_r, dw_mul(mal, a_r));
+    const dw ri = dw_add(r_i, dw_mul(mal, a_i));
+    x[i] = dwc_pack(xr, xi);
+    r[i] = dwc_pack(rr, ri);
     acc_sq(A, rr);
     acc_sq(A, ri);
   }
@@ -96,10 +104,10 @@ __global__ void dw_xpay_kernel(float4 *__restrict__ p, const float4 *__restrict_
   if (S->halt) return;
   const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    float4 pv = p[i], rv = r[i];
-    dw pr = dw_add(dw_make(rv.x, rv.y), dw_mul(be, dw_make(pv.x, pv.y)));
-    dw pi = dw_add(dw_make(rv.z, rv.w), dw_mul(be, dw_make(pv.z, pv.w)));
-    p[i] = make_float4(pr.h, pr.l, pi.h, pi.l);
+    dw p_r, p_i, r_r, r_i;
+    dwc_unpack(p[i], p_r, p_i);
+    dwc_unpack(r[i], r_r, r_i);
+    p[i] = dwc_pack(dw_add(r_r, dw_mul(be, p_r)), dw_add(r_i, dw_mul(be, p_i)));
   }
 }
 

@@ -92,7 +92,7 @@ __global__ void dw_to_f32_kernel(float4 *__restrict__ rs, const float4 *__restri
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = q / vh, i = q % vh;
     const float4 a = r[(2 * j) * vh + i], b = r[(2 * j + 1) * vh + i];
-    rs[q] = make_float4(a.x, a.z, b.x, b.z);  // normalised pairs: hi = nearest float
+    rs[q] = make_float4(a.x, a.y, b.x, b.y);  // normalised pairs: hi = nearest float
   }
 }
 
@@ -102,13 +102,11 @@ __global__ void dw_add_f32_kernel(float4 *__restrict__ x, float4 *__restrict__ x
     const int64_t j = q / vh, i = q % vh;
     const float4 s = xs[q];
     float4 *xa = x + (2 * j) * vh + i, *xb = x + (2 * j + 1) * vh + i;
-    float4 a = *xa, b = *xb;
-    dw ar = dw_add(dw_make(a.x, a.y), dw_make(s.x, 0.f));
-    dw ai = dw_add(dw_make(a.z, a.w), dw_make(s.y, 0.f));
-    dw br = dw_add(dw_make(b.x, b.y), dw_make(s.z, 0.f));
-    dw bi = dw_add(dw_make(b.z, b.w), dw_make(s.w, 0.f));
-    *xa = make_float4(ar.h, ar.l, ai.h, ai.l);
-    *xb = make_float4(br.h, br.l, bi.h, bi.l);
+    dw ar, ai, br, bi;
+    dwc_unpack(*xa, ar, ai);
+    dwc_unpack(*xb, br, bi);
+    *xa = dwc_pack(dw_add(ar, dw_make(s.x, 0.f)), dw_add(ai, dw_make(s.y, 0.f)));
+    *xb = dwc_pack(dw_add(br, dw_make(s.z, 0.f)), dw_add(bi, dw_make(s.w, 0.f)));
     xs[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }

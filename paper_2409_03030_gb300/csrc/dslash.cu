@@ -195,8 +195,7 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_staged_kernel(const HopPar
       cw psi[4][3];
 #pragma unroll
       for (int k = 0; k < 12; ++k) {
-        const float4 v = st[k * kHopThreads];
-        psi[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(v.z, v.w)};
+        dwc_unpack(st[k * kHopThreads], psi[k / 3][k % 3].re, psi[k / 3][k % 3].im);
       }
       const float S = (bwd != DAG) ? 1.f : -1.f;
       cw h[2][3];
@@ -211,8 +210,9 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_staged_kernel(const HopPar
       cw u[3][3];
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
-        const float4 v = st[(12 + k) * kHopThreads];
-        u[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(cs * v.z, cs * v.w)};
+        dw ur, ui;
+        dwc_unpack(st[(12 + k) * kHopThreads], ur, ui);
+        u[k / 3][k % 3] = cw{ur, dw_make(cs * ui.h, cs * ui.l)};
       }
       cw r[2][3];
       matvec2<false>(u, h, r);

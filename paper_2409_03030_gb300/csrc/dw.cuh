@@ -117,6 +117,15 @@ __device__ __forceinline__ void dw_accum_sgn(dw &x, dw v, float s) { x = dw_add_
 // Square-accumulate a*a into (s, c) (for norms).
 __device__ __forceinline__ void acc_sq(dwacc &A, dw a) { acc_mad(A, a, a); }
 
+// A complex double-word number in one 16-byte chunk, laid out
+// (re.h, im.h, re.l, im.l) so that the high and the low halves each form an
+// aligned pair of floats (packed two-lane FP32 arithmetic reads them as is).
+__device__ __forceinline__ void dwc_unpack(float4 v, dw &re, dw &im) {
+  re = dw_make(v.x, v.z);
+  im = dw_make(v.y, v.w);
+}
+__device__ __forceinline__ float4 dwc_pack(dw re, dw im) { return make_float4(re.h, im.h, re.l, im.l); }
+
 __host__ __device__ __forceinline__ float2 dw_split_host(double v) {
   float h = (float)v;
   float l = (float)(v - (double)h);

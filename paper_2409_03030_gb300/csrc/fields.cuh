@@ -21,8 +21,7 @@ template <> struct PT<PREC_DW> {
     const float4 *p = reinterpret_cast<const float4 *>(base) + i;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      float4 v = __ldg(p + k * vh);
-      s[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(v.z, v.w)};
+      dwc_unpack(__ldg(p + k * vh), s[k / 3][k % 3].re, s[k / 3][k % 3].im);
     }
   }
   __device__ static __forceinline__ void store_spinor(void *base, int64_t vh, int64_t i,
@@ -30,9 +29,9 @@ template <> struct PT<PREC_DW> {
     float4 *p = reinterpret_cast<float4 *>(base) + i;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      dw re = dw_norm(s[k / 3][k % 3].re.h, s[k / 3][k % 3].re.l);
-      dw im = dw_norm(s[k / 3][k % 3].im.h, s[k / 3][k % 3].im.l);
-      p[k * vh] = make_float4(re.h, re.l, im.h, im.l);
+      const dw re = dw_norm(s[k / 3][k % 3].re.h, s[k / 3][k % 3].re.l);
+      const dw im = dw_norm(s[k / 3][k % 3].im.h, s[k / 3][k % 3].im.l);
+      p[k * vh] = dwc_pack(re, im);
     }
   }
   // link chunks start at `base` (already offset to parity and direction)
@@ -41,8 +40,7 @@ template <> struct PT<PREC_DW> {
     const float4 *p = reinterpret_cast<const float4 *>(base) + i;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      float4 v = __ldcs(p + k * vh);
-      u[k / 3][k % 3] = cw{dw_make(v.x, v.y), dw_make(v.z, v.w)};
+      dwc_unpack(__ldcs(p + k * vh), u[k / 3][k % 3].re, u[k / 3][k % 3].im);
     }
   }
   __device__ static __forceinline__ void negate_if(C (&h)[2][3], bool neg) {

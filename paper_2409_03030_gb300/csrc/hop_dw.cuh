@@ -156,8 +156,9 @@ __device__ __forceinline__ void dw_hop_site(const float4 *in, const float4 *gaug
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const float4 v = __ldcs(L + (int64_t)(a * sa + b * sb) * vh);
-        u[a][b] = cw{dw_make(v.x, v.y), dw_make(cs * v.z, cs * v.w)};
+        dw ur, ui;
+        dwc_unpack(__ldcs(L + (int64_t)(a * sa + b * sb) * vh), ur, ui);
+        u[a][b] = cw{ur, dw_make(cs * ui.h, cs * ui.l)};
       }
     cw r[2][3];
     matvec2<false>(u, h, r);

@@ -8,13 +8,14 @@
 // which makes each chunk load of a warp one fully coalesced 512-byte access.
 //
 // Spinor layouts (per parity, vh = V/2 sites; component k = 3*spin + colour):
-//   DW   float4[12][vh]  (re.h, re.l, im.h, im.l) of component k
+//   DW   float4[12][vh]  (re.h, im.h, re.l, im.l) of component k
 //   F64  double2[12][vh] (re, im) of component k
 //   F32  float4[6][vh]   components 2j, 2j+1 as (re, im, re, im)
 //   F16N uint4[3][vh]    components 4j..4j+3 as half2 (re, im), scaled by
 //        1/n(site), followed by float n[vh], n = max |real| over the site
 // Gauge layouts (parity p, direction mu, forward link U_mu(x) of the sites x
-// of parity p; element (a,b) is chunk 3a+b):
+// of parity p; element (a,b) is chunk 3a+b; double-word chunks are
+// (re.h, im.h, re.l, im.l) as for spinors):
 //   DW   float4[2][4][9][vh]   F64  double2[2][4][9][vh]
 //   F32  float4[2][4][3][vh]   rows 0 and 1 only (12 reals); row 2 is
 //        recomputed as conj(row0 x row1), exact for SU(3).

@@ -47,7 +47,7 @@ __global__ void gauge_pack_kernel(Geom g, const double *__restrict__ canon, floa
   if (dwo) {
     for (int k = 0; k < 9; ++k) {
       float2 re = split_dev(u[k / 3][k % 3].x), im = split_dev(u[k / 3][k % 3].y);
-      dwo[(blk * 9 + k) * g.vh + cb] = make_float4(re.x, re.y, im.x, im.y);
+      dwo[(blk * 9 + k) * g.vh + cb] = make_float4(re.x, im.x, re.y, im.y);  // (re.h, im.h, re.l, im.l)
     }
   }
   if (f64o) {
@@ -79,7 +79,7 @@ __global__ void spinor_pack_kernel(Geom g, int prec, const double *__restrict__ 
     float4 *o = reinterpret_cast<float4 *>(base);
     for (int k = 0; k < 12; ++k) {
       float2 re = split_dev(v[k].x), im = split_dev(v[k].y);
-      o[k * vh + cb] = make_float4(re.x, re.y, im.x, im.y);
+      o[k * vh + cb] = make_float4(re.x, im.x, re.y, im.y);  // (re.h, im.h, re.l, im.l)
     }
   } else if (prec == PREC_F64) {
     double2 *o = reinterpret_cast<double2 *>(base);
@@ -122,7 +122,7 @@ __global__ void spinor_unpack_kernel(Geom g, int prec, const void *even, const v
     const float4 *o = reinterpret_cast<const float4 *>(base);
     for (int k = 0; k < 12; ++k) {
       float4 q = o[k * vh + cb];
-      v[k] = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+      v[k] = make_double2((double)q.x + (double)q.z, (double)q.y + (double)q.w);
     }
   } else if (prec == PREC_F64) {
     const double2 *o = reinterpret_cast<const double2 *>(base);
