@@ -39,8 +39,8 @@ TOL = 1e-10
 METRIC = "Dslash GB/s vs HBM peak; CG s to 1e-10 mixed vs FP64; serve p50/p99"
 HOP_BYTES = {"dw": 1536, "f64": 1536, "f32": 576, "f16n": 488}  # per output site
 AXPY_BYTES = {"dw": 192, "f64": 192, "f32": 96, "f16n": 52}
-HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "hop_dw.cuh", "fields.cuh", "dw.cuh", "lattice.cuh",
-                      "reduce.cuh"]
+HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "hop_dw.cuh", "hop_dwp.cuh", "hop_lp.cuh", "dw2.cuh",
+                      "fields.cuh", "dw.cuh", "lattice.cuh", "reduce.cuh", "kernels.h"]
 
 
 def parse():
@@ -504,7 +504,7 @@ def run_gpu(args):
             "config": workload_config(),
             "roofline": {"bound": "hbm", "achieved": round(dw_achieved, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(dw_achieved / hbm, 4),
-                         "traffic": traffic, "kernel": "hop_kernel<PREC_DW> (plain hop)",
+                         "traffic": traffic, "kernel": "hop_dwp_kernel (double-word plain hop)",
                          "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",

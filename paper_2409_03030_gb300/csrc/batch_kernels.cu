@@ -10,6 +10,8 @@
 
 #include "batch.h"
 #include "hop_dw.cuh"
+#include "hop_dwp.cuh"
+#include "hop_lp.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -20,41 +22,17 @@ __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
   return A.slots[si].active && !A.S[si].halt;
 }
 
-// One of the eight hops of the low-precision operator for one site; links
-// (rows 0 and 1) through the read-only path, where the blocks of the other
-// right-hand sides on the same sites, running alongside, find them.
-template <int PREC, int MU, bool BWD, bool DAG>
-__device__ __forceinline__ void lp_dir(const void *in, const float4 *gauge, int outp, int64_t vh,
-                                       int64_t idx, int64_t nb, bool neg, cf (&acc)[4][3]) {
-  constexpr int S = (BWD != DAG) ? 1 : -1;
-  cf psi[4][3], h[2][3], r[2][3], u[3][3];
-  PT<PREC>::load_spinor(in, vh, nb, psi);
-  project<MU, S>(psi, h);
-  PT<PREC>::negate_if(h, neg);
-  const float4 *L = gauge + (size_t)(((BWD ? 1 - outp : outp) * 4 + MU) * 3) * vh + (BWD ? nb : idx);
-  PT<PREC>::link_from_chunks(__ldg(L), __ldg(L + vh), __ldg(L + 2 * vh), u);
-  matvec2<BWD>(u, h, r);
-  reconstruct<MU, S>(r, acc);
-}
-
-template <int PREC, int MU, bool DAG>
-__device__ __forceinline__ void lp_mu(const void *in, const float4 *gauge, int outp, const Geom &g,
-                                      int64_t idx, int x, int y, int z, int t, cf (&acc)[4][3]) {
-  bool nf, nbk;
-  const int64_t f = hop_neighbour(g, x, y, z, t, 2 * MU, nf);
-  const int64_t bk = hop_neighbour(g, x, y, z, t, 2 * MU + 1, nbk);
-  lp_dir<PREC, MU, false, DAG>(in, gauge, outp, g.vh, idx, f, nf, acc);
-  lp_dir<PREC, MU, true, DAG>(in, gauge, outp, g.vh, idx, bk, nbk, acc);
-}
-
 // Low-precision hop stages of the batched operator.  Work items are
 // (slot, block of 128 sites); consecutive items are the right-hand sides of
-// one group on the same sites, so their link loads meet in L1/L2.
+// one group on the same sites, so their link loads meet in L2.  The site
+// loop (hop_lp.cuh) prefetches the next hop's neighbour and link into shared
+// memory while the current hop computes.
 // STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t, ||w||^2;  2: t = H^dag_oe w;
 // STAGE 3: Ap = w - kappa^2 H^dag_eo t, then (UPDATE) x_s += alpha p,
 //          r_s -= alpha Ap, ||r_s||^2 without storing Ap.
 template <int PREC, int STAGE, bool UPDATE>
 __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
+  extern __shared__ float4 lsm[];
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
   constexpr bool AXPY = STAGE == 1 || STAGE == 3;
@@ -74,18 +52,8 @@ __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArg
       const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
       const void *xv = STAGE == 1 ? Sl.p : Sl.w;
       void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
-      int x, y, z, t;
-      cb_coords(g, idx, OUTP, x, y, z, t);
       cf acc[4][3];
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) acc[a][c] = cf{0.f, 0.f};
-      const float4 *U = G->gauge_f32;
-      lp_mu<PREC, 0, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
-      lp_mu<PREC, 1, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
-      lp_mu<PREC, 2, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
-      lp_mu<PREC, 3, DAG>(in, U, OUTP, g, idx, x, y, z, t, acc);
+      lp_hop_site<PREC, DAG, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc);
       const int64_t vh = g.vh;
       cf o[4][3];
       if (AXPY) {
@@ -217,50 +185,34 @@ __global__ void __launch_bounds__(256) batch_dw_add_kernel(const BatchArgs A) {
 }
 
 // Double-word Mhat^dag Mhat x in four stages (as the low-precision stages, on
-// x, tdw, wdw, Adw).
+// x, tdw, wdw, Adw) for the slots that asked for a reliable update.  Work
+// items are those of the low-precision stages (slot, kLpThreads sites); the
+// site loop is the packed double-word hop of the single-field kernel.
+static_assert(kLpThreads == kHopThreads, "batched double-word stages reuse the hop staging");
+
 template <int STAGE>
-__global__ void __launch_bounds__(256) batch_dw_hop_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kLpThreads, 3) batch_dw_hop_kernel(const BatchArgs A) {
+  extern __shared__ float4 dsm[];
   if (*A.any_update == 0) return;
-  typedef PT<PREC_DW> T;
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
   constexpr bool AXPY = STAGE == 1 || STAGE == 3;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const int nt = *A.ntiles;
-  for (int ti = blockIdx.x; ti < nt; ti += gridDim.x) {
-    const int2 T2 = A.tiles[ti];
-    const GroupDev *G = A.groups + T2.x;
-    const Geom g = G->g;
-    const int64_t i = (int64_t)T2.y * bd + tid;
-    if (i >= g.vh) continue;
-    for (int s = 0; s < G->nslots; ++s) {
-      const int si = G->slot[s];
-      const SlotDev &Sl = A.slots[si];
-      if (!Sl.active || A.S[si].need_update != 1) continue;
-      const float4 *in = STAGE == 0 ? Sl.x : (STAGE == 2 ? Sl.wdw : Sl.tdw);
-      const float4 *xv = STAGE == 1 ? Sl.x : Sl.wdw;
-      float4 *out = STAGE == 0 || STAGE == 2 ? Sl.tdw : (STAGE == 1 ? Sl.wdw : Sl.Adw);
-      cw acc[4][3];
-      dw_hop_site<DAG>(in, G->gauge_dw, g, OUTP, i, acc);
-      cw o[4][3];
-      const dw k2 = dw_make(Sl.k2_dw.x, Sl.k2_dw.y);
-      if (AXPY) {
-        cw xs[4][3];
-        T::load_spinor(xv, g.vh, i, xs);
-        const dw one = dw_make(1.f, 0.f);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) o[a][c] = T::axpby(one, xs[a][c], k2, acc[a][c]);
-      } else {
-        const dw one = dw_make(1.f, 0.f);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) o[a][c] = T::scale(one, acc[a][c]);
-      }
-      T::store_spinor(out, g.vh, i, o);
-    }
+  const int n = *A.n_lp_tiles;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 W = A.lp_tiles[it];
+    const GroupDev *G = A.groups + (W.x >> 4);
+    const int si = G->slot[W.x & 15];
+    const SlotDev &Sl = A.slots[si];
+    if (!Sl.active || A.S[si].need_update != 1) continue;  // uniform over the block
+    const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
+    if (idx >= G->g.vh) continue;  // no block-wide step follows
+    const float4 *in = STAGE == 0 ? Sl.x : (STAGE == 2 ? Sl.wdw : Sl.tdw);
+    const float4 *xv = STAGE == 1 ? Sl.x : Sl.wdw;
+    float4 *out = STAGE == 0 || STAGE == 2 ? Sl.tdw : (STAGE == 1 ? Sl.wdw : Sl.Adw);
+    p2 acc[4][3];
+    dwp_hop_site<DAG>(dsm, in, G->gauge_dw, G->g, OUTP, idx, acc);
+    dwp_store<AXPY, false>(acc, out, xv, G->g.vh, idx, make_float2(1.f, 0.f),
+                           AXPY ? Sl.k2_dw : make_float2(1.f, 0.f));  // t = H v;  w = v - kappa^2 H t
   }
 }
 
@@ -374,12 +326,20 @@ __global__ void batch_resume_kernel(const BatchArgs A) {
 }
 
 // ---- launchers -------------------------------------------------------------------
-cudaError_t batch_configure() { return cudaSuccess; }
+cudaError_t batch_configure() {
+  const void *k[4] = {(const void *)batch_dw_hop_kernel<0>, (const void *)batch_dw_hop_kernel<1>,
+                      (const void *)batch_dw_hop_kernel<2>, (const void *)batch_dw_hop_kernel<3>};
+  for (const void *f : k) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 template <int PREC, int STAGE, bool UPDATE>
 static void lp_stage(const BatchArgs &A, int lp_grid, cudaStream_t s) {
   note_launch();
-  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, 0, s>>>(A);
+  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
 }
 
 template <int PREC>
@@ -398,13 +358,13 @@ static cudaError_t iteration(const BatchArgs &A, int ts, int grid, int lp_grid, 
   note_launch();
   batch_dw_add_kernel<<<grid, ts, 0, s>>>(A);
   note_launch();
-  batch_dw_hop_kernel<0><<<grid, ts, 0, s>>>(A);
+  batch_dw_hop_kernel<0><<<lp_grid, kLpThreads, kDwpSmem, s>>>(A);
   note_launch();
-  batch_dw_hop_kernel<1><<<grid, ts, 0, s>>>(A);
+  batch_dw_hop_kernel<1><<<lp_grid, kLpThreads, kDwpSmem, s>>>(A);
   note_launch();
-  batch_dw_hop_kernel<2><<<grid, ts, 0, s>>>(A);
+  batch_dw_hop_kernel<2><<<lp_grid, kLpThreads, kDwpSmem, s>>>(A);
   note_launch();
-  batch_dw_hop_kernel<3><<<grid, ts, 0, s>>>(A);
+  batch_dw_hop_kernel<3><<<lp_grid, kLpThreads, kDwpSmem, s>>>(A);
   note_launch();
   batch_dw_resid_kernel<<<grid, ts, 0, s>>>(A);
   note_launch();

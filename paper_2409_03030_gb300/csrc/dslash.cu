@@ -12,8 +12,9 @@
 #include "fields.cuh"
 #include "hop.cuh"
 #include "kernels.h"
-#include "dw2.cuh"
 #include "hop_dw.cuh"
+#include "hop_dwp.cuh"
+#include "hop_lp.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -112,11 +113,54 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
   }
 }
 
+// Low-precision hop with the next hop's neighbour and link prefetched into
+// shared memory (hop_lp.cuh); same epilogue as hop_kernel.
+template <int PREC, bool DAG, bool AXPY, bool NORM>
+__global__ void __launch_bounds__(kHopThreads) hop_lp_kernel(const HopParams P) {
+  typedef PT<PREC> T;
+  extern __shared__ float4 lsm[];
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  dwacc nrm{0.f, 0.f};
+  if (idx < P.g.vh) {
+    cf acc[4][3];
+    lp_hop_site<PREC, DAG, false>(lsm, P.in, reinterpret_cast<const float4 *>(P.gauge), P.g,
+                                  P.out_parity, idx, acc);
+    const float b = (float)P.b;
+    cf o[4][3];
+    if (AXPY) {
+      const float a = (float)P.a;
+      cf xs[4][3];
+      T::load_spinor(P.x, P.g.vh, idx, xs);
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::axpby(a, xs[s][c], b, acc[s][c]);
+    } else {
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[s][c] = T::scale(b, acc[s][c]);
+    }
+    T::store_spinor(P.out, P.g.vh, idx, o);
+    if (NORM) nrm = site_norm2<PREC>(o);
+  }
+  if (NORM) {
+    const double s = block_sum_dw(nrm);
+    if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+  }
+}
+
 template <int PREC, bool DAG, bool AXPY, bool NORM>
 static cudaError_t launch_hop_t(const HopParams &P, cudaStream_t s) {
   const unsigned blocks = hop_blocks(P.g.vh);
   note_launch();
-  hop_kernel<PREC, DAG, AXPY, NORM><<<blocks, kHopThreads, 0, s>>>(P);
+  // FP16: staged (measured faster); FP32: plain loads (its six-chunk stages
+  // cost more occupancy than the prefetch gains); FP64: plain.
+  if (PREC == PREC_F16N)
+    hop_lp_kernel<PREC_F16N, DAG, AXPY, NORM><<<blocks, kHopThreads, lp_stage_smem<PREC_F16N>(), s>>>(P);
+  else
+    hop_kernel<PREC, DAG, AXPY, NORM><<<blocks, kHopThreads, 0, s>>>(P);
   return cudaGetLastError();
 }
 
@@ -251,218 +295,28 @@ __global__ void __launch_bounds__(kHopThreads) hop_dw_staged_kernel(const HopPar
 
 
 // ---------------------------------------------------------------------------
-// Double-word hop in packed two-lane arithmetic: every complex double-word
-// operation runs its real and imaginary lanes in one fma/add/mul.rn.f32x2,
-// halving the instruction issue of the scalar kernel above (which is bound by
-// issue, not by the FP32 datapath).  Same staging, same arithmetic lane by
-// lane: projection and reconstruction by sign-carrying TwoSums, the SU(3)
-// product W h = h.re W + h.im (i W) as compensated sums with broadcast
-// half-spinor multipliers.
+// Double-word hop in packed two-lane arithmetic (hop_dwp.cuh): half the
+// instruction issue of the scalar kernel above, which is bound by issue and
+// not by the FP32 datapath.
 #ifndef JQCD_DW_PACKED
 #define JQCD_DW_PACKED 1
 #endif
-#ifndef JQCD_DWP_STAGE_LINKS
-#define JQCD_DWP_STAGE_LINKS 0
+#ifndef JQCD_DWP_MIN_BLOCKS  // resident blocks per SM the register budget is cut for
+#define JQCD_DWP_MIN_BLOCKS 3
 #endif
-constexpr int kDwpStageChunks = JQCD_DWP_STAGE_LINKS ? 21 : 12;
-constexpr size_t kDwpSmem = 2ull * kDwpStageChunks * kHopThreads * 16;
-
-// Issue the copies of hop d's neighbour spinor (and its link when staged).
-__device__ __forceinline__ void stage_hop_p(float4 *st, const float4 *in, const float4 *gauge,
-                                            int64_t vh, int p, int64_t idx, int d, int64_t nb) {
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) cp_async16(st + k * kHopThreads + tid, in + k * vh + nb, true);
-  if (JQCD_DWP_STAGE_LINKS) {
-    const int mu = d >> 1;
-    const bool bwd = (d & 1) != 0;
-    const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-    const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-        cp_async16(st + (12 + 3 * a + b) * kHopThreads + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
-  }
-}
-
-__device__ __forceinline__ p2 ld_p2(const float4 *p) {
-  const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
-  return p2{v.x, v.y};
-}
-
-template <int MU>
-__device__ __forceinline__ void project_p(const p2 (&psi)[4][3], p2 (&h)[2][3], float S) {
-  const f2 sS = f2_make(S, S), nS = f2_make(-S, -S), sI = f2_make(-S, S), sIm = f2_make(S, -S);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (MU == 0) { h[0][c] = p2_add_sgn(psi[0][c], p2_swap(psi[3][c]), sI); h[1][c] = p2_add_sgn(psi[1][c], p2_swap(psi[2][c]), sI); }
-    if (MU == 1) { h[0][c] = p2_add_sgn(psi[0][c], psi[3][c], nS);          h[1][c] = p2_add_sgn(psi[1][c], psi[2][c], sS); }
-    if (MU == 2) { h[0][c] = p2_add_sgn(psi[0][c], p2_swap(psi[2][c]), sI); h[1][c] = p2_add_sgn(psi[1][c], p2_swap(psi[3][c]), sIm); }
-    if (MU == 3) { h[0][c] = p2_add_sgn(psi[0][c], psi[2][c], sS);          h[1][c] = p2_add_sgn(psi[1][c], psi[3][c], sS); }
-  }
-}
-
-template <int MU>
-__device__ __forceinline__ void reconstruct_p(const p2 (&r)[2][3], p2 (&acc)[4][3], float S) {
-  const f2 sS = f2_make(S, S), nS = f2_make(-S, -S), sI = f2_make(-S, S), sIm = f2_make(S, -S);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    acc[0][c] = p2_add(acc[0][c], r[0][c]);
-    acc[1][c] = p2_add(acc[1][c], r[1][c]);
-    if (MU == 0) { acc[2][c] = p2_add_sgn(acc[2][c], p2_swap(r[1][c]), sIm); acc[3][c] = p2_add_sgn(acc[3][c], p2_swap(r[0][c]), sIm); }
-    if (MU == 1) { acc[2][c] = p2_add_sgn(acc[2][c], r[1][c], sS);          acc[3][c] = p2_add_sgn(acc[3][c], r[0][c], nS); }
-    if (MU == 2) { acc[2][c] = p2_add_sgn(acc[2][c], p2_swap(r[0][c]), sIm); acc[3][c] = p2_add_sgn(acc[3][c], p2_swap(r[1][c]), sI); }
-    if (MU == 3) { acc[2][c] = p2_add_sgn(acc[2][c], r[0][c], sS);          acc[3][c] = p2_add_sgn(acc[3][c], r[1][c], sS); }
-  }
-}
-
-// r[s][a] = sum_b W_ab h[s][b] with W h = h.re W + h.im (i W).
-__device__ __forceinline__ void matvec_p(const p2 (&W)[3][3], const p2 (&h)[2][3], p2 (&r)[2][3]) {
-  const f2 m1 = f2_make(-1.f, 1.f);
-  p2 iW[3][3];  // i W = (-W.im, W.re)
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) iW[a][b] = p2_scale_sgn(p2_swap(W[a][b]), m1);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    mul2 mr[3], mi[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const f2 rh = f2_lo(h[s][b].h), ih = f2_hi(h[s][b].h);
-      mr[b] = mul2{rh, f2_lo(h[s][b].l), f2_neg(rh)};
-      mi[b] = mul2{ih, f2_hi(h[s][b].l), f2_neg(ih)};
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc2 A = acc2_first(mr[0], W[a][0]);
-      acc2_mad(A, mi[0], iW[a][0]);
-#pragma unroll
-      for (int b = 1; b < 3; ++b) {
-        acc2_mad(A, mr[b], W[a][b]);
-        acc2_mad(A, mi[b], iW[a][b]);
-      }
-      r[s][a] = acc2_get(A);
-    }
-  }
-}
 
 template <bool DAG, bool AXPY, bool NORM>
-__global__ void __launch_bounds__(kHopThreads, 3) hop_dwp_kernel(const HopParams P) {
+__global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kernel(const HopParams P) {
   extern __shared__ float4 dsm[];
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const Geom &g = P.g;
-  const int64_t vh = g.vh;
   dwacc nrm{0.f, 0.f};
-  if (idx < vh) {
-    int x, y, z, t;
-    cb_coords(g, idx, P.out_parity, x, y, z, t);
+  if (idx < P.g.vh) {
     p2 acc[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[a][c] = p2{0ull, 0ull};
-    const float4 *in = reinterpret_cast<const float4 *>(P.in);
-    const float4 *gauge = reinterpret_cast<const float4 *>(P.gauge);
-    const int p = P.out_parity;
-    const int tid = threadIdx.x;
-    bool neg_next;
-    int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
-    stage_hop_p(dsm, in, gauge, vh, p, idx, 0, nb);
-    cp_async_commit();
-#pragma unroll 1
-    for (int d = 0; d < 8; ++d) {
-      const bool neg = neg_next;
-      const int mu = d >> 1;
-      const bool bwd = (d & 1) != 0;
-      const f2 cc = f2_make(1.f, bwd ? -1.f : 1.f);  // conjugation of the adjoint link
-      p2 W[3][3];
-      if (!JQCD_DWP_STAGE_LINKS) {  // link straight to registers, ahead of its use
-        const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-        const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) {
-            const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(L + (int64_t)(a * sa + b * sb) * vh));
-            W[a][b] = p2{v.x, v.y};
-          }
-      }
-      if (d < 7) {
-        nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-        stage_hop_p(dsm + ((d + 1) & 1) * kDwpStageChunks * kHopThreads, in, gauge, vh, p, idx, d + 1, nb);
-      }
-      cp_async_commit();
-      cp_async_wait1();
-      const float4 *st = dsm + (d & 1) * kDwpStageChunks * kHopThreads + tid;
-      p2 psi[4][3];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(st + k * kHopThreads);
-      const float S = (bwd != DAG) ? 1.f : -1.f;
-      p2 h[2][3];
-      switch (mu) {
-        case 0: project_p<0>(psi, h, S); break;
-        case 1: project_p<1>(psi, h, S); break;
-        case 2: project_p<2>(psi, h, S); break;
-        default: project_p<3>(psi, h, S);
-      }
-      if (neg) {
-        const f2 mm = f2_make(-1.f, -1.f);
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) h[a][c] = p2_scale_sgn(h[a][c], mm);
-      }
-#pragma unroll
-      for (int k = 0; k < 9; ++k)
-        W[k / 3][k % 3] = p2_scale_sgn(JQCD_DWP_STAGE_LINKS ? ld_p2(st + (12 + k) * kHopThreads) : W[k / 3][k % 3], cc);
-      p2 r[2][3];
-      matvec_p(W, h, r);
-      switch (mu) {
-        case 0: reconstruct_p<0>(r, acc, S); break;
-        case 1: reconstruct_p<1>(r, acc, S); break;
-        case 2: reconstruct_p<2>(r, acc, S); break;
-        default: reconstruct_p<3>(r, acc, S);
-      }
-    }
-    // out = a x + b acc
-    const f2 bh = f2_make(P.b_split.x, P.b_split.x);
-    const mul2 Bm{bh, f2_make(P.b_split.y, P.b_split.y), f2_neg(bh)};
-    const f2 ah = f2_make(P.a_split.x, P.a_split.x);
-    const mul2 Am{ah, f2_make(P.a_split.y, P.a_split.y), f2_neg(ah)};
-    acc2 nq{0ull, 0ull};
-    ulonglong2 *__restrict__ o = reinterpret_cast<ulonglong2 *>(P.out) + idx;
-    p2 xs[12];
-    if (AXPY) {  // all loads before the first store
-      const ulonglong2 *__restrict__ xp = reinterpret_cast<const ulonglong2 *>(P.x) + idx;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const ulonglong2 v = __ldg(xp + k * vh);
-        xs[k] = p2{v.x, v.y};
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      acc2 R = acc2_first(Bm, p2_norm(acc[k / 3][k % 3]));
-      if (AXPY) acc2_mad(R, Am, xs[k]);
-      const p2 q = p2_norm(acc2_get(R));
-      o[k * vh] = make_ulonglong2(q.h, q.l);
-      if (NORM) {
-        const mul2 Q{q.h, q.l, f2_neg(q.h)};
-        if (k == 0) nq = acc2_first(Q, q);
-        else acc2_mad(nq, Q, q);
-      }
-    }
-    if (NORM) {
-      float s0, s1, c0, c1;
-      f2_split(nq.s, s0, s1);
-      f2_split(nq.c, c0, c1);
-      float s, e;
-      two_sum(s0, s1, s, e);
-      nrm = dwacc{s, __fadd_rn(__fadd_rn(c0, c1), e)};
-    }
+    dwp_hop_site<DAG>(dsm, reinterpret_cast<const float4 *>(P.in),
+                      reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
+    nrm = dwp_store<AXPY, NORM>(acc, reinterpret_cast<float4 *>(P.out),
+                                reinterpret_cast<const float4 *>(P.x), P.g.vh, idx, P.a_split, P.b_split);
   }
   if (NORM) {
     const double s = block_sum_dw(nrm);
