@@ -180,7 +180,7 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
 }
 
 constexpr int kDwStageChunks = 21;  // 12 spinor + 9 link chunks of 16 bytes
-constexpr size_t kDwStagedSmem = 2ull * kDwStageChunks * kHopThreads * 16;
+[[maybe_unused]] constexpr size_t kDwStagedSmem = 2ull * kDwStageChunks * kHopThreads * 16;
 
 // Issue the copies of hop d's neighbour spinor and link (in [a][b] order of
 // the matrix W the hop multiplies) into one stage, chunk-major [k][thread].
