@@ -93,27 +93,28 @@ __device__ __forceinline__ p2 p2_scale_sgn(p2 a, f2 sg) { return p2{f2_mul(sg, a
 struct acc2 {
   f2 s, c;
 };
-// A = multiplier (h, l and nh = -h), B = multiplicand.
+// A = multiplier (h, l), B = multiplicand.  The error of the high product
+// is e = fma(A.h, B.h, -p), exact; the negation is a sign flip of p.
 struct mul2 {
-  f2 h, l, nh;
+  f2 h, l;
 };
 __device__ __forceinline__ acc2 acc2_first(const mul2 &A, p2 B) {
   acc2 R;
   R.s = f2_mul(A.h, B.h);
-  const f2 ne = f2_fma(A.nh, B.h, R.s);  // = -(A.h*B.h - s), exact
-  f2 c = f2_fma(A.h, B.l, f2_neg(ne));
+  const f2 e = f2_fma(A.h, B.h, f2_neg(R.s));  // A.h*B.h - s, exact
+  const f2 c = f2_fma(A.h, B.l, e);
   R.c = f2_fma(A.l, B.h, c);
   return R;
 }
 __device__ __forceinline__ void acc2_mad(acc2 &R, const mul2 &A, p2 B) {
   const f2 p = f2_mul(A.h, B.h);
-  const f2 ne = f2_fma(A.nh, B.h, p);
+  const f2 e = f2_fma(A.h, B.h, f2_neg(p));
   f2 c = f2_fma(A.h, B.l, R.c);
   c = f2_fma(A.l, B.h, c);
   f2 s, t;
   two_sum2(R.s, p, s, t);
   R.s = s;
-  R.c = f2_add(f2_sub(c, ne), t);
+  R.c = f2_add(f2_add(c, e), t);
 }
 __device__ __forceinline__ p2 acc2_get(const acc2 &R) { return p2{R.s, R.c}; }
 

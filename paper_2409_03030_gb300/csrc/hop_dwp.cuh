@@ -3,7 +3,7 @@
 //
 // Every complex double-word operation runs its real and imaginary lanes in
 // one fma/add/mul.rn.f32x2: projection and reconstruction by sign-carrying
-// TwoSums, the SU(3) product W h = h.re W + h.im (i W) as compensated sums
+// TwoSums, the SU(3) product W h = h.re W + i (h.im W) as compensated sums
 // with broadcast half-spinor multipliers.  (Folding the link's signs into the
 // multipliers instead saves FP32 multiplies but costs registers: the kernel
 // then spills and runs slower on sm_103.)
@@ -46,51 +46,57 @@ __device__ __forceinline__ void project_p(const p2 (&psi)[4][3], p2 (&h)[2][3], 
   }
 }
 
-// Spread the two-spin result back onto four spins (lower spins from the
-// projector's structure).
-template <int MU>
-__device__ __forceinline__ void reconstruct_p(const p2 (&r)[2][3], p2 (&acc)[4][3], float S) {
-  const f2 sS = f2_make(S, S), nS = f2_make(-S, -S), sI = f2_make(-S, S), sIm = f2_make(S, -S);
+// r[a] = sum_b W_ab h[b] = A + i B with A = sum_b h.re W_ab and
+// B = sum_b h.im W_ab for one spin of the half-spinor: two compensated sums
+// of exact products against the same link lanes (half-spinor components
+// broadcast to both lanes), joined by one TwoSum with B's lanes swapped and
+// its new real lane negated.  No copy of i W is formed, which keeps 36
+// registers free.
+__device__ __forceinline__ void matvec_half_p(const p2 (&W)[3][3], const p2 (&h)[3], p2 (&r)[3]) {
+  mul2 mr[3], mi[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    acc[0][c] = p2_add(acc[0][c], r[0][c]);
-    acc[1][c] = p2_add(acc[1][c], r[1][c]);
-    if (MU == 0) { acc[2][c] = p2_add_sgn(acc[2][c], p2_swap(r[1][c]), sIm); acc[3][c] = p2_add_sgn(acc[3][c], p2_swap(r[0][c]), sIm); }
-    if (MU == 1) { acc[2][c] = p2_add_sgn(acc[2][c], r[1][c], sS);          acc[3][c] = p2_add_sgn(acc[3][c], r[0][c], nS); }
-    if (MU == 2) { acc[2][c] = p2_add_sgn(acc[2][c], p2_swap(r[0][c]), sIm); acc[3][c] = p2_add_sgn(acc[3][c], p2_swap(r[1][c]), sI); }
-    if (MU == 3) { acc[2][c] = p2_add_sgn(acc[2][c], r[0][c], sS);          acc[3][c] = p2_add_sgn(acc[3][c], r[1][c], sS); }
+  for (int b = 0; b < 3; ++b) {
+    mr[b] = mul2{f2_lo(h[b].h), f2_lo(h[b].l)};
+    mi[b] = mul2{f2_hi(h[b].h), f2_hi(h[b].l)};
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    acc2 A = acc2_first(mr[0], W[a][0]);
+    acc2 B = acc2_first(mi[0], W[a][0]);
+#pragma unroll
+    for (int b = 1; b < 3; ++b) {
+      acc2_mad(A, mr[b], W[a][b]);
+      acc2_mad(B, mi[b], W[a][b]);
+    }
+    // i B = (-B.im, B.re): swap the lanes, flip the sign of lane 0
+    constexpr f2 kLane0 = 0x0000000080000000ull;
+    r[a] = p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0});
   }
 }
 
-// r[s][a] = sum_b W_ab h[s][b] with W h = h.re W + h.im (i W): compensated
-// sums of exact products, the half-spinor components broadcast to both lanes.
-__device__ __forceinline__ void matvec_p(const p2 (&W)[3][3], const p2 (&h)[2][3], p2 (&r)[2][3]) {
-  const f2 m1 = f2_make(-1.f, 1.f);
-  p2 iW[3][3];  // i W = (-W.im, W.re)
+// Reconstruction of one spin s of the two-spin result: out_s += r and the
+// lower spin that (1 + S gamma_mu) ties to s gets the phase times r.
+template <int MU, int SP>
+__device__ __forceinline__ void reconstruct_half_p(const p2 (&r)[3], p2 (&acc)[4][3], float S) {
+  const f2 sS = f2_make(S, S), nS = f2_make(-S, -S), sI = f2_make(-S, S), sIm = f2_make(S, -S);
+  constexpr int L = (MU <= 1) ? 3 - SP : 2 + SP;  // lower spin fed by spin SP
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) iW[a][b] = p2_scale_sgn(p2_swap(W[a][b]), m1);
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    mul2 mr[3], mi[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const f2 rh = f2_lo(h[s][b].h), ih = f2_hi(h[s][b].h);
-      mr[b] = mul2{rh, f2_lo(h[s][b].l), f2_neg(rh)};
-      mi[b] = mul2{ih, f2_hi(h[s][b].l), f2_neg(ih)};
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      acc2 A = acc2_first(mr[0], W[a][0]);
-      acc2_mad(A, mi[0], iW[a][0]);
-#pragma unroll
-      for (int b = 1; b < 3; ++b) {
-        acc2_mad(A, mr[b], W[a][b]);
-        acc2_mad(A, mi[b], iW[a][b]);
-      }
-      r[s][a] = acc2_get(A);
-    }
+  for (int c = 0; c < 3; ++c) {
+    acc[SP][c] = p2_add(acc[SP][c], r[c]);
+    if (MU == 0) acc[L][c] = p2_add_sgn(acc[L][c], p2_swap(r[c]), sIm);
+    if (MU == 1) acc[L][c] = p2_add_sgn(acc[L][c], r[c], SP == 0 ? nS : sS);
+    if (MU == 2) acc[L][c] = p2_add_sgn(acc[L][c], p2_swap(r[c]), SP == 0 ? sIm : sI);
+    if (MU == 3) acc[L][c] = p2_add_sgn(acc[L][c], r[c], sS);
+  }
+}
+
+template <int SP>
+__device__ __forceinline__ void reconstruct_half_mu(int mu, const p2 (&r)[3], p2 (&acc)[4][3], float S) {
+  switch (mu) {
+    case 0: reconstruct_half_p<0, SP>(r, acc, S); break;
+    case 1: reconstruct_half_p<1, SP>(r, acc, S); break;
+    case 2: reconstruct_half_p<2, SP>(r, acc, S); break;
+    default: reconstruct_half_p<3, SP>(r, acc, S);
   }
 }
 
@@ -158,13 +164,12 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
-    p2 r[2][3];
-    matvec_p(W, h, r);
-    switch (mu) {
-      case 0: reconstruct_p<0>(r, acc, S); break;
-      case 1: reconstruct_p<1>(r, acc, S); break;
-      case 2: reconstruct_p<2>(r, acc, S); break;
-      default: reconstruct_p<3>(r, acc, S);
+    {  // spin 0 of the half-spinor, then spin 1: one three-colour result live
+      p2 r[3];
+      matvec_half_p(W, h[0], r);
+      reconstruct_half_mu<0>(mu, r, acc, S);
+      matvec_half_p(W, h[1], r);
+      reconstruct_half_mu<1>(mu, r, acc, S);
     }
   }
 }
@@ -176,9 +181,9 @@ __device__ __forceinline__ dwacc dwp_store(const p2 (&acc)[4][3], float4 *out_ba
                                            const float4 *x_base, int64_t vh, int64_t idx,
                                            float2 a_split, float2 b_split) {
   const f2 bh = f2_make(b_split.x, b_split.x);
-  const mul2 Bm{bh, f2_make(b_split.y, b_split.y), f2_neg(bh)};
+  const mul2 Bm{bh, f2_make(b_split.y, b_split.y)};
   const f2 ah = f2_make(a_split.x, a_split.x);
-  const mul2 Am{ah, f2_make(a_split.y, a_split.y), f2_neg(ah)};
+  const mul2 Am{ah, f2_make(a_split.y, a_split.y)};
   acc2 nq{0ull, 0ull};
   ulonglong2 *__restrict__ o = reinterpret_cast<ulonglong2 *>(out_base) + idx;
   p2 xs[12];
@@ -197,7 +202,7 @@ __device__ __forceinline__ dwacc dwp_store(const p2 (&acc)[4][3], float4 *out_ba
     const p2 q = p2_norm(acc2_get(R));
     o[k * vh] = make_ulonglong2(q.h, q.l);
     if (NORM) {
-      const mul2 Q{q.h, q.l, f2_neg(q.h)};
+      const mul2 Q{q.h, q.l};
       if (k == 0) nq = acc2_first(Q, q);
       else acc2_mad(nq, Q, q);
     }
