@@ -12,7 +12,10 @@ in the timed solves (1536 B per output site, +192 B when the hop also reads
 an axpy operand) divided by the wall time of the solves, summed over ranks.
 e2e   = the same quantity through jqcd_cg_solve with host buffers in pinned
 memory (copy of b in, copy of x out, inside the timed region).
-roofline = the double-word hop kernel timed alone on the same lattice.
+roofline = the double-word hop kernel timed alone on the same lattice.  It is
+bound by the FP32 datapath (error-free double-word arithmetic), so the
+roofline is its FP32 lane operations per second against SMs x 128 lanes x
+clock; its HBM fraction (the metric's "Dslash GB/s vs HBM peak") rides along.
 cpu_baseline / --impl reference = the FP64 CPU oracle on host cores.
 
 Multi-GPU (torchrun): each rank solves its own replica (independent problems,
@@ -126,6 +129,29 @@ def peaks():
             d = json.load(fh)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+# FP32 lane operations (add, mul or fma, each on one lane) per output site of
+# the plain double-word hop, counted from its arithmetic: per hop, projection
+# 6 x 9, link conjugation 9 x 2, mat-vec 2 x 3 x (2 x 28 + 8), reconstruction
+# 2 x 3 x 17 packed two-lane operations; epilogue 12 x 10; times 2 lanes.
+DW_HOP_LANE_OPS = 2 * (8 * (6 * 9 + 9 * 2 + 2 * 3 * (2 * 28 + 8) + 2 * 3 * 17) + 12 * 10)
+NOMINAL_HBM_GBS = 7900.0
+
+
+def alu_peak_tops(device=0):
+    """FP32 lane operations per second of the GPU: SMs x 128 FP32 lanes x
+    the maximum SM clock (MEASURED_PEAKS.json, else the device's own)."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    mhz = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            mhz = json.load(fh).get("sm_max_mhz")
+    if not mhz:
+        mhz = getattr(props, "clock_rate", 2070000) / 1000.0
+    return props.multi_processor_count * 128 * float(mhz) * 1e6 / 1e12
 
 
 def reduce_over_ranks(max_values, sum_values, device):
@@ -440,6 +466,8 @@ def run_gpu(args):
                ("f16n", jqcd.PREC_F16N)]}
     hbm, peak_kind = peaks()
     dw_achieved = vh * HOP_BYTES["dw"] / (hop_ms["dw"] * 1e-3) / 1e9
+    alu_achieved = vh * DW_HOP_LANE_OPS / (hop_ms["dw"] * 1e-3) / 1e12
+    alu_peak = alu_peak_tops(local)
     traffic = profiled_traffic()
 
     # CG to 1e-10: double-word vs mixed precision, on the workload lattice and
@@ -502,10 +530,15 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32x2 (double-word, FP64-class)", "data": "synthetic",
             "config": workload_config(),
-            "roofline": {"bound": "hbm", "achieved": round(dw_achieved, 1), "peak": hbm,
-                         "unit": "GB/s", "frac": round(dw_achieved / hbm, 4),
+            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 2), "peak": round(alu_peak, 2),
+                         "unit": "Tops/s (FP32 lane operations)", "frac": round(alu_achieved / alu_peak, 4),
                          "traffic": traffic, "kernel": "hop_dwp_kernel (double-word plain hop)",
-                         "peak_kind": f"{peak_kind} copy bandwidth (burst)"},
+                         "ops_per_site": DW_HOP_LANE_OPS,
+                         "peak_kind": "SMs x 128 FP32 lanes x maximum SM clock",
+                         "hbm": {"achieved": round(dw_achieved, 1), "peak": hbm, "unit": "GB/s",
+                                 "frac": round(dw_achieved / hbm, 4),
+                                 "frac_nominal": round(dw_achieved / NOMINAL_HBM_GBS, 4),
+                                 "peak_kind": f"{peak_kind} copy bandwidth (burst); nominal 7.9 TB/s"}},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},
