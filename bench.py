@@ -80,19 +80,22 @@ def sample_description(iters):
             f"({iters + 2} applications of Mhat^dag Mhat incl. start and true residual)")
 
 
-def time_oracle_cg(U, b, iters):
-    """Oracle CG run for `iters` iterations; returns (GB/s of hop bytes, seconds, threads)."""
-    import numpy as np
+def time_oracle_cg(U, b, iters, threads=0):
+    """Oracle CG run for `iters` iterations on `threads` threads (0: all it
+    uses by default); returns (GB/s of hop bytes, seconds, threads used)."""
     import oracle
     rhs = oracle.zero_parity(DIMS, b, 1)
-    t0 = time.perf_counter()
-    oracle.cg(DIMS, U, rhs, KAPPA, eo=True, tol=1e-30, maxiter=iters)
-    dt = time.perf_counter() - t0
+    before = oracle.set_threads(0)
+    used = oracle.set_threads(threads) if threads > 0 else before
+    try:
+        t0 = time.perf_counter()
+        oracle.cg(DIMS, U, rhs, KAPPA, eo=True, tol=1e-30, maxiter=iters)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(before)
     vh = vol(DIMS) // 2
     hop_bytes = (iters + 2) * vh * (4 * 1536 + 2 * 192)
-    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    del np
-    return hop_bytes / dt / 1e9, dt, threads
+    return hop_bytes / dt / 1e9, dt, used
 
 
 def kernel_hash():
@@ -446,24 +449,38 @@ def run_gpu(args):
     e2e_value = e2e_bytes / e2e_s / 1e9
 
     # dominant kernel alone: double-word hop, plus the other precisions
-    def time_hop(prec, n=40):
+    def time_hop(prec, n=40, gg=None, src=None):
+        gg = g if gg is None else gg
+        src = b if src is None else src
         with torch.cuda.stream(stream):
-            pe, po = g.pack(b, prec, stream=stream)
-            out = g.empty(prec)
+            pe, po = gg.pack(src, prec, stream=stream)
+            out = gg.empty(prec)
         for _ in range(5):
-            g.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
+            gg.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
         stream.synchronize()
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(n):
-            g.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
+            gg.dslash_eo(prec, 0, 0, po, None, out, stream=stream)
         a1.record(stream)
         stream.synchronize()
         return a0.elapsed_time(a1) / n
 
-    hop_ms = {name: time_hop(code) for name, code in
-              [("dw", jqcd.PREC_DW), ("f64", jqcd.PREC_F64), ("f32", jqcd.PREC_F32),
-               ("f16n", jqcd.PREC_F16N)]}
+    precs = [("dw", jqcd.PREC_DW), ("f64", jqcd.PREC_F64), ("f32", jqcd.PREC_F32),
+             ("f16n", jqcd.PREC_F16N)]
+
+    def hop_sweep(gg, dims, src):
+        vhs = vol(dims) // 2
+        return {name: round(vhs * HOP_BYTES[name] / (time_hop(code, gg=gg, src=src) * 1e-3) / 1e9, 1)
+                for name, code in precs}
+
+    hop_ms = {name: time_hop(code) for name, code in precs}
+    sweep = {"x".join(map(str, DIMS)): {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
+                                        for k, v in hop_ms.items()}}
+    d16 = (16, 16, 16, 16)
+    g16 = ctx.gauge_upload(d16, synth.gauge(d16, "expi", eps=EPS, seed=21))
+    sweep["16x16x16x16 (L2-resident)"] = hop_sweep(g16, d16, synth.gaussian_spinor(d16, seed=22))
+    g16.free()
     hbm, peak_kind = peaks()
     dw_achieved = vh * HOP_BYTES["dw"] / (hop_ms["dw"] * 1e-3) / 1e9
     alu_achieved = vh * DW_HOP_LANE_OPS / (hop_ms["dw"] * 1e-3) / 1e12
@@ -509,6 +526,7 @@ def run_gpu(args):
             b2e, b2o = g2.pack(synth.gaussian_spinor(d2, seed=12), jqcd.PREC_DW, stream=stream)
         stream.synchronize()
         cg_c2 = cg_table(g2, b2e, b2o, 0.122, 3)
+        sweep["32x32x32x64"] = hop_sweep(g2, d2, synth.gaussian_spinor(d2, seed=12))
         cg_c2["workload"] = "32^3x64, exp(i*0.4*H) links, kappa 0.122, even-odd, tol 1e-10"
         g2.free()
 
@@ -520,8 +538,13 @@ def run_gpu(args):
         _, dt1, _ = time_oracle_cg(U, b, 1)  # calibrate: ~10 s sample
         iters = int(min(30, max(1, round(10.0 / max(dt1 / 3.0, 1e-3)) - 2)))
         v, dt, threads = time_oracle_cg(U, b, iters)
+        v1, dt1s, _ = time_oracle_cg(U, b, 1, threads=1)  # one thread, one iteration
         cpu = {"value": round(v, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
-               "sample": sample_description(iters) + f", {dt:.1f} s"}
+               "sample": sample_description(iters) + f", {dt:.1f} s",
+               "single_thread": {"value": round(v1, 3), "unit": "GB/s", "cores": 1,
+                                 "sample": sample_description(1) + f", {dt1s:.1f} s"},
+               "gpu_speedup": {"vs_all_cores": round(value / v, 1),
+                               "vs_one_core": round(value / v1, 1)}}
 
     if rank == 0:
         line = {
@@ -550,6 +573,7 @@ def run_gpu(args):
                    "modes_24x24x24x48": cg_work, "modes_32x32x32x64": cg_c2},
             "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
                            for k, v in hop_ms.items()},
+            "dslash_sweep_gbs": sweep,
             "batch": batch,
             "serve": serve,
         }

@@ -63,6 +63,8 @@ def _configure(lib):
     lib.jo_solve.argtypes = [ip, c_int, c_double, dp, c_int, dp, dp, c_double, c_int,
                              ip, dp, dp]
     lib.jo_zero_parity.argtypes = [ip, dp, c_int]
+    lib.jo_set_threads.argtypes = [c_int]
+    lib.jo_set_threads.restype = c_int
     for name in ("jo_hop", "jo_dirac", "jo_hop_sites", "jo_schur", "jo_normal_apply",
                  "jo_cg", "jo_solve", "jo_zero_parity"):
         getattr(lib, name).restype = c_int
@@ -188,6 +190,11 @@ def zero_parity(dims, psi, parity):
     out = np.array(psi, dtype=np.complex128, order="C")
     _check(_load().jo_zero_parity(cd, _p(out), int(parity)), "jo_zero_parity")
     return out
+
+
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's site loop (n <= 0: unchanged); returns the count in force."""
+    return int(_load().jo_set_threads(int(n)))
 
 
 def parity_mask(dims) -> np.ndarray:

@@ -443,3 +443,19 @@ int jo_zero_parity(const int dims[4], double *psi, int parity) {
   zero_parity(&L, psi, parity);
   return 0;
 }
+
+/* Threads of the site loop (OpenMP builds; returns the count now in force,
+ * 1 without OpenMP).  n <= 0 leaves the setting unchanged.  Used to time the
+ * oracle single-threaded next to the all-core run; no arithmetic changes. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int jo_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
