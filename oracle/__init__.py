@@ -64,6 +64,8 @@ def _configure(lib):
                              ip, dp, dp]
     lib.jo_zero_parity.argtypes = [ip, dp, c_int]
     lib.jo_set_threads.argtypes = [c_int]
+    lib.jo_fermi_force.argtypes = [ip, c_int, c_double, dp, dp, dp, dp]
+    lib.jo_fermi_force.restype = c_int
     lib.jo_set_threads.restype = c_int
     for name in ("jo_hop", "jo_dirac", "jo_hop_sites", "jo_schur", "jo_normal_apply",
                  "jo_cg", "jo_solve", "jo_zero_parity"):
@@ -190,6 +192,33 @@ def zero_parity(dims, psi, parity):
     out = np.array(psi, dtype=np.complex128, order="C")
     _check(_load().jo_zero_parity(cd, _p(out), int(parity)), "jo_zero_parity")
     return out
+
+
+def fermi_force_xy(dims, U, X, Y, kappa, t_antiperiodic=True):
+    """U_mu(x) dS/dU_mu(x) for all links from X = (D^dag D)^-1 eta and Y = D X
+    (convention dS = Re Tr[(dS/dU) dU]); canonical link layout like U."""
+    d, cd = _dims(dims)
+    out = np.zeros_like(U)
+    _check(_load().jo_fermi_force(cd, int(t_antiperiodic), float(kappa), _p(U), _p(X), _p(Y),
+                                  _p(out)), "jo_fermi_force")
+    return out
+
+
+def fermi_action(dims, U, eta, kappa, tol=1e-12, t_antiperiodic=True):
+    """S = eta^dag (D^dag D)^-1 eta (paper: evaluate_FermiAction) by textbook CG
+    on D^dag D.  Returns (S, X) with X = (D^dag D)^-1 eta."""
+    X, iters, rel_res, ok = cg(dims, U, eta, kappa, eo=False, tol=tol, maxiter=100000,
+                               t_antiperiodic=t_antiperiodic)
+    if not ok:
+        raise RuntimeError("oracle CG did not converge")
+    return float(np.vdot(eta, X).real), X
+
+
+def fermi_force(dims, U, eta, kappa, tol=1e-12, t_antiperiodic=True):
+    """(S, U dS/dU) of S = eta^dag (D^dag D)^-1 eta (paper: calc_UdSfdU)."""
+    S, X = fermi_action(dims, U, eta, kappa, tol, t_antiperiodic)
+    Y = dirac(dims, U, X, kappa, t_antiperiodic=t_antiperiodic)
+    return S, fermi_force_xy(dims, U, X, Y, kappa, t_antiperiodic)
 
 
 def set_threads(n: int = 0) -> int:

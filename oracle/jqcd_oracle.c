@@ -459,3 +459,66 @@ int jo_set_threads(int n) {
   return 1;
 #endif
 }
+
+/* Derivative of the two-flavour Wilson fermion action
+ *   S = eta^dag (D^dag D)^{-1} eta          (paper: evaluate_FermiAction)
+ * with respect to every link (paper: calc_UdSfdU, "U dSf/dU").
+ *
+ * Given X = (D^dag D)^{-1} eta and Y = D X, a change dU of the links gives
+ *   dS = -X^dag d(D^dag D) X = -2 Re(Y^dag dD X) = 2 kappa Re(Y^dag dH X),
+ * and U_mu(x) enters H twice: (1 - gamma_mu) U_mu(x) psi(x+mu) at site x and
+ * (1 + gamma_mu) U_mu(x)^dag psi(x) at site x+mu, both times the boundary sign
+ * s (-1 for a link crossing the antiperiodic time boundary).  Hence, with the
+ * convention dS = Re Tr[(dS/dU) dU] for every complex 3x3 variation dU,
+ *   dS/dU_mu(x) = 2 kappa s (A + B^dag),
+ *   A_{ba} = sum_{alpha,beta} (1 - gamma_mu)_{alpha beta} X_{beta b}(x+mu) conj(Y_{alpha a}(x)),
+ *   B_{ba} = sum_{alpha,beta} (1 + gamma_mu)_{alpha beta} X_{beta b}(x)    conj(Y_{alpha a}(x+mu)),
+ * and out = U_mu(x) dS/dU_mu(x) in the canonical link layout.  For the
+ * variation U -> exp(eps w) U (w in su(3)) this gives dS/deps = Re Tr[out w].
+ * Written from the definition: explicit 4x4 gamma matrices, no spin projection.
+ */
+int jo_fermi_force(const int dims[4], int tanti, double kappa, const double *U, const double *X,
+                   const double *Y, double *out) {
+  lat_t L;
+  if (lat_init(&L, dims, tanti) || !U || !X || !Y || !out) return -1;
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < L.V; ++x) {
+    int64_t c[4];
+    site_coords(&L, x, c);
+    for (int mu = 0; mu < 4; ++mu) {
+      int64_t nc[4] = {c[0], c[1], c[2], c[3]};
+      double s = 1.0;
+      nc[mu] = c[mu] + 1;
+      if (nc[mu] == L.n[mu]) {
+        nc[mu] = 0;
+        if (mu == 3 && L.tanti) s = -1.0;
+      }
+      const int64_t xp = site_index(&L, nc);
+      cplx M[3][3];  /* M[b][a] = A_{ba} + conj(B_{ab}) */
+      for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+          cplx acc = cm(0, 0);
+          for (int alpha = 0; alpha < 4; ++alpha)
+            for (int beta = 0; beta < 4; ++beta) {
+              const double d = (alpha == beta) ? 1.0 : 0.0;
+              const cplx gm = cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */
+              const cplx gp = cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);   /* 1 + gamma */
+              /* A_{ba} term */
+              acc = cadd(acc, cmul(gm, cmul(spin_ld(&L, X, xp, b, beta),
+                                             cconj(spin_ld(&L, Y, x, a, alpha)))));
+              /* conj(B_{ab}) term: B_{ab} = (1+gamma)_{alpha beta} X_{beta a}(x) conj(Y_{alpha b}(x+mu)) */
+              acc = cadd(acc, cconj(cmul(gp, cmul(spin_ld(&L, X, x, a, beta),
+                                                   cconj(spin_ld(&L, Y, xp, b, alpha))))));
+            }
+          M[b][a] = acc;
+        }
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) {
+          cplx acc = cm(0, 0);
+          for (int b = 0; b < 3; ++b) acc = cadd(acc, cmul(link(&L, U, mu, x, i, b), M[b][a]));
+          st(out, i + 3 * (a + 3 * (x + L.V * mu)), cscale(acc, 2.0 * kappa * s));
+        }
+    }
+  }
+  return 0;
+}

@@ -7,6 +7,7 @@ import subprocess
 import pytest
 
 import oracle
+import test_oracle_force as force_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "jqcd_oracle.c")
@@ -32,6 +33,13 @@ MUTATIONS = {
                        "hop_axpy(&L, U, b, t, 1, 0, 0.0, -kappa);"),
     "eo_rhs_without_dagger": ("schur(&L, kappa, U, t, rhs, -1, t2);",
                               "schur(&L, kappa, U, t, rhs, 1, t2);"),
+    "force_projectors_swapped": ("cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */",
+                                 "cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);  /* 1 - gamma */"),
+    "force_no_boundary_sign": ("if (mu == 3 && L.tanti) s = -1.0;", ""),
+    "force_second_term_not_conjugated": ("acc = cadd(acc, cconj(cmul(gp,", "acc = cadd(acc, (cmul(gp,"),
+    "force_factor_two_dropped": ("cscale(acc, 2.0 * kappa * s)", "cscale(acc, kappa * s)"),
+    "force_link_on_the_right": ("cmul(link(&L, U, mu, x, i, b), M[b][a])",
+                                "cmul(M[i][b], link(&L, U, mu, x, b, a))"),
 }
 
 PINS = [
@@ -42,6 +50,8 @@ PINS = [
     ("adjoint", lambda: pins.test_adjoint_and_gamma5_hermiticity()),
     ("dense", lambda: pins.test_dense_brute_force((2, 2, 2, 4), True)),
     ("cg_free", lambda: pins.test_cg_free_field_inverse()),
+    ("force_derivative", lambda: force_pins.test_force_is_the_derivative_of_the_action(True)),
+    ("force_covariance", lambda: force_pins.test_force_gauge_covariance()),
 ]
 
 
@@ -60,10 +70,11 @@ def _build_mutant(tmp_path, name):
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_mutation(name, tmp_path, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", _build_mutant(tmp_path, name))
-    caught = []
-    for pin, fn in PINS:
+    caught = None
+    for pin, fn in PINS:  # stop at the first pin that fails
         try:
             fn()
         except (AssertionError, RuntimeError, ValueError, FloatingPointError):
-            caught.append(pin)
+            caught = pin
+            break
     assert caught, f"no pin detects mutation {name}"
