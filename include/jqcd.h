@@ -294,6 +294,50 @@ JQCD_API jqcd_status jqcd_serve_poll(jqcd_ctx *ctx, uint64_t ticket, jqcd_solve_
 /* Wait for every submitted request to finish, stop the thread, report stats. */
 JQCD_API jqcd_status jqcd_serve_stop(jqcd_ctx *ctx, jqcd_serve_stats *stats);
 
+/* ---- fermion action and force (paper, section "Definition of fermion
+ * actions": FermiAction, evaluate_FermiAction, calc_UdSfdU) ----------------
+ * Two-flavour Wilson action of a pseudofermion eta,
+ *   S = eta^dag (D^dag D)^{-1} eta = |(D^dag)^{-1} eta|^2,
+ * computed from two solves of D z = c (each even-odd preconditioned, as
+ * jqcd_cg_solve, in params->mode): Y = gamma5 D^{-1} gamma5 eta = (D^dag)^{-1}
+ * eta and X = D^{-1} Y = (D^dag D)^{-1} eta; S = Re <eta, X>.
+ * The pseudofermion heatbath eta = D^dag xi (paper: sample_pseudofermions!)
+ * is jqcd_dirac_apply with dagger = 1; then S = |xi|^2.
+ *
+ * U dS/dU (one 3x3 complex matrix per link): with dS = Re Tr[(dS/dU) dU] for
+ * every complex variation dU of a link, the library returns
+ *   G_mu(x) = U_mu(x) dS/dU_mu(x) = 2 kappa s U_mu(x) (A + B^dag),
+ *   A_ba = sum_alpha [(1 - gamma_mu) X(x+mu)]_alpha,b conj(Y_alpha,a(x)),
+ *   B_ba = sum_alpha [(1 + gamma_mu) X(x)]_alpha,b    conj(Y_alpha,a(x+mu)),
+ * s = -1 for links that cross the antiperiodic time boundary, else 1.  For
+ * U -> exp(eps w) U with w in su(3): dS/deps = Re Tr[G w].  The HMC momentum
+ * update takes the traceless anti-Hermitian part of G.  Layout: the canonical
+ * link layout of jqcd_gauge_upload (4*V matrices, element (a, b) of link
+ * (site, mu) at a + 3*(b + 3*(site + V*mu))), complex doubles.  Arithmetic is
+ * double-word (FP64-class); X and Y are accurate to the solves' tol. */
+
+/* S only.  eta: host canonical spinor (copied).  info (may be NULL) sums the
+ * two solves' iterations, hop bytes and times; its residuals are the larger
+ * of the two. */
+JQCD_API jqcd_status jqcd_fermi_action(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                       const double *eta, double *action, jqcd_solve_info *info);
+/* S and G.  udsdu: host, 4*V*9 complex doubles (written); action may be NULL. */
+JQCD_API jqcd_status jqcd_fermi_force(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                      const double *eta, double *udsdu, double *action,
+                                      jqcd_solve_info *info);
+/* G from given X and Y (host canonical spinors): the per-link kernel alone. */
+JQCD_API jqcd_status jqcd_fermi_force_xy(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const double *X,
+                                         const double *Y, double *udsdu);
+/* Device form: X_*, Y_* caller-owned JQCD_PREC_DW spinors per parity; out:
+ * caller-owned device buffer of jqcd_linkfield_bytes() holding G as a
+ * double-word link field ([parity][mu][3*a+b][site] chunks of
+ * (re.h, im.h, re.l, im.l), the layout of the uploaded double-word gauge
+ * field).  Asynchronous on `stream`. */
+JQCD_API jqcd_status jqcd_fermi_force_dev(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const void *X_even,
+                                          const void *X_odd, const void *Y_even, const void *Y_odd, void *out,
+                                          void *stream);
+JQCD_API jqcd_status jqcd_linkfield_bytes(const jqcd_lattice *lat, size_t *bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,8 @@ def _configure(lib):
     lib.jo_set_threads.argtypes = [c_int]
     lib.jo_fermi_force.argtypes = [ip, c_int, c_double, dp, dp, dp, dp]
     lib.jo_fermi_force.restype = c_int
+    lib.jo_fermi_force_links.argtypes = [ip, c_int, c_double, dp, dp, dp, i64p, ctypes.c_int64, dp]
+    lib.jo_fermi_force_links.restype = c_int
     lib.jo_set_threads.restype = c_int
     for name in ("jo_hop", "jo_dirac", "jo_hop_sites", "jo_schur", "jo_normal_apply",
                  "jo_cg", "jo_solve", "jo_zero_parity"):
@@ -201,6 +203,18 @@ def fermi_force_xy(dims, U, X, Y, kappa, t_antiperiodic=True):
     out = np.zeros_like(U)
     _check(_load().jo_fermi_force(cd, int(t_antiperiodic), float(kappa), _p(U), _p(X), _p(Y),
                                   _p(out)), "jo_fermi_force")
+    return out
+
+
+def fermi_force_links(dims, U, X, Y, kappa, links, t_antiperiodic=True):
+    """U dS/dU of the given links (site + V*mu, lexicographic site); shape (n, 3, 3)
+    as [k, b, a] like the link arrays."""
+    d, cd = _dims(dims)
+    ls = np.ascontiguousarray(np.asarray(links, dtype=np.int64))
+    out = np.zeros((len(ls), 3, 3), dtype=np.complex128)
+    _check(_load().jo_fermi_force_links(cd, int(t_antiperiodic), float(kappa), _p(U), _p(X), _p(Y),
+                                        ls.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), len(ls),
+                                        _p(out)), "jo_fermi_force_links")
     return out
 
 

@@ -477,48 +477,70 @@ int jo_set_threads(int n) {
  * variation U -> exp(eps w) U (w in su(3)) this gives dS/deps = Re Tr[out w].
  * Written from the definition: explicit 4x4 gamma matrices, no spin projection.
  */
+/* U_mu(x) dS/dU_mu(x) of one link into res[i][a] (element (i, a)). */
+static void force_link(const lat_t *L, double kappa, const double *U, const double *X, const double *Y,
+                       int64_t x, int mu, cplx res[3][3]) {
+  int64_t c[4];
+  site_coords(L, x, c);
+  int64_t nc[4] = {c[0], c[1], c[2], c[3]};
+  double s = 1.0;
+  nc[mu] = c[mu] + 1;
+  if (nc[mu] == L->n[mu]) {
+    nc[mu] = 0;
+    if (mu == 3 && L->tanti) s = -1.0;
+  }
+  const int64_t xp = site_index(L, nc);
+  cplx M[3][3];  /* M[b][a] = A_{ba} + conj(B_{ab}) */
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      cplx acc = cm(0, 0);
+      for (int alpha = 0; alpha < 4; ++alpha)
+        for (int beta = 0; beta < 4; ++beta) {
+          const double d = (alpha == beta) ? 1.0 : 0.0;
+          const cplx gm = cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */
+          const cplx gp = cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);   /* 1 + gamma */
+          /* A_{ba} term */
+          acc = cadd(acc, cmul(gm, cmul(spin_ld(L, X, xp, b, beta), cconj(spin_ld(L, Y, x, a, alpha)))));
+          /* conj(B_{ab}) term: B_{ab} = (1+gamma)_{alpha beta} X_{beta a}(x) conj(Y_{alpha b}(x+mu)) */
+          acc = cadd(acc, cconj(cmul(gp, cmul(spin_ld(L, X, x, a, beta), cconj(spin_ld(L, Y, xp, b, alpha))))));
+        }
+      M[b][a] = acc;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) {
+      cplx acc = cm(0, 0);
+      for (int b = 0; b < 3; ++b) acc = cadd(acc, cmul(link(L, U, mu, x, i, b), M[b][a]));
+      res[i][a] = cscale(acc, 2.0 * kappa * s);
+    }
+}
+
 int jo_fermi_force(const int dims[4], int tanti, double kappa, const double *U, const double *X,
                    const double *Y, double *out) {
   lat_t L;
   if (lat_init(&L, dims, tanti) || !U || !X || !Y || !out) return -1;
 #pragma omp parallel for schedule(static)
-  for (int64_t x = 0; x < L.V; ++x) {
-    int64_t c[4];
-    site_coords(&L, x, c);
+  for (int64_t x = 0; x < L.V; ++x)
     for (int mu = 0; mu < 4; ++mu) {
-      int64_t nc[4] = {c[0], c[1], c[2], c[3]};
-      double s = 1.0;
-      nc[mu] = c[mu] + 1;
-      if (nc[mu] == L.n[mu]) {
-        nc[mu] = 0;
-        if (mu == 3 && L.tanti) s = -1.0;
-      }
-      const int64_t xp = site_index(&L, nc);
-      cplx M[3][3];  /* M[b][a] = A_{ba} + conj(B_{ab}) */
-      for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) {
-          cplx acc = cm(0, 0);
-          for (int alpha = 0; alpha < 4; ++alpha)
-            for (int beta = 0; beta < 4; ++beta) {
-              const double d = (alpha == beta) ? 1.0 : 0.0;
-              const cplx gm = cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */
-              const cplx gp = cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);   /* 1 + gamma */
-              /* A_{ba} term */
-              acc = cadd(acc, cmul(gm, cmul(spin_ld(&L, X, xp, b, beta),
-                                             cconj(spin_ld(&L, Y, x, a, alpha)))));
-              /* conj(B_{ab}) term: B_{ab} = (1+gamma)_{alpha beta} X_{beta a}(x) conj(Y_{alpha b}(x+mu)) */
-              acc = cadd(acc, cconj(cmul(gp, cmul(spin_ld(&L, X, x, a, beta),
-                                                   cconj(spin_ld(&L, Y, xp, b, alpha))))));
-            }
-          M[b][a] = acc;
-        }
+      cplx r[3][3];
+      force_link(&L, kappa, U, X, Y, x, mu, r);
       for (int i = 0; i < 3; ++i)
-        for (int a = 0; a < 3; ++a) {
-          cplx acc = cm(0, 0);
-          for (int b = 0; b < 3; ++b) acc = cadd(acc, cmul(link(&L, U, mu, x, i, b), M[b][a]));
-          st(out, i + 3 * (a + 3 * (x + L.V * mu)), cscale(acc, 2.0 * kappa * s));
-        }
+        for (int a = 0; a < 3; ++a) st(out, i + 3 * (a + 3 * (x + L.V * mu)), r[i][a]);
     }
+  return 0;
+}
+
+/* The same for n links only: links[k] = site + V*mu (lexicographic site);
+ * out[k] holds the 3x3 matrix, element (i, a) at i + 3*a (complex). */
+int jo_fermi_force_links(const int dims[4], int tanti, double kappa, const double *U, const double *X,
+                         const double *Y, const int64_t *links, int64_t n, double *out) {
+  lat_t L;
+  if (lat_init(&L, dims, tanti) || !U || !X || !Y || !links || !out || n < 0) return -1;
+  for (int64_t k = 0; k < n; ++k) {
+    if (links[k] < 0 || links[k] >= 4 * L.V) return -1;
+    cplx r[3][3];
+    force_link(&L, kappa, U, X, Y, links[k] % L.V, (int)(links[k] / L.V), r);
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < 3; ++a) st(out, 9 * k + i + 3 * a, r[i][a]);
   }
   return 0;
 }

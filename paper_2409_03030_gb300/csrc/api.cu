@@ -2,6 +2,7 @@
 // applications and the conjugate-gradient drivers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -523,3 +524,150 @@ extern "C" jqcd_status jqcd_dslash_eo_noalloc(jqcd_ctx *ctx, uint64_t gauge_id, 
   if (norm2_dev) CK(launch_finalize_sum(scratch, (int)hop_blocks(G->g.vh), norm2_dev, s), "norm");
   return JQCD_OK;
 }
+
+// ---- fermion action and force ------------------------------------------------
+namespace {
+
+void add_info(jqcd_solve_info *acc, const jqcd_solve_info &s) {
+  acc->iters += s.iters;
+  acc->reliable_updates += s.reliable_updates;
+  acc->restarts += s.restarts;
+  acc->true_rel_resid = std::max(acc->true_rel_resid, s.true_rel_resid);
+  acc->full_rel_resid = std::max(acc->full_rel_resid, s.full_rel_resid);
+  acc->gpu_seconds += s.gpu_seconds;
+  acc->hop_bytes += s.hop_bytes;
+  acc->hop_count += s.hop_count;
+}
+
+// X = (D^dag D)^{-1} eta into G->fX and Y = (D^dag)^{-1} eta into G->fY for the
+// double-word eta in G->feta, by two solves of D z = c:
+// Y = gamma5 D^{-1} gamma5 eta, X = D^{-1} Y.  Then S = Re <eta, X>.
+jqcd_status fermi_solves(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params &params,
+                         jqcd_solve_info *inf, double *action) {
+  cudaStream_t s = ctx->stream;
+  const int64_t vh = G->g.vh;
+  jqcd_solve_params P = params;
+  P.use_x0 = 0;
+  std::string msg;
+  jqcd_solve_info one;
+  CK(launch_gamma5_dw(G->vb, G->feta, vh, s), "gamma5");
+  memset(&one, 0, sizeof one);
+  jqcd_status st = solve_resident(*G, P, s, &one, &msg);
+  add_info(inf, one);
+  if (st != JQCD_OK) {
+    if (st == JQCD_ECUDA) ctx->poisoned = true;
+    return fail(ctx, st, "fermion action, first solve: %s", msg.c_str());
+  }
+  CK(launch_gamma5_dw(G->fY, G->vsol, vh, s), "gamma5");
+  CK(launch_dw_copy(G->vb, G->fY, 24 * vh, s), "copy");
+  memset(&one, 0, sizeof one);
+  st = solve_resident(*G, P, s, &one, &msg);
+  add_info(inf, one);
+  if (st != JQCD_OK) {
+    if (st == JQCD_ECUDA) ctx->poisoned = true;
+    return fail(ctx, st, "fermion action, second solve: %s", msg.c_str());
+  }
+  CK(launch_dw_copy(G->fX, G->vsol, 24 * vh, s), "copy");
+  const int nb = (int)blas_blocks(24 * vh);
+  double *S_dev = G->partials + (G->n_partials() - 1);
+  CK(launch_dw_dot_re(G->feta, G->fX, 24 * vh, G->partials, nb, s), "dot");
+  CK(launch_finalize_sum(G->partials, nb, S_dev, s), "dot finalize");
+  double S = 0.0;
+  CK(cudaMemcpyAsync(&S, S_dev, sizeof S, cudaMemcpyDeviceToHost, s), "action D2H");
+  CK(cudaStreamSynchronize(s), "action sync");
+  if (action) *action = S;
+  return JQCD_OK;
+}
+
+jqcd_status fermi_common(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                         const double *eta, double *udsdu, double *action, jqcd_solve_info *info,
+                         const char *what) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !eta) return fail(ctx, JQCD_EINVAL, "%s: bad argument", what);
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_force(), "force workspace alloc");
+  CK(cudaMemcpyAsync(G->canon, eta, G->canon_bytes(), cudaMemcpyHostToDevice, s), "eta H2D");
+  CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->vec_even(G->feta), G->vec_odd(G->feta), s), "eta pack");
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  st = fermi_solves(ctx, G, *params, &inf, action);
+  if (st == JQCD_OK && udsdu) {
+    const int64_t nh = 12 * G->g.vh;
+    CK(launch_fermi_force(G->g, G->fX, G->fX + nh, G->fY, G->fY + nh, (const float4 *)G->gauge_dw,
+                          params->kappa, G->fout, s), "force");
+    CK(launch_linkfield_unpack(G->g, G->fout, G->lcanon, s), "force unpack");
+    CK(cudaMemcpyAsync(udsdu, G->lcanon, G->link_canon_bytes(), cudaMemcpyDeviceToHost, s), "force D2H");
+    CK(cudaStreamSynchronize(s), "force sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+jqcd_status jqcd_fermi_action(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                              const double *eta, double *action, jqcd_solve_info *info) {
+  if (!action) return fail(ctx, JQCD_EINVAL, "fermi_action: action is NULL");
+  return fermi_common(ctx, gauge_id, params, eta, nullptr, action, info, "fermi_action");
+}
+
+jqcd_status jqcd_fermi_force(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                             const double *eta, double *udsdu, double *action, jqcd_solve_info *info) {
+  if (!udsdu) return fail(ctx, JQCD_EINVAL, "fermi_force: udsdu is NULL");
+  return fermi_common(ctx, gauge_id, params, eta, udsdu, action, info, "fermi_force");
+}
+
+jqcd_status jqcd_fermi_force_xy(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const double *X,
+                                const double *Y, double *udsdu) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!X || !Y || !udsdu) return fail(ctx, JQCD_EINVAL, "fermi_force_xy: bad argument");
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_force(), "force workspace alloc");
+  const int64_t nh = 12 * G->g.vh;
+  CK(cudaMemcpyAsync(G->canon, X, G->canon_bytes(), cudaMemcpyHostToDevice, s), "X H2D");
+  CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->fX, G->fX + nh, s), "X pack");
+  CK(cudaMemcpyAsync(G->canon, Y, G->canon_bytes(), cudaMemcpyHostToDevice, s), "Y H2D");
+  CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->fY, G->fY + nh, s), "Y pack");
+  CK(launch_fermi_force(G->g, G->fX, G->fX + nh, G->fY, G->fY + nh, (const float4 *)G->gauge_dw, kappa,
+                        G->fout, s), "force");
+  CK(launch_linkfield_unpack(G->g, G->fout, G->lcanon, s), "force unpack");
+  CK(cudaMemcpyAsync(udsdu, G->lcanon, G->link_canon_bytes(), cudaMemcpyDeviceToHost, s), "force D2H");
+  CK(cudaStreamSynchronize(s), "force sync");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_fermi_force_dev(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const void *X_even,
+                                 const void *X_odd, const void *Y_even, const void *Y_odd, void *out,
+                                 void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!X_even || !X_odd || !Y_even || !Y_odd || !out)
+    return fail(ctx, JQCD_EINVAL, "fermi_force_dev: bad argument");
+  CK(launch_fermi_force(G->g, (const float4 *)X_even, (const float4 *)X_odd, (const float4 *)Y_even,
+                        (const float4 *)Y_odd, (const float4 *)G->gauge_dw, kappa, (float4 *)out,
+                        (cudaStream_t)stream), "force");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_linkfield_bytes(const jqcd_lattice *lat, size_t *bytes) {
+  if (!bytes) return JQCD_EINVAL;
+  Geom g;
+  if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
+  *bytes = (size_t)72 * 16 * g.vh;
+  return JQCD_OK;
+}
+
+}  // extern "C"

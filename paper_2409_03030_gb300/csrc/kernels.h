@@ -122,4 +122,18 @@ cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cuda
 cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
                             int max_iters, double delta2, cudaStream_t s);
 
+// ---- fermion action and force (force.cu) ------------------------------------
+// out [2][4][9][vh] double-word link field = U dS/dU from X = (D^dag D)^-1 eta
+// and Y = D X (double-word spinors per parity).
+cudaError_t launch_fermi_force(const Geom &g, const float4 *xe, const float4 *xo, const float4 *ye,
+                               const float4 *yo, const float4 *gauge_dw, double kappa, float4 *out,
+                               cudaStream_t s);
+// out = gamma5 in, whole-lattice double-word spinor (24 vh chunks); in place allowed.
+cudaError_t launch_gamma5_dw(float4 *out, const float4 *in, int64_t vh, cudaStream_t s);
+// Per-block partials of Re <a, b> over n double-word complex numbers.
+cudaError_t launch_dw_dot_re(const float4 *a, const float4 *b, int64_t n, double *partials, int nblocks,
+                             cudaStream_t s);
+// Double-word link field -> canonical host-layout links (complex double).
+cudaError_t launch_linkfield_unpack(const Geom &g, const float4 *dwf, double *canon, cudaStream_t s);
+
 }  // namespace jqcd

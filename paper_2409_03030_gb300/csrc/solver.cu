@@ -79,6 +79,17 @@ cudaError_t GaugeEntry::ensure_solver() {
   return e;
 }
 
+cudaError_t GaugeEntry::ensure_force() {
+  cudaError_t e = ensure_solver();
+  const size_t full = 2 * spinor_parity_bytes(PREC_DW, g.vh);
+  float4 **vs[] = {&feta, &fX, &fY};
+  for (float4 **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc_t(v, full);
+  if (e == cudaSuccess && !fout) e = alloc_t(&fout, linkfield_bytes());
+  if (e == cudaSuccess && !lcanon) e = alloc_t(&lcanon, link_canon_bytes());
+  return e;
+}
+
 cudaError_t GaugeEntry::ensure_mixed(int hop_prec) {
   const int k = hop_prec == PREC_F16N ? 1 : 0;
   const size_t f32 = spinor_parity_bytes(PREC_F32, g.vh);

@@ -31,6 +31,10 @@ struct GaugeEntry {
   // native FP64 solver vectors (whole lattice)
   double2 *fb = nullptr, *fsol = nullptr, *fr = nullptr, *fp = nullptr, *fAp = nullptr,
           *fw = nullptr, *ft = nullptr, *frhs = nullptr;
+  // fermion action / force workspace: eta, X, Y (whole-lattice double-word),
+  // the double-word link-field result and its canonical host-layout staging
+  float4 *feta = nullptr, *fX = nullptr, *fY = nullptr, *fout = nullptr;
+  double *lcanon = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void *> device_allocs;
 
@@ -49,6 +53,9 @@ struct GaugeEntry {
   cudaError_t ensure_solver();
   cudaError_t ensure_mixed(int hop_prec);
   cudaError_t ensure_f64();
+  cudaError_t ensure_force();
+  size_t linkfield_bytes() const { return (size_t)72 * 16 * g.vh; }  // [2][4][9][vh] float4
+  size_t link_canon_bytes() const { return sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh); }
   int n_partials() const;
   float4 *vec_even(float4 *v) const { return v; }
   float4 *vec_odd(float4 *v) const { return v + 12 * g.vh; }

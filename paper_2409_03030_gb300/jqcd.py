@@ -105,6 +105,13 @@ _SIGNATURES = {
     "jqcd_serve_stop": (_st, [_vp, ctypes.POINTER(jqcd_serve_stats)]),
     "jqcd_cg_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _vp, _vp, _vp, _vp,
                                 ctypes.POINTER(jqcd_solve_info), _vp]),
+    "jqcd_fermi_action": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _dp, _dp,
+                                ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_fermi_force": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), _dp, _dp, _dp,
+                               ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_fermi_force_xy": (_st, [_vp, _u64, ctypes.c_double, _dp, _dp, _dp]),
+    "jqcd_fermi_force_dev": (_st, [_vp, _u64, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "jqcd_linkfield_bytes": (_st, [ctypes.POINTER(jqcd_lattice), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
 
@@ -330,6 +337,58 @@ class Gauge:
         if check:
             self.ctx.check(st, "jqcd_cg_solve")
         return x, info.as_dict(), st
+
+    # ---- fermion action and force (paper: evaluate_FermiAction, calc_UdSfdU) ----
+    def link_shape(self):
+        nx, ny, nz, nt = self.dims
+        return (4, nt, nz, ny, nx, 3, 3)  # [mu, t, z, y, x, b, a] like the uploaded links
+
+    def fermi_action(self, eta, kappa, tol=1e-10, maxiter=20000, mode=CG_DW, check=True):
+        """S = eta^dag (D^dag D)^-1 eta; returns (S, info dict, status)."""
+        eta = np.ascontiguousarray(eta, dtype=np.complex128)
+        p = self.params(kappa, tol, maxiter, True, mode)
+        S = ctypes.c_double(0.0)
+        info = jqcd_solve_info()
+        st = jqcd_fermi_action(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(eta), ctypes.byref(S),
+                               ctypes.byref(info))
+        if check:
+            self.ctx.check(st, "jqcd_fermi_action")
+        return S.value, info.as_dict(), st
+
+    def fermi_force(self, eta, kappa, tol=1e-10, maxiter=20000, mode=CG_DW, check=True):
+        """(S, U dS/dU as links [mu,t,z,y,x,b,a], info dict, status)."""
+        eta = np.ascontiguousarray(eta, dtype=np.complex128)
+        p = self.params(kappa, tol, maxiter, True, mode)
+        G = np.zeros(self.link_shape(), dtype=np.complex128)
+        S = ctypes.c_double(0.0)
+        info = jqcd_solve_info()
+        st = jqcd_fermi_force(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(eta), _host_ptr(G),
+                              ctypes.byref(S), ctypes.byref(info))
+        if check:
+            self.ctx.check(st, "jqcd_fermi_force")
+        return S.value, G, info.as_dict(), st
+
+    def fermi_force_xy(self, X, Y, kappa):
+        """U dS/dU from given X = (D^dag D)^-1 eta and Y = D X (host spinors)."""
+        X = np.ascontiguousarray(X, dtype=np.complex128)
+        Y = np.ascontiguousarray(Y, dtype=np.complex128)
+        G = np.zeros(self.link_shape(), dtype=np.complex128)
+        self.ctx.check(jqcd_fermi_force_xy(self.ctx.h, self.id, float(kappa), _host_ptr(X), _host_ptr(Y),
+                                           _host_ptr(G)), "jqcd_fermi_force_xy")
+        return G
+
+    def linkfield_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        lat = lattice(self.dims, self.t_antiperiodic)
+        if jqcd_linkfield_bytes(ctypes.byref(lat), ctypes.byref(n)) != OK:
+            raise ValueError("bad lattice")
+        return n.value
+
+    def fermi_force_dev(self, kappa, X_even, X_odd, Y_even, Y_odd, out, stream=None):
+        """U dS/dU into a device double-word link field (out: linkfield_bytes())."""
+        self.ctx.check(jqcd_fermi_force_dev(self.ctx.h, self.id, float(kappa), _dev_ptr(X_even),
+                                            _dev_ptr(X_odd), _dev_ptr(Y_even), _dev_ptr(Y_odd),
+                                            _dev_ptr(out), _stream_ptr(stream)), "jqcd_fermi_force_dev")
 
     def cg_solve_dev(self, b_even, b_odd, x_even, x_odd, kappa, tol=1e-10, maxiter=20000, eo=True,
                      mode=CG_DW, verbose=0, delta=0.0, use_x0=False, stream=None, check=True):

@@ -35,11 +35,11 @@ MUTATIONS = {
                               "schur(&L, kappa, U, t, rhs, 1, t2);"),
     "force_projectors_swapped": ("cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */",
                                  "cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);  /* 1 - gamma */"),
-    "force_no_boundary_sign": ("if (mu == 3 && L.tanti) s = -1.0;", ""),
+    "force_no_boundary_sign": ("if (mu == 3 && L->tanti) s = -1.0;", ""),
     "force_second_term_not_conjugated": ("acc = cadd(acc, cconj(cmul(gp,", "acc = cadd(acc, (cmul(gp,"),
     "force_factor_two_dropped": ("cscale(acc, 2.0 * kappa * s)", "cscale(acc, kappa * s)"),
-    "force_link_on_the_right": ("cmul(link(&L, U, mu, x, i, b), M[b][a])",
-                                "cmul(M[i][b], link(&L, U, mu, x, b, a))"),
+    "force_link_on_the_right": ("cmul(link(L, U, mu, x, i, b), M[b][a])",
+                                "cmul(M[i][b], link(L, U, mu, x, b, a))"),
 }
 
 PINS = [
