@@ -269,6 +269,42 @@ def workload_config():
             "parallelism": "replicas"}
 
 
+def bench_force(ctx, jqcd, synth, np, torch, stream, g, b):
+    """Fermion action and force on the workload lattice (kappa 0.12): the
+    per-link kernel alone on resident X, Y (1536 algorithmic bytes per site:
+    X, Y once, 4 links in, 4 matrices out), and the whole action + force
+    (two even-odd solves to 1e-10, the dot product, the kernel) from a host
+    pseudofermion, double-word and mixed FP16."""
+    X = synth.gaussian_spinor(DIMS, seed=81)
+    with torch.cuda.stream(stream):
+        xe, xo = g.pack(X, jqcd.PREC_DW, stream=stream)
+        ye, yo = g.pack(b, jqcd.PREC_DW, stream=stream)
+        out = torch.empty(g.linkfield_bytes(), dtype=torch.uint8, device=xe.device)
+    for _ in range(3):
+        g.fermi_force_dev(KAPPA, xe, xo, ye, yo, out, stream=stream)
+    stream.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 10
+    a0.record(stream)
+    for _ in range(n):
+        g.fermi_force_dev(KAPPA, xe, xo, ye, yo, out, stream=stream)
+    a1.record(stream)
+    stream.synchronize()
+    us = a0.elapsed_time(a1) / n * 1e3
+    V = vol(DIMS)
+    hbm, _ = peaks()
+    res = {"kernel": "force_kernel (U dS/dU, double-word)", "us": round(us, 1),
+           "gbs": round(V * 1536 / us / 1e3, 1), "hbm_frac": round(V * 1536 / us / 1e3 / hbm, 4)}
+    for name, mode in [("dw", jqcd.CG_DW), ("mixed_f16", jqcd.CG_MIXED_F16)]:
+        g.fermi_force(b, KAPPA, tol=TOL, mode=mode)  # warm-up
+        t0 = time.perf_counter()
+        S, _, info, st = g.fermi_force(b, KAPPA, tol=TOL, mode=mode)
+        res[f"action_force_{name}"] = {"s": round(time.perf_counter() - t0, 4),
+                                       "gpu_s": round(info["gpu_seconds"], 4),
+                                       "iters": info["iters"], "action": S, "status": st}
+    return res
+
+
 def bench_batch(ctx, jqcd, synth, np):
     """12 point sources on 24^3x48 + 12 Gaussian sources on 16^4 (kappa 0.12,
     exp(i 0.3 H) links, tol 1e-10, FP16 inner): one jqcd_cg_solve_batch call
@@ -530,6 +566,7 @@ def run_gpu(args):
         cg_c2["workload"] = "32^3x64, exp(i*0.4*H) links, kappa 0.122, even-odd, tol 1e-10"
         g2.free()
 
+    force = bench_force(ctx, jqcd, synth, np, torch, stream, g, b)
     batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
     serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
 
@@ -574,6 +611,7 @@ def run_gpu(args):
             "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
                            for k, v in hop_ms.items()},
             "dslash_sweep_gbs": sweep,
+            "force": force,
             "batch": batch,
             "serve": serve,
         }

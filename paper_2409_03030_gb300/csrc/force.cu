@@ -14,11 +14,14 @@
 // reconstruction table of the hop), so each spin sum is two colour outer
 // products, h_s conj(w_s)^T, with h the projected half-spinor of X and
 // w_s = Y_s + conj-phase * Y_alpha for the lower spins alpha that map to s.
+// Arithmetic: the packed two-lane double-word operations of the hop
+// (compensated sums of exact products, hop_dwp.cuh).
 #include <cuda_runtime.h>
 
 #include "fields.cuh"
 #include "hop.cuh"
 #include "hop_dw.cuh"
+#include "hop_dwp.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
 
@@ -28,10 +31,21 @@ namespace {
 
 constexpr int kForceThreads = 128;
 
+// a + phase<PH> b for complex double-word pairs (PH: 0 -> 1, 1 -> i, 2 -> -1,
+// 3 -> -i); i b = (-b.im, b.re).
+template <int PH>
+__device__ __forceinline__ p2 p2_add_phase(p2 a, p2 b) {
+  if (PH == 0) return p2_add(a, b);
+  if (PH == 2) return p2_add_sgn(a, b, f2_make(-1.f, -1.f));
+  if (PH == 1) return p2_add_sgn(a, p2_swap(b), f2_make(-1.f, 1.f));
+  return p2_add_sgn(a, p2_swap(b), f2_make(1.f, -1.f));
+}
+
 // w_s = Y_s + sum over the lower spins alpha with k_alpha = s of
-// conj(phase_alpha) Y_alpha, for the projector (1 + S gamma_mu).
+// conj(phase_alpha) Y_alpha, for the projector (1 + S gamma_mu): then
+// sum_alpha [(1 + S gamma_mu) Z]_alpha conj(Y_alpha) = sum_s h_s conj(w_s).
 template <int MU, int S>
-__device__ __forceinline__ void adjoint_half(const cw (&y)[4][3], cw (&w)[2][3]) {
+__device__ __forceinline__ void adjoint_half_p(const p2 (&y)[4][3], p2 (&w)[2][3]) {
   typedef SpinTab<MU> T;
   constexpr int Q2 = (T::q2 + (S < 0 ? 2 : 0)) & 3;
   constexpr int Q3 = (T::q3 + (S < 0 ? 2 : 0)) & 3;
@@ -43,14 +57,62 @@ __device__ __forceinline__ void adjoint_half(const cw (&y)[4][3], cw (&w)[2][3])
   }
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    w[T::k2][c] = cadd(w[T::k2][c], phase<C2>(y[2][c]));
-    w[T::k3][c] = cadd(w[T::k3][c], phase<C3>(y[3][c]));
+    w[T::k2][c] = p2_add_phase<C2>(w[T::k2][c], y[2][c]);
+    w[T::k3][c] = p2_add_phase<C3>(w[T::k3][c], y[3][c]);
   }
 }
 
-__device__ __forceinline__ void load_dw_spinor(const float4 *base, int64_t vh, int64_t i, cw (&s)[4][3]) {
+__device__ __forceinline__ void load_dw_spinor_p(const float4 *base, int64_t vh, int64_t i, p2 (&s)[4][3]) {
+  const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base) + i;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) dwc_unpack(__ldg(base + k * vh + i), s[k / 3][k % 3].re, s[k / 3][k % 3].im);
+  for (int k = 0; k < 12; ++k) {
+    const ulonglong2 v = __ldg(q + k * vh);
+    s[k / 3][k % 3] = p2{v.x, v.y};
+  }
+}
+
+// Broadcast multiplier of the real part of conj(z) (both lanes z.re) and of
+// its imaginary part (both lanes -z.im).
+__device__ __forceinline__ mul2 conj_re(p2 z) { return mul2{f2_lo(z.h), f2_lo(z.l)}; }
+__device__ __forceinline__ mul2 conj_im(p2 z) { return mul2{f2_neg(f2_hi(z.h)), f2_neg(f2_hi(z.l))}; }
+
+// One part of M: P_ba = sum_s v_sb conj(c_sa) with, for the A part
+// (SWAP = false), v = projected (1 + S gamma_mu) Z at site iz and c = adjoint
+// half of W at site iw; for the B^dag part (SWAP = true) the roles swap:
+// v = adjoint half of Z (Y(x+mu)), c = projected W (X(x)).  M = P (first
+// part) or M + P.
+template <int MU, int S>
+__device__ __forceinline__ void outer_part(const float4 *Zf, int64_t iz, const float4 *Wf, int64_t iw,
+                                           int64_t vh, p2 (&M)[3][3], bool SWAP) {
+  p2 v[2][3], c[2][3];
+  {
+    p2 s4[4][3];
+    if (!SWAP) {
+      load_dw_spinor_p(Zf, vh, iz, s4);
+      project_p<MU>(s4, v, (float)S);
+      load_dw_spinor_p(Wf, vh, iw, s4);
+      adjoint_half_p<MU, S>(s4, c);
+    } else {
+      load_dw_spinor_p(Zf, vh, iz, s4);
+      adjoint_half_p<MU, S>(s4, v);
+      load_dw_spinor_p(Wf, vh, iw, s4);
+      project_p<MU>(s4, c, (float)S);
+    }
+  }
+  constexpr f2 kLane0 = 0x0000000080000000ull;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const mul2 r0 = conj_re(c[0][a]), r1 = conj_re(c[1][a]);
+    const mul2 i0 = conj_im(c[0][a]), i1 = conj_im(c[1][a]);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      acc2 A = acc2_first(r0, v[0][b]), B = acc2_first(i0, v[0][b]);
+      acc2_mad(A, r1, v[1][b]);
+      acc2_mad(B, i1, v[1][b]);
+      const p2 P = p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0});
+      M[b][a] = p2_norm(SWAP ? p2_add(M[b][a], p2_norm(P)) : P);
+    }
+  }
 }
 
 // X and Y of both parities as double-word spinor fields.
@@ -58,91 +120,69 @@ struct FieldPair {
   const float4 *xe, *xo, *ye, *yo;
 };
 
-// U dS/dU of direction MU for the link at site (p, cb).
+// U dS/dU of direction MU for the link at site (p, cb), packed double-word
+// arithmetic.  M_ba = A_ba + conj(B_ab) = sum_s [h_sb conj(w_sa) + wp_sb conj(hp_sa)],
+// each element as complex scalars times vector components split into the
+// real and imaginary parts of the scalars; then G = 2 kappa s U M, column by
+// column through the hop's mat-vec.
 template <int MU>
 __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int x, int y, int z, int t,
-                                           const FieldPair &F, const float4 *gauge, dw two_kappa,
+                                           const FieldPair &F, const float4 *gauge, float2 two_kappa,
                                            float4 *out) {
   const int64_t vh = g.vh;
   bool neg;
   const int64_t nb = hop_neighbour(g, x, y, z, t, 2 * MU, neg);  // x + mu, parity 1-p
   const float4 *Xh = p ? F.xo : F.xe, *Yh = p ? F.yo : F.ye;
   const float4 *Xn = p ? F.xe : F.xo, *Yn = p ? F.ye : F.yo;
-  cw h[2][3], w[2][3], hp[2][3], wp[2][3];
+  p2 M[3][3];
+  // A part, sum_s h_sb conj(w_sa), then the B^dag part, sum_s wp_sb conj(hp_sa),
+  // added in: only one pair of half-spinor fields is live at a time
+  outer_part<MU, -1>(Xn, nb, Yh, cb, vh, M, false);  // (1 - gamma_mu) X(x+mu), Y(x)
+  outer_part<MU, 1>(Yn, nb, Xh, cb, vh, M, true);    // (1 + gamma_mu) X(x), Y(x+mu), swapped roles
+  p2 U[3][3];
   {
-    cw s4[4][3];
-    load_dw_spinor(Xn, vh, nb, s4);
-    project<MU, -1>(s4, h);     // rows 0, 1 of (1 - gamma_mu) X(x+mu)
-    load_dw_spinor(Yh, vh, cb, s4);
-    adjoint_half<MU, -1>(s4, w);  // partner of Y(x)
-    load_dw_spinor(Xh, vh, cb, s4);
-    project<MU, 1>(s4, hp);     // rows 0, 1 of (1 + gamma_mu) X(x)
-    load_dw_spinor(Yn, vh, nb, s4);
-    adjoint_half<MU, 1>(s4, wp);  // partner of Y(x+mu)
+    const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(gauge) + (size_t)((p * 4 + MU) * 9) * vh + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const ulonglong2 v = __ldcs(L + k * vh);
+      U[k / 3][k % 3] = p2{v.x, v.y};
+    }
   }
-  // M_ba = A_ba + conj(B_ab) = sum_s h_sb conj(w_sa) + conj(hp_sa) wp_sb
-  cw M[3][3];
+  const float fs = neg ? -1.f : 1.f;  // boundary sign, exact
+  const f2 fh = f2_make(fs * two_kappa.x, fs * two_kappa.x);
+  const mul2 Fm{fh, f2_make(fs * two_kappa.y, fs * two_kappa.y)};
+  ulonglong2 *o = reinterpret_cast<ulonglong2 *>(out) + (size_t)((p * 4 + MU) * 9) * vh + cb;
 #pragma unroll
-  for (int b = 0; b < 3; ++b)
+  for (int a = 0; a < 3; ++a) {
+    const p2 col[3] = {M[0][a], M[1][a], M[2][a]};
+    p2 Gc[3];
+    matvec_half_p(U, col, Gc);  // G_ia = sum_b U_ib M_ba
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dwacc re = acc_first(h[0][b].re, w[0][a].re), im = acc_first(h[0][b].im, w[0][a].re);
-      acc_mad(re, h[0][b].im, w[0][a].im);
-      acc_mad(im, dw_neg(h[0][b].re), w[0][a].im);
-      acc_mad(re, h[1][b].re, w[1][a].re);
-      acc_mad(re, h[1][b].im, w[1][a].im);
-      acc_mad(im, h[1][b].im, w[1][a].re);
-      acc_mad(im, dw_neg(h[1][b].re), w[1][a].im);
-#pragma unroll
-      for (int s = 0; s < 2; ++s) {
-        acc_mad(re, hp[s][a].re, wp[s][b].re);
-        acc_mad(re, hp[s][a].im, wp[s][b].im);
-        acc_mad(im, hp[s][a].re, wp[s][b].im);
-        acc_mad(im, dw_neg(hp[s][a].im), wp[s][b].re);
-      }
-      const dw r = acc_get(re), i = acc_get(im);
-      M[b][a] = cw{dw_norm(r.h, r.l), dw_norm(i.h, i.l)};
+    for (int i = 0; i < 3; ++i) {
+      const p2 q = p2_norm(acc2_get(acc2_first(Fm, p2_norm(Gc[i]))));
+      __stcs(o + (3 * i + a) * vh, make_ulonglong2(q.h, q.l));
     }
-  // G = 2 kappa s U M
-  const dw f = neg ? dw_neg(two_kappa) : two_kappa;
-  const float4 *L = gauge + (size_t)((p * 4 + MU) * 9) * vh + cb;
-  cw u[3][3];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) dwc_unpack(__ldcs(L + k * vh), u[k / 3][k % 3].re, u[k / 3][k % 3].im);
-  float4 *o = out + (size_t)((p * 4 + MU) * 9) * vh + cb;
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      dwacc re = acc_first(u[i][0].re, M[0][a].re), im = acc_first(u[i][0].re, M[0][a].im);
-      acc_mad(re, dw_neg(u[i][0].im), M[0][a].im);
-      acc_mad(im, u[i][0].im, M[0][a].re);
-#pragma unroll
-      for (int b = 1; b < 3; ++b) {
-        acc_mad(re, u[i][b].re, M[b][a].re);
-        acc_mad(re, dw_neg(u[i][b].im), M[b][a].im);
-        acc_mad(im, u[i][b].re, M[b][a].im);
-        acc_mad(im, u[i][b].im, M[b][a].re);
-      }
-      const dw r = acc_get(re), m = acc_get(im);
-      __stcs(o + (3 * i + a) * vh, dwc_pack(dw_mul(f, dw_norm(r.h, r.l)), dw_mul(f, dw_norm(m.h, m.l))));
-    }
+  }
 }
 
-__global__ void __launch_bounds__(kForceThreads) force_kernel(Geom g, FieldPair F,
-                                                              const float4 *__restrict__ gauge,
-                                                              float2 two_kappa, float4 *__restrict__ out) {
+__global__ void __launch_bounds__(kForceThreads, 3) force_kernel(Geom g, FieldPair F,
+                                                                 const float4 *__restrict__ gauge,
+                                                                 float2 two_kappa, float4 *__restrict__ out) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 2 * g.vh) return;
   const int p = (int)(q / g.vh);
   const int64_t cb = q - (int64_t)p * g.vh;
   int x, y, z, t;
   cb_coords(g, cb, p, x, y, z, t);
-  const dw tk = dw_make(two_kappa.x, two_kappa.y);
-  force_link<0>(g, p, cb, x, y, z, t, F, gauge, tk, out);
-  force_link<1>(g, p, cb, x, y, z, t, F, gauge, tk, out);
-  force_link<2>(g, p, cb, x, y, z, t, F, gauge, tk, out);
-  force_link<3>(g, p, cb, x, y, z, t, F, gauge, tk, out);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {  // one direction's code live at a time
+    switch (mu) {
+      case 0: force_link<0>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
+      case 1: force_link<1>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
+      case 2: force_link<2>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
+      default: force_link<3>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out);
+    }
+  }
 }
 
 // out = gamma5 in on a whole-lattice double-word spinor (chunks k = 3*spin + c;
