@@ -63,6 +63,9 @@ def _configure(lib):
     lib.jo_solve.argtypes = [ip, c_int, c_double, dp, c_int, dp, dp, c_double, c_int,
                              ip, dp, dp]
     lib.jo_zero_parity.argtypes = [ip, dp, c_int]
+    lib.jo_cg_shift.argtypes = [ip, c_int, c_double, dp, c_int, c_double, dp, dp, c_double, c_int,
+                                ip, dp]
+    lib.jo_cg_shift.restype = c_int
     lib.jo_set_threads.argtypes = [c_int]
     lib.jo_fermi_force.argtypes = [ip, c_int, c_double, dp, dp, dp, dp]
     lib.jo_fermi_force.restype = c_int
@@ -171,6 +174,20 @@ def cg(dims, U, rhs, kappa, eo=True, tol=1e-10, maxiter=10000, x0=None, t_antipe
     rc = _check(_load().jo_cg(cd, int(t_antiperiodic), float(kappa), _p(U), int(bool(eo)),
                               _p(rhs), _p(x), float(tol), int(maxiter), ctypes.byref(it),
                               ctypes.byref(tr)), "jo_cg")
+    return x, it.value, tr.value, rc == 0
+
+
+def cg_shift(dims, U, rhs, kappa, shift, eo=True, tol=1e-10, maxiter=10000, t_antiperiodic=True):
+    """Textbook CG on (A + shift) x = rhs, A = Mhat^dag Mhat (eo, even sites) or
+    D^dag D: what a multi-shift solve returns for that shift.
+    Returns (x, iters, true_rel, converged)."""
+    d, cd = _dims(dims)
+    x = _spinor(d)
+    it = ctypes.c_int(0)
+    tr = ctypes.c_double(0)
+    rc = _check(_load().jo_cg_shift(cd, int(t_antiperiodic), float(kappa), _p(U), int(bool(eo)),
+                                    float(shift), _p(rhs), _p(x), float(tol), int(maxiter),
+                                    ctypes.byref(it), ctypes.byref(tr)), "jo_cg_shift")
     return x, it.value, tr.value, rc == 0
 
 

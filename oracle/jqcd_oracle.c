@@ -280,11 +280,13 @@ static double redot(const double *a, const double *b, int64_t nreal) { /* Re <a,
 }
 
 /* Normal-equation operators.  op 0: A = D^dagger D (whole lattice).
- * op 1: A = Mhat^dagger Mhat (even sites). */
+ * op 1: A = Mhat^dagger Mhat (even sites).  Applied as A + shift (shift = 0
+ * except for the shifted systems of multi-shift solves). */
 typedef struct {
   lat_t L;
   int op;
   double kappa;
+  double shift;
   const double *U;
   double *t1, *t2;
 } normal_op;
@@ -297,6 +299,8 @@ static void apply_A(normal_op *A, const double *in, double *out) {
     schur(&A->L, A->kappa, A->U, in, A->t1, 1, A->t2);
     schur(&A->L, A->kappa, A->U, A->t1, out, -1, A->t2);
   }
+  if (A->shift != 0.0)
+    for (int64_t i = 0; i < 24 * A->L.V; ++i) out[i] += A->shift * in[i];
 }
 
 /* out = A in for op 0 (D^dag D) or op 1 (Mhat^dag Mhat); paper: DdagD_operator. */
@@ -315,7 +319,8 @@ int jo_normal_apply(const int dims[4], int tanti, double kappa, const double *U,
 }
 
 /* Conjugate gradient (Hestenes-Stiefel) on the Hermitian positive-definite
- * system A x = rhs, A = D^dag D (op 0) or Mhat^dag Mhat (op 1), in FP64:
+ * system (A + shift) x = rhs, A = D^dag D (op 0) or Mhat^dag Mhat (op 1), in FP64
+ * (A stands for A + shift below):
  *   r = rhs - A x, p = r;
  *   repeat: alpha = <r,r>/<p,Ap>; x += alpha p; r -= alpha Ap;
  *           beta = <r',r'>/<r,r>; p = r' + beta p
@@ -324,11 +329,11 @@ int jo_normal_apply(const int dims[4], int tanti, double kappa, const double *U,
  * On return *true_rel = ||rhs - A x|| / ||rhs|| recomputed from x.
  * Paper: solve_DinvX! with the stopping tolerance eps_CG.
  * Returns 0 on convergence, 1 if maxiter was reached, <0 on error. */
-int jo_cg(const int dims[4], int tanti, double kappa, const double *U, int op, const double *rhs,
-          double *x, double tol, int maxiter, int *iters, double *true_rel) {
+static int cg_impl(const int dims[4], int tanti, double kappa, const double *U, int op, double shift,
+                   const double *rhs, double *x, double tol, int maxiter, int *iters, double *true_rel) {
   normal_op A;
   if (lat_init(&A.L, dims, tanti) || !U || !rhs || !x || op < 0 || op > 1) return -1;
-  A.op = op; A.kappa = kappa; A.U = U;
+  A.op = op; A.kappa = kappa; A.U = U; A.shift = shift;
   int64_t n = 24 * A.L.V;
   double *r = (double *)malloc(sizeof(double) * n);
   double *p = (double *)malloc(sizeof(double) * n);
@@ -375,6 +380,19 @@ int jo_cg(const int dims[4], int tanti, double kappa, const double *U, int op, c
   }
   free(r); free(p); free(Ap); free(A.t1); free(A.t2);
   return rc;
+}
+
+/* cg_impl without a shift: the CG of solve_DinvX!. */
+int jo_cg(const int dims[4], int tanti, double kappa, const double *U, int op, const double *rhs,
+          double *x, double tol, int maxiter, int *iters, double *true_rel) {
+  return cg_impl(dims, tanti, kappa, U, op, 0.0, rhs, x, tol, maxiter, iters, true_rel);
+}
+
+/* The same CG on the shifted system (A + shift) x = rhs (shift >= 0): the
+ * definition of what a multi-shift solve returns for each of its shifts. */
+int jo_cg_shift(const int dims[4], int tanti, double kappa, const double *U, int op, double shift,
+                const double *rhs, double *x, double tol, int maxiter, int *iters, double *true_rel) {
+  return cg_impl(dims, tanti, kappa, U, op, shift, rhs, x, tol, maxiter, iters, true_rel);
 }
 
 /* Solve D x = b (paper: solve_DinvX!(x, D, b)).

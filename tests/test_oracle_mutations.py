@@ -9,6 +9,7 @@ import pytest
 import oracle
 import test_oracle_force as force_pins
 import test_oracle_pins as pins
+import test_oracle_shift as shift_pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "jqcd_oracle.c")
 
@@ -33,6 +34,7 @@ MUTATIONS = {
                        "hop_axpy(&L, U, b, t, 1, 0, 0.0, -kappa);"),
     "eo_rhs_without_dagger": ("schur(&L, kappa, U, t, rhs, -1, t2);",
                               "schur(&L, kappa, U, t, rhs, 1, t2);"),
+    "shift_sign": ("out[i] += A->shift * in[i];", "out[i] -= A->shift * in[i];"),
     "force_projectors_swapped": ("cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */",
                                  "cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);  /* 1 - gamma */"),
     "force_no_boundary_sign": ("if (mu == 3 && L->tanti) s = -1.0;", ""),
@@ -50,6 +52,7 @@ PINS = [
     ("adjoint", lambda: pins.test_adjoint_and_gamma5_hermiticity()),
     ("dense", lambda: pins.test_dense_brute_force((2, 2, 2, 4), True)),
     ("cg_free", lambda: pins.test_cg_free_field_inverse()),
+    ("shifted_cg", lambda: shift_pins.test_shifted_cg_against_dense(True)),
     ("force_derivative", lambda: force_pins.test_force_is_the_derivative_of_the_action(True)),
     ("force_covariance", lambda: force_pins.test_force_gauge_covariance()),
 ]
