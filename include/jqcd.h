@@ -338,6 +338,29 @@ JQCD_API jqcd_status jqcd_fermi_force_dev(jqcd_ctx *ctx, uint64_t gauge_id, doub
                                           void *stream);
 JQCD_API jqcd_status jqcd_linkfield_bytes(const jqcd_lattice *lat, size_t *bytes);
 
+/* ---- multi-shift CG (rational HMC; the paper lists RHMC among its
+ * algorithms) -------------------------------------------------------------
+ * Solves (Mhat^dag Mhat + shifts[i]) x_i = rhs, i < nshift (1..32), on the
+ * even sites in one Krylov space: one operator application per iteration for
+ * all shifts (double-word arithmetic; params: eo = 1, mode JQCD_CG_DW, kappa,
+ * tol, maxiter).  Shifts must be finite and >= 0.  Shift i stops once its
+ * recursive residual |zeta_i r| <= tol |rhs|; every x_i's true residual
+ * ||rhs - (A + sigma_i) x_i|| / ||rhs|| is recomputed and reported in
+ * infos[i] (iters = the iteration at which shift i stopped).  Returns
+ * JQCD_OK when every shift meets tol, JQCD_ENOCONV otherwise (x_i hold the
+ * last iterates), JQCD_EBREAKDOWN on a non-positive <p, Ap>. */
+/* rhs: host canonical spinor (odd sites ignored); x[i]: host canonical
+ * spinors written with zeros on the odd sites; infos: NULL or nshift entries. */
+JQCD_API jqcd_status jqcd_cg_multishift(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                        int32_t nshift, const double *shifts, const double *rhs,
+                                        double *const *x, jqcd_solve_info *infos);
+/* Device form: rhs_even one JQCD_PREC_DW parity; x_even[i] caller-owned
+ * JQCD_PREC_DW parity buffers (a host array of nshift device pointers).
+ * Synchronises `stream` before return. */
+JQCD_API jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                            int32_t nshift, const double *shifts, const void *rhs_even,
+                                            void *const *x_even, jqcd_solve_info *infos, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -13,6 +13,7 @@
 #include <memory>
 #include <string>
 #include <vector>
+#include <vector>
 
 #include <mutex>
 
@@ -667,6 +668,92 @@ jqcd_status jqcd_linkfield_bytes(const jqcd_lattice *lat, size_t *bytes) {
   Geom g;
   if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
   *bytes = (size_t)72 * 16 * g.vh;
+  return JQCD_OK;
+}
+
+}  // extern "C"
+
+// ---- multi-shift CG ------------------------------------------------------------
+extern "C" {
+
+jqcd_status jqcd_cg_multishift(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                               int32_t nshift, const double *shifts, const double *rhs, double *const *x,
+                               jqcd_solve_info *infos) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !shifts || !rhs || !x || nshift < 1 || nshift > kMsMaxShifts)
+    return fail(ctx, JQCD_EINVAL, "cg_multishift: bad argument");
+  for (int i = 0; i < nshift; ++i)
+    if (!x[i]) return fail(ctx, JQCD_EINVAL, "cg_multishift: x[%d] is NULL", i);
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_multishift(nshift), "multishift workspace alloc");
+  // per-shift solution buffers (one double-word parity each), kept for reuse
+  std::vector<float4 *> xs(nshift);
+  for (int i = 0; i < nshift; ++i) {
+    while ((int)G->ms_x.size() <= i) {
+      float4 *p = nullptr;
+      CK(G->alloc_t(&p, spinor_parity_bytes(PREC_DW, G->g.vh)), "multishift x alloc");
+      G->ms_x.push_back(p);
+    }
+    xs[i] = G->ms_x[i];
+  }
+  CK(cudaMemcpyAsync(G->canon, rhs, G->canon_bytes(), cudaMemcpyHostToDevice, s), "rhs H2D");
+  CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->vec_even(G->vrhs), G->vec_odd(G->vrhs), s), "rhs pack");
+  std::vector<jqcd_solve_info> inf(nshift);
+  std::string msg;
+  st = solve_multishift(*G, *params, nshift, shifts, xs.data(), s, inf.data(), &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    float4 *zero_odd = G->vec_odd(G->vt);
+    CK(launch_dw_zero(zero_odd, 12 * G->g.vh, s), "zero");
+    for (int i = 0; i < nshift; ++i) {
+      CK(launch_spinor_unpack(G->g, PREC_DW, xs[i], zero_odd, G->canon, s), "x unpack");
+      CK(cudaMemcpyAsync(x[i], G->canon, G->canon_bytes(), cudaMemcpyDeviceToHost, s), "x D2H");
+    }
+    CK(cudaStreamSynchronize(s), "multishift sync");
+  }
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int i = 0; i < nshift; ++i) {
+      infos[i] = inf[i];
+      infos[i].seconds = secs;
+    }
+  if (st != JQCD_OK) return fail(ctx, st, "cg_multishift: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                   int32_t nshift, const double *shifts, const void *rhs_even,
+                                   void *const *x_even, jqcd_solve_info *infos, void *stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !shifts || !rhs_even || !x_even || nshift < 1 || nshift > kMsMaxShifts)
+    return fail(ctx, JQCD_EINVAL, "cg_multishift_dev: bad argument");
+  std::vector<float4 *> xs(nshift);
+  for (int i = 0; i < nshift; ++i) {
+    if (!x_even[i]) return fail(ctx, JQCD_EINVAL, "cg_multishift_dev: x_even[%d] is NULL", i);
+    xs[i] = (float4 *)x_even[i];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_multishift(nshift), "multishift workspace alloc");
+  CK(launch_dw_copy(G->vec_even(G->vrhs), (const float4 *)rhs_even, 12 * G->g.vh, s), "copy rhs");
+  std::vector<jqcd_solve_info> inf(nshift);
+  std::string msg;
+  st = solve_multishift(*G, *params, nshift, shifts, xs.data(), s, inf.data(), &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (infos)
+    for (int i = 0; i < nshift; ++i) {
+      infos[i] = inf[i];
+      infos[i].seconds = secs;
+    }
+  if (st != JQCD_OK) return fail(ctx, st, "cg_multishift_dev: %s", msg.c_str());
   return JQCD_OK;
 }
 

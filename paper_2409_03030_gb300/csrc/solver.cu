@@ -31,6 +31,7 @@ constexpr int kMaxRestarts = 8;
 GaugeEntry::~GaugeEntry() {
   for (void *p : device_allocs) cudaFree(p);
   if (S_host) cudaFreeHost(S_host);
+  if (ms_S_host) cudaFreeHost(ms_S_host);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
 }

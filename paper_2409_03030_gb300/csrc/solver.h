@@ -7,6 +7,7 @@
 
 #include "jqcd.h"
 #include "kernels.h"
+#include "multishift.h"
 
 namespace jqcd {
 
@@ -35,6 +36,10 @@ struct GaugeEntry {
   // the double-word link-field result and its canonical host-layout staging
   float4 *feta = nullptr, *fX = nullptr, *fY = nullptr, *fout = nullptr;
   double *lcanon = nullptr;
+  // multi-shift CG workspace: per-shift search directions and scalars
+  std::vector<float4 *> ms_p, ms_x;  // ms_x: solutions of the host-buffer entry
+  MsScalars *ms_S = nullptr;
+  MsScalars *ms_S_host = nullptr;  // pinned mirror
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void *> device_allocs;
 
@@ -54,6 +59,7 @@ struct GaugeEntry {
   cudaError_t ensure_mixed(int hop_prec);
   cudaError_t ensure_f64();
   cudaError_t ensure_force();
+  cudaError_t ensure_multishift(int nshift);
   size_t linkfield_bytes() const { return (size_t)72 * 16 * g.vh; }  // [2][4][9][vh] float4
   size_t link_canon_bytes() const { return sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh); }
   int n_partials() const;

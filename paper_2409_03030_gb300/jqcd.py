@@ -112,6 +112,10 @@ _SIGNATURES = {
     "jqcd_fermi_force_xy": (_st, [_vp, _u64, ctypes.c_double, _dp, _dp, _dp]),
     "jqcd_fermi_force_dev": (_st, [_vp, _u64, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
     "jqcd_linkfield_bytes": (_st, [ctypes.POINTER(jqcd_lattice), ctypes.POINTER(ctypes.c_size_t)]),
+    "jqcd_cg_multishift": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp, _dp,
+                                 ctypes.POINTER(_dp), ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_cg_multishift_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp,
+                                     _vp, ctypes.POINTER(_vp), ctypes.POINTER(jqcd_solve_info), _vp]),
 }
 
 
@@ -337,6 +341,35 @@ class Gauge:
         if check:
             self.ctx.check(st, "jqcd_cg_solve")
         return x, info.as_dict(), st
+
+    # ---- multi-shift CG (RHMC) ----------------------------------------------------
+    def cg_multishift(self, rhs, kappa, shifts, tol=1e-10, maxiter=20000, check=True):
+        """Solve (Mhat^dag Mhat + shifts[i]) x_i = rhs (even sites) for all i at
+        once; returns (list of x_i, list of info dicts, status)."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
+        n = len(shifts)
+        sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+        xs = [np.zeros_like(rhs) for _ in range(n)]
+        xp = (_dp * n)(*[_host_ptr(x) for x in xs])
+        infos = (jqcd_solve_info * n)()
+        p = self.params(kappa, tol, maxiter, True, CG_DW)
+        st = jqcd_cg_multishift(self.ctx.h, self.id, ctypes.byref(p), n, sh, _host_ptr(rhs), xp, infos)
+        if check:
+            self.ctx.check(st, "jqcd_cg_multishift")
+        return xs, [i.as_dict() for i in infos], st
+
+    def cg_multishift_dev(self, rhs_even, x_evens, kappa, shifts, tol=1e-10, maxiter=20000, stream=None,
+                          check=True):
+        n = len(shifts)
+        sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
+        xp = (_vp * n)(*[_dev_ptr(x) for x in x_evens])
+        infos = (jqcd_solve_info * n)()
+        p = self.params(kappa, tol, maxiter, True, CG_DW)
+        st = jqcd_cg_multishift_dev(self.ctx.h, self.id, ctypes.byref(p), n, sh, _dev_ptr(rhs_even), xp, infos,
+                                    _stream_ptr(stream))
+        if check:
+            self.ctx.check(st, "jqcd_cg_multishift_dev")
+        return [i.as_dict() for i in infos], st
 
     # ---- fermion action and force (paper: evaluate_FermiAction, calc_UdSfdU) ----
     def link_shape(self):
