@@ -305,6 +305,28 @@ def bench_force(ctx, jqcd, synth, np, torch, stream, g, b):
     return res
 
 
+def bench_multishift(jqcd, g, stream, rhs_even):
+    """Multi-shift CG on the workload lattice: eight RHMC-like shifts of
+    Mhat^dag Mhat to 1e-10 in one Krylov space, against the same eight
+    systems solved one at a time (a one-shift solve each)."""
+    shifts = [1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.3]
+    xs = [g.empty(jqcd.PREC_DW) for _ in shifts]
+    g.cg_multishift_dev(rhs_even, xs, KAPPA, shifts, tol=TOL, stream=stream)  # warm-up
+    infos, st = g.cg_multishift_dev(rhs_even, xs, KAPPA, shifts, tol=TOL, stream=stream)
+    t_multi = infos[0]["gpu_seconds"]
+    t_single, it_single = 0.0, []
+    for i, sg in enumerate(shifts):
+        inf1, _ = g.cg_multishift_dev(rhs_even, [xs[i]], KAPPA, [sg], tol=TOL, stream=stream)
+        t_single += inf1[0]["gpu_seconds"]
+        it_single.append(inf1[0]["iters"])
+    return {"workload": "8 shifts 1e-4..0.3 of Mhat^dag Mhat, 24^3x48, kappa 0.12, tol 1e-10, double-word",
+            "multishift_s": round(t_multi, 4), "separate_s": round(t_single, 4),
+            "speedup": round(t_single / t_multi, 2), "iters": [i["iters"] for i in infos],
+            "iters_separate": it_single,
+            "max_true_rel_resid": max(i["true_rel_resid"] for i in infos), "status": st,
+            "hop_gbs": round(infos[0]["hop_bytes"] / t_multi / 1e9, 1)}
+
+
 def bench_batch(ctx, jqcd, synth, np):
     """12 point sources on 24^3x48 + 12 Gaussian sources on 16^4 (kappa 0.12,
     exp(i 0.3 H) links, tol 1e-10, FP16 inner): one jqcd_cg_solve_batch call
@@ -567,6 +589,7 @@ def run_gpu(args):
         g2.free()
 
     force = bench_force(ctx, jqcd, synth, np, torch, stream, g, b)
+    multishift = bench_multishift(jqcd, g, stream, be)
     batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
     serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
 
@@ -612,6 +635,7 @@ def run_gpu(args):
                            for k, v in hop_ms.items()},
             "dslash_sweep_gbs": sweep,
             "force": force,
+            "multishift": multishift,
             "batch": batch,
             "serve": serve,
         }
