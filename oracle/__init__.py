@@ -66,6 +66,11 @@ def _configure(lib):
     lib.jo_cg_shift.argtypes = [ip, c_int, c_double, dp, c_int, c_double, dp, dp, c_double, c_int,
                                 ip, dp]
     lib.jo_cg_shift.restype = c_int
+    lib.jo_stag_hop.argtypes = [ip, c_int, dp, dp, dp, c_int, c_int]
+    lib.jo_stag_dirac.argtypes = [ip, c_int, c_double, dp, dp, dp, c_int]
+    lib.jo_stag_solve.argtypes = [ip, c_int, c_double, dp, dp, dp, c_double, c_int, ip, dp, dp]
+    for name in ("jo_stag_hop", "jo_stag_dirac", "jo_stag_solve"):
+        getattr(lib, name).restype = c_int
     lib.jo_set_threads.argtypes = [c_int]
     lib.jo_fermi_force.argtypes = [ip, c_int, c_double, dp, dp, dp, dp]
     lib.jo_fermi_force.restype = c_int
@@ -250,6 +255,42 @@ def fermi_force(dims, U, eta, kappa, tol=1e-12, t_antiperiodic=True):
     S, X = fermi_action(dims, U, eta, kappa, tol, t_antiperiodic)
     Y = dirac(dims, U, X, kappa, t_antiperiodic=t_antiperiodic)
     return S, fermi_force_xy(dims, U, X, Y, kappa, t_antiperiodic)
+
+
+# ---- staggered fermions: one colour vector per site, shape [t, z, y, x, colour] ----
+def _colour(dims):
+    nx, ny, nz, nt = dims
+    return np.zeros((nt, nz, ny, nx, 3), dtype=np.complex128)
+
+
+def stag_hop(dims, U, psi, dagger=False, out_parity=-1, t_antiperiodic=True):
+    """D_hop psi = (1/2) sum_mu eta_mu [U psi(x+mu) - U^dag psi(x-mu)] (dagger: -D_hop psi)."""
+    d, cd = _dims(dims)
+    out = _colour(d)
+    _check(_load().jo_stag_hop(cd, int(t_antiperiodic), _p(U), _p(psi), _p(out), int(dagger),
+                               int(out_parity)), "jo_stag_hop")
+    return out
+
+
+def stag_dirac(dims, U, psi, mass, dagger=False, t_antiperiodic=True):
+    """Staggered D psi = m psi + D_hop psi (dagger: m psi - D_hop psi)."""
+    d, cd = _dims(dims)
+    out = _colour(d)
+    _check(_load().jo_stag_dirac(cd, int(t_antiperiodic), float(mass), _p(U), _p(psi), _p(out),
+                                 int(dagger)), "jo_stag_dirac")
+    return out
+
+
+def stag_solve(dims, U, b, mass, tol=1e-12, maxiter=100000, t_antiperiodic=True):
+    """Solve staggered D x = b by textbook CG on D^dag D.
+    Returns (x, iters, system_true_rel, full_rel, converged)."""
+    d, cd = _dims(dims)
+    x = _colour(d)
+    it, sr, fr = ctypes.c_int(0), ctypes.c_double(0), ctypes.c_double(0)
+    rc = _check(_load().jo_stag_solve(cd, int(t_antiperiodic), float(mass), _p(U), _p(b), _p(x), float(tol),
+                                      int(maxiter), ctypes.byref(it), ctypes.byref(sr), ctypes.byref(fr)),
+                "jo_stag_solve")
+    return x, it.value, sr.value, fr.value, rc == 0
 
 
 def set_threads(n: int = 0) -> int:

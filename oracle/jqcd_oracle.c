@@ -562,3 +562,132 @@ int jo_fermi_force_links(const int dims[4], int tanti, double kappa, const doubl
   }
   return 0;
 }
+
+/* ---- staggered fermions (paper: Dirac_operator "staggered" with "mass") ----
+ * Kogut-Susskind operator on one colour vector per site:
+ *   (D psi)(x) = m psi(x) + (1/2) sum_mu eta_mu(x) [ U_mu(x) psi(x+mu)
+ *                                                  - U_mu(x-mu)^dagger psi(x-mu) ]
+ * eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) (mu = x, y, z, t), and the same
+ * antiperiodic time boundary sign as the Wilson operator.  The hopping part is
+ * anti-Hermitian, so D^dagger = m - D_hop.  Layout: colour c of site s at
+ * c + 3*s (complex). */
+static inline int stag_eta(const int64_t c[4], int mu) {
+  int64_t s = 0;
+  for (int nu = 0; nu < mu; ++nu) s += c[nu];
+  return (s & 1) ? -1 : 1;
+}
+
+/* out = a_in * in + b_hop * D_hop in at sites of parity out_parity (all if < 0);
+ * sgn = +1 for D_hop, -1 for D_hop^dagger = -D_hop. */
+static void stag_hop_axpy(const lat_t *L, const double *U, const double *in, double *out, int sgn,
+                          int out_parity, double a_in, double b_hop) {
+#pragma omp parallel for schedule(static)
+  for (int64_t x = 0; x < L->V; ++x) {
+    int64_t c[4];
+    site_coords(L, x, c);
+    if (out_parity >= 0 && site_parity(c) != out_parity) {
+      for (int a = 0; a < 3; ++a) st(out, a + 3 * x, cm(0, 0));
+      continue;
+    }
+    cplx h[3] = {cm(0, 0), cm(0, 0), cm(0, 0)};
+    for (int mu = 0; mu < 4; ++mu) {
+      const double eta = stag_eta(c, mu);
+      for (int dir = 0; dir < 2; ++dir) {
+        int64_t nc[4] = {c[0], c[1], c[2], c[3]};
+        double bc = 1.0;
+        if (dir == 0) {
+          nc[mu] = c[mu] + 1;
+          if (nc[mu] == L->n[mu]) { nc[mu] = 0; if (mu == 3 && L->tanti) bc = -1.0; }
+        } else {
+          nc[mu] = c[mu] - 1;
+          if (nc[mu] < 0) { nc[mu] = L->n[mu] - 1; if (mu == 3 && L->tanti) bc = -1.0; }
+        }
+        const int64_t y = site_index(L, nc);
+        const double f = 0.5 * eta * bc * (dir == 0 ? 1.0 : -1.0) * sgn;
+        for (int a = 0; a < 3; ++a) {
+          cplx acc = cm(0, 0);
+          for (int b = 0; b < 3; ++b) {
+            const cplx w = (dir == 0) ? link(L, U, mu, x, a, b) : cconj(link(L, U, mu, y, b, a));
+            acc = cadd(acc, cmul(w, ld(in, b + 3 * y)));
+          }
+          h[a] = cadd(h[a], cscale(acc, f));
+        }
+      }
+    }
+    for (int a = 0; a < 3; ++a) {
+      cplx v = cscale(h[a], b_hop);
+      if (a_in != 0.0) v = cadd(v, cscale(ld(in, a + 3 * x), a_in));
+      st(out, a + 3 * x, v);
+    }
+  }
+}
+
+/* out = D_hop in (dagger: D_hop^dagger) at sites of parity out_parity (all if < 0). */
+int jo_stag_hop(const int dims[4], int tanti, const double *U, const double *in, double *out, int dagger,
+                int out_parity) {
+  lat_t L;
+  if (lat_init(&L, dims, tanti) || !U || !in || !out || in == out) return -1;
+  stag_hop_axpy(&L, U, in, out, dagger ? -1 : 1, out_parity, 0.0, 1.0);
+  return 0;
+}
+
+/* out = D in = m in + D_hop in (dagger: m in - D_hop in), whole lattice. */
+int jo_stag_dirac(const int dims[4], int tanti, double mass, const double *U, const double *in, double *out,
+                  int dagger) {
+  lat_t L;
+  if (lat_init(&L, dims, tanti) || !U || !in || !out || in == out) return -1;
+  stag_hop_axpy(&L, U, in, out, dagger ? -1 : 1, -1, mass, 1.0);
+  return 0;
+}
+
+/* Solve D x = b by textbook CG on D^dag D x = D^dag b (whole lattice, FP64),
+ * the plain definition of a staggered solve (paper: solve_DinvX! with the
+ * staggered operator).  x0 = 0.  *true_rel = ||D^dag b - D^dag D x|| / ||D^dag b||,
+ * *full_rel = ||b - D x|| / ||b||.  Returns 0 on convergence, 1 at maxiter. */
+int jo_stag_solve(const int dims[4], int tanti, double mass, const double *U, const double *b, double *x,
+                  double tol, int maxiter, int *iters, double *true_rel, double *full_rel) {
+  lat_t L;
+  if (lat_init(&L, dims, tanti) || !U || !b || !x) return -1;
+  const int64_t n = 6 * L.V;
+  double *rhs = (double *)malloc(sizeof(double) * n), *r = (double *)malloc(sizeof(double) * n);
+  double *p = (double *)malloc(sizeof(double) * n), *Ap = (double *)malloc(sizeof(double) * n);
+  double *t = (double *)malloc(sizeof(double) * n);
+  if (!rhs || !r || !p || !Ap || !t) { free(rhs); free(r); free(p); free(Ap); free(t); return -2; }
+#define STAG_A(in_, out_) do { stag_hop_axpy(&L, U, in_, t, 1, -1, mass, 1.0); \
+                               stag_hop_axpy(&L, U, t, out_, -1, -1, mass, 1.0); } while (0)
+  stag_hop_axpy(&L, U, b, rhs, -1, -1, mass, 1.0);  /* D^dag b */
+  memset(x, 0, sizeof(double) * n);
+  memcpy(r, rhs, sizeof(double) * n);
+  memcpy(p, r, sizeof(double) * n);
+  const double bnorm = sqrt(norm2(rhs, n));
+  double rr = norm2(r, n);
+  int k = 0, rc = 1;
+  if (bnorm == 0.0 || sqrt(rr) <= tol * bnorm) rc = 0;
+  while (rc != 0 && k < maxiter) {
+    STAG_A(p, Ap);
+    const double alpha = rr / redot(p, Ap, n);
+    for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * Ap[i];
+    const double rr_new = norm2(r, n);
+    ++k;
+    if (sqrt(rr_new) <= tol * bnorm) { rc = 0; break; }
+    const double beta = rr_new / rr;
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+    rr = rr_new;
+  }
+  if (iters) *iters = k;
+  if (true_rel) {
+    STAG_A(x, Ap);
+    for (int64_t i = 0; i < n; ++i) r[i] = rhs[i] - Ap[i];
+    *true_rel = bnorm > 0 ? sqrt(norm2(r, n)) / bnorm : 0.0;
+  }
+  if (full_rel) {
+    stag_hop_axpy(&L, U, x, t, 1, -1, mass, 1.0);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    const double bn = sqrt(norm2(b, n));
+    *full_rel = bn > 0 ? sqrt(norm2(r, n)) / bn : 0.0;
+  }
+#undef STAG_A
+  free(rhs); free(r); free(p); free(Ap); free(t);
+  return rc;
+}

@@ -107,6 +107,17 @@ def gaussian_spinor(dims, seed: int = 1) -> np.ndarray:
     return out
 
 
+def gaussian_colour(dims, seed: int = 1) -> np.ndarray:
+    """Gaussian staggered field (one colour vector per site, [t, z, y, x, colour]):
+    spin component 0 of gaussian_spinor(dims, seed), re, im ~ N(0, 1/2)."""
+    return np.ascontiguousarray(gaussian_spinor(dims, seed)[0])
+
+
+def colour_shape(dims):
+    nx, ny, nz, nt = (int(v) for v in dims)
+    return (nt, nz, ny, nx, 3)
+
+
 def point_source(dims, spin: int, colour: int) -> np.ndarray:
     """delta at site (0,0,0,0), spin index `spin`, colour index `colour`."""
     d, cd = _dims(dims)
