@@ -361,6 +361,46 @@ JQCD_API jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, co
                                             int32_t nshift, const double *shifts, const void *rhs_even,
                                             void *const *x_even, jqcd_solve_info *infos, void *stream);
 
+/* ---- staggered fermions (paper: Dirac_operator "staggered" with "mass") ----
+ * Kogut-Susskind operator on one colour vector per site:
+ *   (D psi)(x) = m psi(x) + D_hop psi,
+ *   (D_hop psi)(x) = 1/2 sum_mu eta_mu(x) [U_mu(x) psi(x+mu) - U_mu(x-mu)^dag psi(x-mu)],
+ *   eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) (mu = x, y, z, t),
+ * with the lattice's time boundary sign on hops across t = NT-1 <-> 0.  D_hop
+ * is anti-Hermitian: D^dag = m - D_hop.  Host layout: colour c of site s
+ * (s = ix + NX*(iy + NY*(iz + NZ*it))) at c + 3*s, complex doubles (3*V).
+ * Device layout: per parity three double-word chunks per site
+ * (jqcd_staggered_bytes), the links of the uploaded gauge field.  Arithmetic
+ * is double-word (FP64-class). */
+JQCD_API jqcd_status jqcd_staggered_bytes(const jqcd_lattice *lat, size_t *bytes_per_parity);
+JQCD_API jqcd_status jqcd_staggered_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, void *dev_even,
+                                         void *dev_odd, void *stream);
+/* Synchronises `stream` before return. */
+JQCD_API jqcd_status jqcd_staggered_unpack(jqcd_ctx *ctx, uint64_t gauge_id, const void *dev_even,
+                                           const void *dev_odd, double *host, void *stream);
+/* out_p = a * x_p + b * D_hop(p <- 1-p) in  (dagger: -D_hop); x may be NULL;
+ * norm2_dev (device double, may be NULL) receives ||out_p||^2.  in and out
+ * must not alias.  Asynchronous on `stream`. */
+JQCD_API jqcd_status jqcd_staggered_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t out_parity,
+                                              int32_t dagger, const void *in, const void *x, void *out, double a,
+                                              double b, double *norm2_dev, void *stream);
+/* Whole lattice: out = D in (dagger: D^dag in) = m in +- D_hop in. */
+JQCD_API jqcd_status jqcd_staggered_apply(jqcd_ctx *ctx, uint64_t gauge_id, double mass, int32_t dagger,
+                                          const void *in_even, const void *in_odd, void *out_even, void *out_odd,
+                                          void *stream);
+/* Solve D x = b (paper: solve_DinvX! with the staggered operator): CG on the
+ * even-odd system (m^2 - D_eo D_oe) x_e = m b_e - D_eo b_o (Hermitian
+ * positive definite), x_o = (b_o - D_oe x_e) / m.  params: tol (checked on the
+ * recomputed residual of that system), maxiter, verbose; kappa, eo, mode are
+ * ignored (always even-odd, double-word).  mass > 0.  b, x: host (3*V
+ * complex doubles; b copied, x written).  info->full_rel_resid = ||b - Dx||/||b||. */
+JQCD_API jqcd_status jqcd_staggered_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                          double mass, const double *b, double *x, jqcd_solve_info *info);
+/* The same on device fields (JQCD staggered double-word parities). */
+JQCD_API jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                              double mass, const void *b_even, const void *b_odd, void *x_even,
+                                              void *x_odd, jqcd_solve_info *info, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

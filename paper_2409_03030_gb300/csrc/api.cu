@@ -22,6 +22,7 @@
 #include "kernels.h"
 #include "serve.h"
 #include "solver.h"
+#include "staggered.h"
 
 using namespace jqcd;
 
@@ -754,6 +755,152 @@ jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_
       infos[i].seconds = secs;
     }
   if (st != JQCD_OK) return fail(ctx, st, "cg_multishift_dev: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+}  // extern "C"
+
+// ---- staggered fermions ------------------------------------------------------------
+extern "C" {
+
+jqcd_status jqcd_staggered_bytes(const jqcd_lattice *lat, size_t *bytes) {
+  if (!bytes) return JQCD_EINVAL;
+  Geom g;
+  if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
+  *bytes = stag_parity_bytes(g.vh);
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, void *dev_even,
+                                void *dev_odd, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!host || !dev_even || !dev_odd) return fail(ctx, JQCD_EINVAL, "staggered_pack: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_canon(), "staging alloc");
+  const size_t bytes = sizeof(double) * 2 * 3 * (size_t)(2 * G->g.vh);
+  CK(cudaMemcpyAsync(G->canon, host, bytes, cudaMemcpyHostToDevice, s), "H2D");
+  CK(launch_stag_pack(G->g, G->canon, (float4 *)dev_even, (float4 *)dev_odd, s), "pack");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_unpack(jqcd_ctx *ctx, uint64_t gauge_id, const void *dev_even, const void *dev_odd,
+                                  double *host, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!host || !dev_even || !dev_odd) return fail(ctx, JQCD_EINVAL, "staggered_unpack: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_canon(), "staging alloc");
+  const size_t bytes = sizeof(double) * 2 * 3 * (size_t)(2 * G->g.vh);
+  CK(launch_stag_unpack(G->g, (const float4 *)dev_even, (const float4 *)dev_odd, G->canon, s), "unpack");
+  CK(cudaMemcpyAsync(host, G->canon, bytes, cudaMemcpyDeviceToHost, s), "D2H");
+  CK(cudaStreamSynchronize(s), "unpack sync");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t out_parity, int32_t dagger,
+                                     const void *in, const void *x, void *out, double a, double b,
+                                     double *norm2_dev, void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in || !out || in == out || (out_parity != 0 && out_parity != 1))
+    return fail(ctx, JQCD_EINVAL, "staggered_dslash_eo: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  double *parts = nullptr;
+  if (norm2_dev) {
+    CK(G->ensure_reduce(), "reduce alloc");
+    parts = G->partials;
+  }
+  CK(launch_stag_hop(G->g, out_parity, dagger != 0, (const float4 *)in, (const float4 *)x, (float4 *)out,
+                     (const float4 *)G->gauge_dw, a, b, parts, s), "staggered hop");
+  if (norm2_dev) CK(launch_finalize_sum(parts, (int)stag_blocks(G->g.vh), norm2_dev, s), "norm");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_apply(jqcd_ctx *ctx, uint64_t gauge_id, double mass, int32_t dagger,
+                                 const void *in_even, const void *in_odd, void *out_even, void *out_odd,
+                                 void *stream) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!in_even || !in_odd || !out_even || !out_odd || in_even == out_even || in_odd == out_odd)
+    return fail(ctx, JQCD_EINVAL, "staggered_apply: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const float4 *U = (const float4 *)G->gauge_dw;
+  CK(launch_stag_hop(G->g, 0, dagger != 0, (const float4 *)in_odd, (const float4 *)in_even, (float4 *)out_even,
+                     U, mass, 1.0, nullptr, s), "staggered hop");
+  CK(launch_stag_hop(G->g, 1, dagger != 0, (const float4 *)in_even, (const float4 *)in_odd, (float4 *)out_odd,
+                     U, mass, 1.0, nullptr, s), "staggered hop");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params, double mass,
+                                 const double *b, double *x, jqcd_solve_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !b || !x) return fail(ctx, JQCD_EINVAL, "staggered_solve: bad argument");
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_staggered(), "staggered workspace alloc");
+  const int64_t n = 3 * G->g.vh;
+  const size_t bytes = sizeof(double) * 2 * 3 * (size_t)(2 * G->g.vh);
+  CK(cudaMemcpyAsync(G->canon, b, bytes, cudaMemcpyHostToDevice, s), "b H2D");
+  CK(launch_stag_pack(G->g, G->canon, G->sb, G->sb + n, s), "b pack");
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  std::string msg;
+  st = solve_staggered(*G, mass, *params, s, &inf, &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    CK(launch_stag_unpack(G->g, G->sx, G->sx + n, G->canon, s), "x unpack");
+    CK(cudaMemcpyAsync(x, G->canon, bytes, cudaMemcpyDeviceToHost, s), "x D2H");
+    CK(cudaStreamSynchronize(s), "solve sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (st != JQCD_OK) return fail(ctx, st, "staggered_solve: %s", msg.c_str());
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
+                                     double mass, const void *b_even, const void *b_odd, void *x_even, void *x_odd,
+                                     jqcd_solve_info *info, void *stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!params || !b_even || !b_odd || !x_even || !x_odd)
+    return fail(ctx, JQCD_EINVAL, "staggered_solve_dev: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(G->ensure_staggered(), "staggered workspace alloc");
+  const int64_t n = 3 * G->g.vh;
+  CK(launch_dw_copy(G->sb, (const float4 *)b_even, n, s), "copy b");
+  CK(launch_dw_copy(G->sb + n, (const float4 *)b_odd, n, s), "copy b");
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  std::string msg;
+  st = solve_staggered(*G, mass, *params, s, &inf, &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    CK(launch_dw_copy((float4 *)x_even, G->sx, n, s), "copy x");
+    CK(launch_dw_copy((float4 *)x_odd, G->sx + n, n, s), "copy x");
+    CK(cudaStreamSynchronize(s), "solve sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (st != JQCD_OK) return fail(ctx, st, "staggered_solve_dev: %s", msg.c_str());
   return JQCD_OK;
 }
 

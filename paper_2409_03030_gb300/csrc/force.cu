@@ -198,7 +198,8 @@ __global__ void gamma5_dw_kernel(float4 *out, const float4 *in, int64_t vh) {
 
 // Per-block partial of Re <a, b> over n double-word complex numbers.
 __global__ void dw_dot_re_kernel(const float4 *__restrict__ a, const float4 *__restrict__ b, int64_t n,
-                                 double *partials) {
+                                 double *partials, const int *guard) {
+  if (guard && *guard) return;  // uniform across the grid
   dwacc A{0.f, 0.f};
   bool first = true;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
@@ -259,9 +260,9 @@ cudaError_t launch_gamma5_dw(float4 *out, const float4 *in, int64_t vh, cudaStre
 }
 
 cudaError_t launch_dw_dot_re(const float4 *a, const float4 *b, int64_t n, double *partials, int nblocks,
-                             cudaStream_t s) {
+                             cudaStream_t s, const int *guard) {
   note_launch();
-  dw_dot_re_kernel<<<nblocks, kBlasThreads, 0, s>>>(a, b, n, partials);
+  dw_dot_re_kernel<<<nblocks, kBlasThreads, 0, s>>>(a, b, n, partials, guard);
   return cudaGetLastError();
 }
 

@@ -130,9 +130,10 @@ cudaError_t launch_fermi_force(const Geom &g, const float4 *xe, const float4 *xo
                                cudaStream_t s);
 // out = gamma5 in, whole-lattice double-word spinor (24 vh chunks); in place allowed.
 cudaError_t launch_gamma5_dw(float4 *out, const float4 *in, int64_t vh, cudaStream_t s);
-// Per-block partials of Re <a, b> over n double-word complex numbers.
+// Per-block partials of Re <a, b> over n double-word complex numbers (skipped
+// when guard is set and *guard != 0).
 cudaError_t launch_dw_dot_re(const float4 *a, const float4 *b, int64_t n, double *partials, int nblocks,
-                             cudaStream_t s);
+                             cudaStream_t s, const int *guard = nullptr);
 // Double-word link field -> canonical host-layout links (complex double).
 cudaError_t launch_linkfield_unpack(const Geom &g, const float4 *dwf, double *canon, cudaStream_t s);
 

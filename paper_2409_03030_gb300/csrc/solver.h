@@ -40,6 +40,9 @@ struct GaugeEntry {
   std::vector<float4 *> ms_p, ms_x;  // ms_x: solutions of the host-buffer entry
   MsScalars *ms_S = nullptr;
   MsScalars *ms_S_host = nullptr;  // pinned mirror
+  // staggered workspace (double-word, whole lattice: even half then odd half)
+  float4 *sb = nullptr, *sx = nullptr, *sr = nullptr, *sp = nullptr, *sAp = nullptr, *st = nullptr,
+         *srhs = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void *> device_allocs;
 
@@ -60,6 +63,7 @@ struct GaugeEntry {
   cudaError_t ensure_f64();
   cudaError_t ensure_force();
   cudaError_t ensure_multishift(int nshift);
+  cudaError_t ensure_staggered();
   size_t linkfield_bytes() const { return (size_t)72 * 16 * g.vh; }  // [2][4][9][vh] float4
   size_t link_canon_bytes() const { return sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh); }
   int n_partials() const;

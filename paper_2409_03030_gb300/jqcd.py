@@ -112,6 +112,16 @@ _SIGNATURES = {
     "jqcd_fermi_force_xy": (_st, [_vp, _u64, ctypes.c_double, _dp, _dp, _dp]),
     "jqcd_fermi_force_dev": (_st, [_vp, _u64, ctypes.c_double, _vp, _vp, _vp, _vp, _vp, _vp]),
     "jqcd_linkfield_bytes": (_st, [ctypes.POINTER(jqcd_lattice), ctypes.POINTER(ctypes.c_size_t)]),
+    "jqcd_staggered_bytes": (_st, [ctypes.POINTER(jqcd_lattice), ctypes.POINTER(ctypes.c_size_t)]),
+    "jqcd_staggered_pack": (_st, [_vp, _u64, _dp, _vp, _vp, _vp]),
+    "jqcd_staggered_unpack": (_st, [_vp, _u64, _vp, _vp, _dp, _vp]),
+    "jqcd_staggered_dslash_eo": (_st, [_vp, _u64, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp, ctypes.c_double,
+                                       ctypes.c_double, _vp, _vp]),
+    "jqcd_staggered_apply": (_st, [_vp, _u64, ctypes.c_double, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]),
+    "jqcd_staggered_solve": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_double, _dp, _dp,
+                                   ctypes.POINTER(jqcd_solve_info)]),
+    "jqcd_staggered_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_double, _vp, _vp,
+                                       _vp, _vp, ctypes.POINTER(jqcd_solve_info), _vp]),
     "jqcd_cg_multishift": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp, _dp,
                                  ctypes.POINTER(_dp), ctypes.POINTER(jqcd_solve_info)]),
     "jqcd_cg_multishift_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp,
@@ -341,6 +351,65 @@ class Gauge:
         if check:
             self.ctx.check(st, "jqcd_cg_solve")
         return x, info.as_dict(), st
+
+    # ---- staggered fermions (paper: Dirac_operator "staggered") ----------------------
+    def colour_shape(self):
+        nx, ny, nz, nt = self.dims
+        return (nt, nz, ny, nx, 3)
+
+    def stag_bytes(self) -> int:
+        n = ctypes.c_size_t(0)
+        lat = lattice(self.dims, self.t_antiperiodic)
+        if jqcd_staggered_bytes(ctypes.byref(lat), ctypes.byref(n)) != OK:
+            raise ValueError("bad lattice")
+        return n.value
+
+    def stag_empty(self):
+        import torch
+        return torch.empty(self.stag_bytes(), dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
+
+    def stag_pack(self, host, stream=None):
+        host = np.ascontiguousarray(host, dtype=np.complex128)
+        ev, od = self.stag_empty(), self.stag_empty()
+        self.ctx.check(jqcd_staggered_pack(self.ctx.h, self.id, _host_ptr(host), _dev_ptr(ev), _dev_ptr(od),
+                                           _stream_ptr(stream)), "jqcd_staggered_pack")
+        return ev, od
+
+    def stag_unpack(self, even, odd, stream=None):
+        out = np.empty(self.colour_shape(), dtype=np.complex128)
+        self.ctx.check(jqcd_staggered_unpack(self.ctx.h, self.id, _dev_ptr(even), _dev_ptr(odd), _host_ptr(out),
+                                             _stream_ptr(stream)), "jqcd_staggered_unpack")
+        return out
+
+    def stag_dslash_eo(self, out_parity, dagger, inp, x, out, a=0.0, b=1.0, norm2=None, stream=None):
+        self.ctx.check(jqcd_staggered_dslash_eo(self.ctx.h, self.id, int(out_parity), int(dagger), _dev_ptr(inp),
+                                                _dev_ptr(x), _dev_ptr(out), float(a), float(b), _dev_ptr(norm2),
+                                                _stream_ptr(stream)), "jqcd_staggered_dslash_eo")
+
+    def stag_apply(self, mass, dagger, ie, io, oe, oo, stream=None):
+        self.ctx.check(jqcd_staggered_apply(self.ctx.h, self.id, float(mass), int(dagger), _dev_ptr(ie), _dev_ptr(io),
+                                            _dev_ptr(oe), _dev_ptr(oo), _stream_ptr(stream)), "jqcd_staggered_apply")
+
+    def stag_solve(self, b, mass, tol=1e-10, maxiter=20000, check=True):
+        """Solve the staggered D x = b from host arrays; returns (x, info dict, status)."""
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+        x = np.zeros_like(b)
+        p = self.params(0.0, tol, maxiter, True, CG_DW)
+        info = jqcd_solve_info()
+        st = jqcd_staggered_solve(self.ctx.h, self.id, ctypes.byref(p), float(mass), _host_ptr(b), _host_ptr(x),
+                                  ctypes.byref(info))
+        if check:
+            self.ctx.check(st, "jqcd_staggered_solve")
+        return x, info.as_dict(), st
+
+    def stag_solve_dev(self, be, bo, xe, xo, mass, tol=1e-10, maxiter=20000, stream=None, check=True):
+        p = self.params(0.0, tol, maxiter, True, CG_DW)
+        info = jqcd_solve_info()
+        st = jqcd_staggered_solve_dev(self.ctx.h, self.id, ctypes.byref(p), float(mass), _dev_ptr(be), _dev_ptr(bo),
+                                      _dev_ptr(xe), _dev_ptr(xo), ctypes.byref(info), _stream_ptr(stream))
+        if check:
+            self.ctx.check(st, "jqcd_staggered_solve_dev")
+        return info.as_dict(), st
 
     # ---- multi-shift CG (RHMC) ----------------------------------------------------
     def cg_multishift(self, rhs, kappa, shifts, tol=1e-10, maxiter=20000, check=True):
