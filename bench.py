@@ -305,6 +305,39 @@ def bench_force(ctx, jqcd, synth, np, torch, stream, g, b):
     return res
 
 
+def bench_staggered(jqcd, synth, torch, stream, g):
+    """Staggered operator on the workload lattice and links: the double-word
+    hop alone (algorithmic bytes per output site: colour vector in once, 8
+    double-word links, out = 1248 B) and the even-odd solve of D x = b to
+    1e-10 at m = 0.05."""
+    b = synth.gaussian_colour(DIMS, seed=91)
+    with torch.cuda.stream(stream):
+        be, bo = g.stag_pack(b, stream=stream)
+        out = g.stag_empty()
+    for _ in range(5):
+        g.stag_dslash_eo(0, 0, bo, None, out, stream=stream)
+    stream.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 40
+    a0.record(stream)
+    for _ in range(n):
+        g.stag_dslash_eo(0, 0, bo, None, out, stream=stream)
+    a1.record(stream)
+    stream.synchronize()
+    us = a0.elapsed_time(a1) / n * 1e3
+    vh = vol(DIMS) // 2
+    hbm, _ = peaks()
+    gbs = vh * 1248 / us / 1e3
+    with torch.cuda.stream(stream):
+        xe, xo = g.stag_empty(), g.stag_empty()
+    g.stag_solve_dev(be, bo, xe, xo, 0.05, tol=TOL, stream=stream)  # warm-up
+    info, st = g.stag_solve_dev(be, bo, xe, xo, 0.05, tol=TOL, stream=stream)
+    return {"hop_us": round(us, 1), "hop_gbs": round(gbs, 1), "hop_hbm_frac": round(gbs / hbm, 4),
+            "solve": {"mass": 0.05, "s": round(info["gpu_seconds"], 4), "iters": info["iters"],
+                      "true_rel_resid": info["true_rel_resid"], "full_rel_resid": info["full_rel_resid"],
+                      "status": st}}
+
+
 def bench_multishift(jqcd, g, stream, rhs_even):
     """Multi-shift CG on the workload lattice: eight RHMC-like shifts of
     Mhat^dag Mhat to 1e-10 in one Krylov space, against the same eight
@@ -590,6 +623,7 @@ def run_gpu(args):
 
     force = bench_force(ctx, jqcd, synth, np, torch, stream, g, b)
     multishift = bench_multishift(jqcd, g, stream, be)
+    staggered = bench_staggered(jqcd, synth, torch, stream, g)
     batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
     serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
 
@@ -636,6 +670,7 @@ def run_gpu(args):
             "dslash_sweep_gbs": sweep,
             "force": force,
             "multishift": multishift,
+            "staggered": staggered,
             "batch": batch,
             "serve": serve,
         }
