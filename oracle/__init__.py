@@ -71,6 +71,10 @@ def _configure(lib):
     lib.jo_stag_solve.argtypes = [ip, c_int, c_double, dp, dp, dp, c_double, c_int, ip, dp, dp]
     for name in ("jo_stag_hop", "jo_stag_dirac", "jo_stag_solve"):
         getattr(lib, name).restype = c_int
+    lib.jo_plaquette_sum.argtypes = [ip, dp]
+    lib.jo_plaquette_sum.restype = c_double
+    lib.jo_gauge_force.argtypes = [ip, c_double, dp, dp]
+    lib.jo_gauge_force.restype = c_int
     lib.jo_set_threads.argtypes = [c_int]
     lib.jo_fermi_force.argtypes = [ip, c_int, c_double, dp, dp, dp, dp]
     lib.jo_fermi_force.restype = c_int
@@ -291,6 +295,108 @@ def stag_solve(dims, U, b, mass, tol=1e-12, maxiter=100000, t_antiperiodic=True)
                                       int(maxiter), ctypes.byref(it), ctypes.byref(sr), ctypes.byref(fr)),
                 "jo_stag_solve")
     return x, it.value, sr.value, fr.value, rc == 0
+
+
+# ---- pure-gauge part of the HMC (plaquette action, its force) -------------------
+def plaquette_sum(dims, U):
+    """sum over x and mu < nu of Re Tr P_munu(x)."""
+    d, cd = _dims(dims)
+    return float(_load().jo_plaquette_sum(cd, _p(U)))
+
+
+def gauge_action(dims, U, beta):
+    """S_g = -(beta/3) sum Re Tr P (the paper's plaquette gauge action, Sg = -evaluate/NC)."""
+    return -beta / 3.0 * plaquette_sum(dims, U)
+
+
+def gauge_force(dims, U, beta):
+    """U dS_g/dU for every link (convention dS = Re Tr[(dS/dU) dU])."""
+    d, cd = _dims(dims)
+    out = np.zeros_like(U)
+    _check(_load().jo_gauge_force(cd, float(beta), _p(U), _p(out)), "jo_gauge_force")
+    return out
+
+
+# Gell-Mann generators T^a = lambda^a / 2 (Tr T^a T^b = delta_ab / 2)
+def gell_mann():
+    l = np.zeros((8, 3, 3), dtype=complex)
+    l[0][0, 1] = l[0][1, 0] = 1
+    l[1][0, 1], l[1][1, 0] = -1j, 1j
+    l[2][0, 0], l[2][1, 1] = 1, -1
+    l[3][0, 2] = l[3][2, 0] = 1
+    l[4][0, 2], l[4][2, 0] = -1j, 1j
+    l[5][1, 2] = l[5][2, 1] = 1
+    l[6][1, 2], l[6][2, 1] = -1j, 1j
+    l[7] = np.diag([1, 1, -2]) / np.sqrt(3)
+    return l / 2
+
+
+def _mats(F):
+    """link-layout array [mu, t, z, y, x, b, a] -> matrices [..., a, b]."""
+    return np.swapaxes(F, -1, -2)
+
+
+def _links(M):
+    return np.ascontiguousarray(np.swapaxes(M, -1, -2))
+
+
+def momenta(normals):
+    """P = i sum_a p^a T^a per link from normals of shape [mu, t, z, y, x, 8]
+    (the momentum refresh of the MD step); link layout like U."""
+    return _links(1j * np.einsum("...a,aij->...ij", normals, gell_mann()))
+
+
+def kinetic(P):
+    """K = sum over links of -Tr(P^2) = (1/2) sum (p^a)^2."""
+    M = _mats(P)
+    return float(-np.einsum("...ij,...ji->...", M, M).sum().real)
+
+
+def traceless_antihermitian(G):
+    """TA(G) = (G - G^dag)/2 - Tr(G - G^dag)/6, per link (link layout in and out)."""
+    M = _mats(G)
+    A = (M - np.conj(np.swapaxes(M, -1, -2))) / 2
+    tr = np.einsum("...ii->...", A) / 3
+    return _links(A - tr[..., None, None] * np.eye(3))
+
+
+def exp_update(U, P, eps):
+    """U <- exp(eps P) U per link (exp through the Hermitian eigendecomposition of -i P)."""
+    H = -1j * _mats(P)
+    lam, v = np.linalg.eigh(H)
+    E = np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * eps * lam), v.conj())
+    return _links(E @ _mats(U))
+
+
+def hmc_forces(dims, U, eta, beta, kappa, tol, t_antiperiodic=True):
+    """U dS/dU of S_g + S_f (S_f = eta^dag (D^dag D)^-1 eta; no fermions when eta is None)."""
+    G = gauge_force(dims, U, beta)
+    if eta is not None:
+        _, Gf = fermi_force(dims, U, eta, kappa, tol=tol, t_antiperiodic=t_antiperiodic)
+        G = G + Gf
+    return G
+
+
+def hmc_trajectory(dims, U, normals, xi, beta, kappa, n_md, tau=1.0, tol=1e-12, P0=None,
+                   t_antiperiodic=True):
+    """One HMC trajectory as the paper's MDstep!: momenta from normals (or P0),
+    pseudofermion eta = D^dag xi (no fermions when xi is None), S_f,old = |xi|^2,
+    n_md leapfrog steps U(dt/2) P(dt) U(dt/2) of dt = tau / n_md with
+    dP/dt = (1/2) TA(U dS/dU), and H = K + S_g + S_f before and after.
+    Returns (U_new, P_new, H_old, H_new)."""
+    P = momenta(normals) if P0 is None else P0.copy()
+    eta = None if xi is None else dirac(dims, U, xi, kappa, dagger=True, t_antiperiodic=t_antiperiodic)
+    S_f = 0.0 if xi is None else float(np.vdot(xi, xi).real)
+    H_old = kinetic(P) + gauge_action(dims, U, beta) + S_f
+    dt = tau / n_md
+    for _ in range(n_md):
+        U = exp_update(U, P, dt / 2)
+        G = hmc_forces(dims, U, eta, beta, kappa, tol, t_antiperiodic)
+        P = P + dt * 0.5 * traceless_antihermitian(G)
+        U = exp_update(U, P, dt / 2)
+    S_f = 0.0 if eta is None else fermi_action(dims, U, eta, kappa, tol=tol, t_antiperiodic=t_antiperiodic)[0]
+    H_new = kinetic(P) + gauge_action(dims, U, beta) + S_f
+    return U, P, H_old, H_new
 
 
 def set_threads(n: int = 0) -> int:

@@ -691,3 +691,86 @@ int jo_stag_solve(const int dims[4], int tanti, double mass, const double *U, co
   free(rhs); free(r); free(p); free(Ap); free(t);
   return rc;
 }
+
+/* ---- pure-gauge part of the HMC (paper: section "Hybrid Monte Carlo") -----
+ * Wilson plaquette action, as the paper's example builds it (plaquette loops
+ * and their adjoints, Sg = -evaluate_GaugeAction / NC):
+ *   S_g = -(beta / 3) sum_x sum_{mu<nu} Re Tr P_munu(x),
+ *   P_munu(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag.
+ * Its link derivative in the convention of jo_fermi_force (dS = Re Tr[(dS/dU) dU]):
+ *   U dS_g/dU_mu(x) = -(beta / 3) U_mu(x) V_mu(x),  V = sum over the six staples
+ *   V_mu(x) = sum_{nu != mu} [ U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+ *                            + U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu) ]. */
+typedef struct { cplx m[3][3]; } mat3;
+
+static mat3 mat_link(const lat_t *L, const double *U, int mu, int64_t s) {
+  mat3 r;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) r.m[a][b] = link(L, U, mu, s, a, b);
+  return r;
+}
+static mat3 mat_mul(mat3 A, mat3 B) {
+  mat3 r;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      cplx acc = cm(0, 0);
+      for (int k = 0; k < 3; ++k) acc = cadd(acc, cmul(A.m[a][k], B.m[k][b]));
+      r.m[a][b] = acc;
+    }
+  return r;
+}
+static mat3 mat_dag(mat3 A) {
+  mat3 r;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) r.m[a][b] = cconj(A.m[b][a]);
+  return r;
+}
+static int64_t shift_site(const lat_t *L, int64_t s, int mu, int step) {
+  int64_t c[4];
+  site_coords(L, s, c);
+  c[mu] = (c[mu] + step + L->n[mu]) % L->n[mu];
+  return site_index(L, c);
+}
+
+/* Sum over x and mu < nu of Re Tr P_munu(x). */
+double jo_plaquette_sum(const int dims[4], const double *U) {
+  lat_t L;
+  if (lat_init(&L, dims, 0) || !U) return NAN;
+  double sum = 0.0;
+  for (int64_t x = 0; x < L.V; ++x)
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const mat3 P = mat_mul(mat_mul(mat_link(&L, U, mu, x), mat_link(&L, U, nu, shift_site(&L, x, mu, 1))),
+                               mat_mul(mat_dag(mat_link(&L, U, mu, shift_site(&L, x, nu, 1))),
+                                       mat_dag(mat_link(&L, U, nu, x))));
+        sum += P.m[0][0].re + P.m[1][1].re + P.m[2][2].re;
+      }
+  return sum;
+}
+
+/* out = U dS_g/dU for every link (canonical link layout). */
+int jo_gauge_force(const int dims[4], double beta, const double *U, double *out) {
+  lat_t L;
+  if (lat_init(&L, dims, 0) || !U || !out) return -1;
+  for (int64_t x = 0; x < L.V; ++x)
+    for (int mu = 0; mu < 4; ++mu) {
+      mat3 V;
+      memset(&V, 0, sizeof V);
+      const int64_t xpm = shift_site(&L, x, mu, 1);
+      for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        const int64_t xpn = shift_site(&L, x, nu, 1), xmn = shift_site(&L, x, nu, -1);
+        const int64_t xpmmn = shift_site(&L, xpm, nu, -1);
+        const mat3 up = mat_mul(mat_mul(mat_link(&L, U, nu, xpm), mat_dag(mat_link(&L, U, mu, xpn))),
+                                mat_dag(mat_link(&L, U, nu, x)));
+        const mat3 dn = mat_mul(mat_mul(mat_dag(mat_link(&L, U, nu, xpmmn)), mat_dag(mat_link(&L, U, mu, xmn))),
+                                mat_link(&L, U, nu, xmn));
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) V.m[a][b] = cadd(V.m[a][b], cadd(up.m[a][b], dn.m[a][b]));
+      }
+      const mat3 G = mat_mul(mat_link(&L, U, mu, x), V);
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) st(out, a + 3 * (b + 3 * (x + L.V * mu)), cscale(G.m[a][b], -beta / 3.0));
+    }
+  return 0;
+}

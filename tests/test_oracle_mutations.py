@@ -8,6 +8,7 @@ import pytest
 
 import oracle
 import test_oracle_force as force_pins
+import test_oracle_hmc as hmc_pins
 import test_oracle_pins as pins
 import test_oracle_shift as shift_pins
 import test_oracle_staggered as stag_pins
@@ -49,6 +50,10 @@ MUTATIONS = {
     "stag_half_dropped": ("const double f = 0.5 * eta", "const double f = eta"),
     "stag_backward_link_not_daggered": ("(dir == 0) ? link(L, U, mu, x, a, b) : cconj(link(L, U, mu, y, b, a));\n            acc = cadd(acc, cmul(w, ld(in, b + 3 * y)));",
                                         "(dir == 0) ? link(L, U, mu, x, a, b) : link(L, U, mu, y, a, b);\n            acc = cadd(acc, cmul(w, ld(in, b + 3 * y)));"),
+    "gauge_force_no_lower_staple": ("cadd(up.m[a][b], dn.m[a][b])", "up.m[a][b]"),
+    "gauge_force_sign": ("cscale(G.m[a][b], -beta / 3.0)", "cscale(G.m[a][b], beta / 3.0)"),
+    "plaquette_trace_imaginary": ("sum += P.m[0][0].re + P.m[1][1].re + P.m[2][2].re;",
+                                  "sum += P.m[0][0].im + P.m[1][1].re + P.m[2][2].re;"),
     "force_projectors_swapped": ("cm(d - GRE[mu][alpha][beta], -GIM[mu][alpha][beta]);  /* 1 - gamma */",
                                  "cm(d + GRE[mu][alpha][beta], GIM[mu][alpha][beta]);  /* 1 - gamma */"),
     "force_no_boundary_sign": ("if (mu == 3 && L->tanti) s = -1.0;", ""),
@@ -69,6 +74,8 @@ PINS = [
     ("shifted_cg", lambda: shift_pins.test_shifted_cg_against_dense(True)),
     ("staggered_dense", lambda: stag_pins.test_staggered_dense_brute_force((2, 2, 2, 4), True)),
     ("staggered_free", lambda: stag_pins.test_staggered_free_field(True)),
+    ("cold_start", lambda: hmc_pins.test_cold_start_action()),
+    ("gauge_force_derivative", lambda: hmc_pins.test_gauge_force_is_the_derivative()),
     ("force_derivative", lambda: force_pins.test_force_is_the_derivative_of_the_action(True)),
     ("force_covariance", lambda: force_pins.test_force_gauge_covariance()),
 ]
