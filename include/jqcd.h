@@ -401,6 +401,47 @@ JQCD_API jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, 
                                               double mass, const void *b_even, const void *b_odd, void *x_even,
                                               void *x_odd, jqcd_solve_info *info, void *stream);
 
+/* ---- hybrid Monte Carlo (paper: section "Hybrid Monte Carlo", MDstep!) ----
+ * One trajectory on the resident gauge field: momenta refresh from the given
+ * normals, pseudofermion eta = D^dag xi, n_md leapfrog steps
+ * U(dt/2) P(dt) U(dt/2) with dt = tau / n_md, and the Metropolis test with the
+ * given uniform u: accepted iff u <= exp(-dH).  A rejected trajectory leaves
+ * the gauge field as it was.
+ *   H = K + S_g + S_f,  K = -sum_links Tr P^2 = sum (p^a)^2 / 2, P = i sum_a p^a T^a
+ *   (T^a = Gell-Mann / 2), S_g = -(beta/3) sum_{x, mu<nu} Re Tr P_munu(x)
+ *   (the paper's plaquette action, Sg = -evaluate_GaugeAction / NC),
+ *   S_f = eta^dag (D^dag D)^{-1} eta (jqcd_fermi_action; S_f before = |xi|^2),
+ *   dU/dt = P U, dP/dt = TA(U dS/dU) / 2 (U dS/dU: gauge part plus jqcd_fermi_force).
+ * Gauge-field kernels run in FP64; the FP64 links are the master copy and the
+ * double-word and FP32 copies are refreshed after every update.  Random
+ * numbers are inputs: normals[8*l + a] (l = site + V*mu, a < 8) are the
+ * momentum coefficients p^a, xi (host canonical spinor, ignored without
+ * fermions) the Gaussian pseudofermion source. */
+typedef struct {
+  double beta;       /* plaquette coupling (paper's example: 5.5) */
+  double kappa;      /* Wilson hopping parameter */
+  double tau;        /* trajectory length (paper: 1) */
+  double tol;        /* CG tolerance of the fermion solves */
+  int32_t n_md;      /* leapfrog steps (paper: MDsteps = 10) */
+  int32_t fermions;  /* 1: two-flavour Wilson fermions; 0: pure gauge */
+  int32_t mode;      /* CG mode of the fermion solves (JQCD_CG_DW, _MIXED_F32, _MIXED_F16) */
+  int32_t maxiter;   /* per fermion solve */
+} jqcd_hmc_params;
+typedef struct {
+  double H_old, H_new, dH;
+  double plaquette;  /* sum Re Tr P / (18 V) of the field after the trajectory */
+  double seconds;
+  int32_t accepted;
+  int32_t cg_iters;  /* iterations of every fermion solve */
+} jqcd_hmc_info;
+JQCD_API jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc_params *params,
+                                         const double *normals, const double *xi, double u, jqcd_hmc_info *info);
+/* Average plaquette sum Re Tr P / (18 V) of the resident field (paper's
+ * calculate_Plaquette normalisation: 1 for the cold start). */
+JQCD_API jqcd_status jqcd_gauge_plaquette(jqcd_ctx *ctx, uint64_t gauge_id, double *plaquette);
+/* Copy the resident FP64 links to the host (canonical link layout, 36*V complex doubles). */
+JQCD_API jqcd_status jqcd_gauge_download(jqcd_ctx *ctx, uint64_t gauge_id, double *links);
+
 #ifdef __cplusplus
 }
 #endif

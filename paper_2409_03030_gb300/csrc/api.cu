@@ -23,6 +23,7 @@
 #include "serve.h"
 #include "solver.h"
 #include "staggered.h"
+#include "hmc.h"
 
 using namespace jqcd;
 
@@ -902,6 +903,134 @@ jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqc
   if (info) *info = inf;
   if (st != JQCD_OK) return fail(ctx, st, "staggered_solve_dev: %s", msg.c_str());
   return JQCD_OK;
+}
+
+}  // extern "C"
+
+// ---- hybrid Monte Carlo ------------------------------------------------------------
+extern "C" {
+
+jqcd_status jqcd_gauge_plaquette(jqcd_ctx *ctx, uint64_t gauge_id, double *plaquette) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!plaquette) return fail(ctx, JQCD_EINVAL, "gauge_plaquette: plaquette is NULL");
+  CK(G->ensure_hmc(), "hmc workspace alloc");
+  double sum = 0.0;
+  CK(hmc_plaquette_sum(*G, &sum, ctx->stream), "plaquette");
+  *plaquette = sum / (18.0 * (double)(2 * G->g.vh));
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_gauge_download(jqcd_ctx *ctx, uint64_t gauge_id, double *links) {
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!links) return fail(ctx, JQCD_EINVAL, "gauge_download: links is NULL");
+  cudaStream_t s = ctx->stream;
+  CK(G->ensure_force(), "staging alloc");  // lcanon: 36 V complex doubles
+  CK(launch_links_unpack(*G, G->lcanon, s), "links unpack");
+  CK(cudaMemcpyAsync(links, G->lcanon, G->link_canon_bytes(), cudaMemcpyDeviceToHost, s), "links D2H");
+  CK(cudaStreamSynchronize(s), "download sync");
+  return JQCD_OK;
+}
+
+jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc_params *hp, const double *normals,
+                                const double *xi, double u, jqcd_hmc_info *info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  jqcd_status st = check_ctx(ctx);
+  if (st) return st;
+  GaugeEntry *G = find_gauge(ctx, gauge_id);
+  if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
+  if (!hp || !normals || (hp->fermions && !xi)) return fail(ctx, JQCD_EINVAL, "hmc_trajectory: bad argument");
+  if (hp->n_md < 1 || !(hp->tau > 0.0) || !std::isfinite(hp->beta) || !(hp->beta >= 0.0))
+    return fail(ctx, JQCD_EINVAL, "hmc_trajectory: n_md >= 1, tau > 0, beta >= 0");
+  cudaStream_t s = ctx->stream;
+  const int64_t V = 2 * G->g.vh, nh = 12 * G->g.vh;
+  CK(G->ensure_hmc(), "hmc workspace alloc");
+  if (hp->fermions) CK(G->ensure_force(), "force workspace alloc");
+  const size_t lf = (size_t)72 * 16 * G->g.vh;
+  jqcd_solve_params sp;
+  memset(&sp, 0, sizeof sp);
+  sp.kappa = hp->kappa;
+  sp.tol = hp->tol;
+  sp.maxiter = hp->maxiter > 0 ? hp->maxiter : 20000;
+  sp.eo = 1;
+  sp.mode = hp->mode;
+  jqcd_hmc_info out;
+  memset(&out, 0, sizeof out);
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  // save the links, refresh the momenta
+  CK(cudaMemcpyAsync(G->hUbak, G->gauge_f64, lf, cudaMemcpyDeviceToDevice, s), "links backup");
+  CK(cudaMemcpyAsync(G->hNormals, normals, sizeof(double) * 32 * (size_t)V, cudaMemcpyHostToDevice, s),
+     "normals H2D");
+  CK(hmc_momenta_set(*G, G->hNormals, s), "momenta");
+  double S_f = 0.0;
+  if (hp->fermions) {
+    // eta = D^dag xi into feta (xi staged in fY); S_f,old = |xi|^2
+    CK(cudaMemcpyAsync(G->canon, xi, G->canon_bytes(), cudaMemcpyHostToDevice, s), "xi H2D");
+    CK(launch_spinor_pack(G->g, PREC_DW, G->canon, G->fY, G->fY + nh, s), "xi pack");
+    HopParams Pe = G->hop_params(PREC_DW, 0, G->fY + nh, G->fY, G->feta, 1.0, -hp->kappa, nullptr);
+    HopParams Po = G->hop_params(PREC_DW, 1, G->fY, G->fY + nh, G->feta + nh, 1.0, -hp->kappa, nullptr);
+    CK(launch_hop(PREC_DW, Pe, true, true, false, s), "heatbath hop");
+    CK(launch_hop(PREC_DW, Po, true, true, false, s), "heatbath hop");
+    const int nb = (int)blas_blocks(2 * nh);
+    double *dev = G->partials + (G->n_partials() - 1);
+    CK(launch_dw_norm2(G->fY, 2 * nh, G->partials, s), "norm");
+    CK(launch_finalize_sum(G->partials, nb, dev, s), "norm");
+    CK(cudaMemcpyAsync(&S_f, dev, sizeof(double), cudaMemcpyDeviceToHost, s), "norm D2H");
+    CK(cudaStreamSynchronize(s), "sync");
+  }
+  double K = 0.0, plaq = 0.0;
+  CK(hmc_kinetic(*G, &K, s), "kinetic");
+  CK(hmc_plaquette_sum(*G, &plaq, s), "plaquette");
+  out.H_old = K - hp->beta / 3.0 * plaq + S_f;
+  // leapfrog
+  const double dt = hp->tau / hp->n_md;
+  for (int step = 0; step < hp->n_md; ++step) {
+    CK(hmc_links_update(*G, 0.5 * dt, s), "link update");
+    CK(hmc_gauge_force(*G, hp->beta, s), "gauge force");
+    if (hp->fermions) {
+      jqcd_solve_info fi;
+      memset(&fi, 0, sizeof fi);
+      st = fermi_solves(ctx, G, sp, &fi, nullptr);
+      add_info(&inf, fi);
+      if (st != JQCD_OK) break;
+      CK(launch_fermi_force(G->g, G->fX, G->fX + nh, G->fY, G->fY + nh, (const float4 *)G->gauge_dw, hp->kappa,
+                            G->fout, s), "fermion force");
+    }
+    CK(hmc_momenta_update(*G, hp->fermions ? G->fout : nullptr, 0.5 * dt, s), "momenta update");
+    CK(hmc_links_update(*G, 0.5 * dt, s), "link update");
+  }
+  if (st == JQCD_OK) {
+    S_f = 0.0;
+    if (hp->fermions) {
+      jqcd_solve_info fi;
+      memset(&fi, 0, sizeof fi);
+      st = fermi_solves(ctx, G, sp, &fi, &S_f);
+      add_info(&inf, fi);
+    }
+  }
+  if (st == JQCD_OK) {
+    CK(hmc_kinetic(*G, &K, s), "kinetic");
+    CK(hmc_plaquette_sum(*G, &plaq, s), "plaquette");
+    out.H_new = K - hp->beta / 3.0 * plaq + S_f;
+    out.dH = out.H_new - out.H_old;
+    out.accepted = std::isfinite(out.dH) && u <= std::exp(-out.dH);
+  }
+  if (!out.accepted) {  // restore the links (also after a failed solve)
+    CK(cudaMemcpyAsync(G->gauge_f64, G->hUbak, lf, cudaMemcpyDeviceToDevice, s), "links restore");
+    CK(launch_hmc_links_refresh(*G, s), "links refresh");
+  }
+  CK(hmc_plaquette_sum(*G, &plaq, s), "plaquette");
+  out.plaquette = plaq / (18.0 * (double)V);
+  out.cg_iters = inf.iters;
+  out.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = out;
+  return st;  // fermi_solves has set the error text on failure
 }
 
 }  // extern "C"

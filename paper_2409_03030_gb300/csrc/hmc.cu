@@ -1,0 +1,413 @@
+// Hybrid Monte Carlo on the resident gauge field (paper: section "Hybrid
+// Monte Carlo", MDstep!): Wilson plaquette gauge action with beta, su(3)
+// momenta, leapfrog steps U(dt/2) P(dt) U(dt/2), two-flavour Wilson fermions
+// through the action/force of force.cu, Metropolis on H = K + S_g + S_f.
+//
+// Conventions (U dS/dU as in force.cu: dS = Re Tr[(dS/dU) dU]):
+//   S_g = -(beta/3) sum_x sum_{mu<nu} Re Tr P_munu(x),
+//   U dS_g/dU_mu(x) = -(beta/3) U_mu(x) V_mu(x) (V: the six staples),
+//   P = i sum_a p^a T^a, T^a = lambda^a / 2, K = -sum Tr P^2 = sum (p^a)^2 / 2,
+//   dP/dt = TA(U dS/dU) / 2, dU/dt = P U, TA(G) = (G - G^dag)/2 - Tr(G - G^dag)/6.
+// The gauge kernels run in native FP64 (they are a small part of a trajectory
+// next to the fermion solves); the FP64 links are the master copy and the
+// double-word and 12-real FP32 copies are refreshed from them after every
+// update.  Layouts: FP64 link-type fields double2[2][4][9][vh] (parity, mu,
+// element 3a+b, checkerboard site), like the uploaded FP64 gauge field.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "dw.cuh"
+#include "hmc.h"
+#include "kernels.h"
+#include "reduce.cuh"
+#include "solver.h"
+
+namespace jqcd {
+
+namespace {
+
+constexpr int kHmcThreads = 128;
+
+struct m3 {
+  double2 e[3][3];
+};
+
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cadd_d(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+__device__ __forceinline__ m3 m3_mul(const m3 &A, const m3 &B) {
+  m3 r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double2 acc = cmul_d(A.e[a][0], B.e[0][b]);
+      acc = cadd_d(acc, cmul_d(A.e[a][1], B.e[1][b]));
+      r.e[a][b] = cadd_d(acc, cmul_d(A.e[a][2], B.e[2][b]));
+    }
+  return r;
+}
+__device__ __forceinline__ m3 m3_dag(const m3 &A) {
+  m3 r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) r.e[a][b] = make_double2(A.e[b][a].x, -A.e[b][a].y);
+  return r;
+}
+__device__ __forceinline__ m3 m3_load(const double2 *F, int64_t vh, int p, int mu, int64_t cb) {
+  m3 r;
+  const double2 *q = F + (size_t)((p * 4 + mu) * 9) * vh + cb;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) r.e[k / 3][k % 3] = q[k * vh];
+  return r;
+}
+__device__ __forceinline__ void m3_store(double2 *F, int64_t vh, int p, int mu, int64_t cb, const m3 &A) {
+  double2 *q = F + (size_t)((p * 4 + mu) * 9) * vh + cb;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) q[k * vh] = A.e[k / 3][k % 3];
+}
+
+// link U_nu at the site c shifted by (s1 in mu1) and (s2 in mu2)
+__device__ __forceinline__ m3 link_at(const double2 *U, const Geom &g, const int c[4], int nu, int mu1, int s1,
+                                      int mu2, int s2) {
+  int d[4] = {c[0], c[1], c[2], c[3]};
+  const int n1 = mu1 == 0 ? g.nx : (mu1 == 1 ? g.ny : (mu1 == 2 ? g.nz : g.nt));
+  const int n2 = mu2 == 0 ? g.nx : (mu2 == 1 ? g.ny : (mu2 == 2 ? g.nz : g.nt));
+  if (s1) d[mu1] = (d[mu1] + s1 + n1) % n1;
+  if (s2) d[mu2] = (d[mu2] + s2 + n2) % n2;
+  return m3_load(U, g.vh, (d[0] + d[1] + d[2] + d[3]) & 1, nu, cb_index(g, d[0], d[1], d[2], d[3]));
+}
+
+__device__ __forceinline__ void site_of_thread(const Geom &g, int64_t q, int *p, int64_t *cb, int c[4]) {
+  *p = (int)(q / g.vh);
+  *cb = q - (int64_t)*p * g.vh;
+  cb_coords(g, *cb, *p, c[0], c[1], c[2], c[3]);
+}
+
+// U dS_g/dU for every link: one thread per (site, mu)
+__global__ void __launch_bounds__(kHmcThreads) gauge_force_kernel(Geom g, const double2 *__restrict__ U, double beta,
+                                                                  double2 *__restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 8 * g.vh) return;
+  const int mu = (int)(q / (2 * g.vh));
+  int p, c[4];
+  int64_t cb;
+  site_of_thread(g, q % (2 * g.vh), &p, &cb, c);
+  m3 V;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) V.e[a][b] = make_double2(0.0, 0.0);
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == mu) continue;
+    // upper staple U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+    const m3 up = m3_mul(m3_mul(link_at(U, g, c, nu, mu, 1, nu, 0), m3_dag(link_at(U, g, c, mu, nu, 1, mu, 0))),
+                         m3_dag(link_at(U, g, c, nu, mu, 0, nu, 0)));
+    // lower staple U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+    const m3 dn = m3_mul(m3_mul(m3_dag(link_at(U, g, c, nu, mu, 1, nu, -1)), m3_dag(link_at(U, g, c, mu, nu, -1, mu, 0))),
+                         link_at(U, g, c, nu, nu, -1, mu, 0));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) V.e[a][b] = cadd_d(V.e[a][b], cadd_d(up.e[a][b], dn.e[a][b]));
+  }
+  m3 G = m3_mul(m3_load(U, g.vh, p, mu, cb), V);
+  const double f = -beta / 3.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) G.e[a][b] = make_double2(f * G.e[a][b].x, f * G.e[a][b].y);
+  m3_store(out, g.vh, p, mu, cb, G);
+}
+
+// per-block partials of sum_{mu<nu} Re Tr P_munu(x): one thread per site
+__global__ void __launch_bounds__(kHmcThreads) plaquette_kernel(Geom g, const double2 *__restrict__ U,
+                                                                double *partials) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (q < 2 * g.vh) {
+    int p, c[4];
+    int64_t cb;
+    site_of_thread(g, q, &p, &cb, c);
+    for (int mu = 0; mu < 4; ++mu)
+      for (int nu = mu + 1; nu < 4; ++nu) {
+        const m3 A = m3_mul(m3_load(U, g.vh, p, mu, cb), link_at(U, g, c, nu, mu, 1, nu, 0));
+        const m3 B = m3_mul(m3_dag(link_at(U, g, c, mu, nu, 1, mu, 0)), m3_dag(m3_load(U, g.vh, p, nu, cb)));
+        // Re Tr (A B)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) s += A.e[a][k].x * B.e[k][a].x - A.e[a][k].y * B.e[k][a].y;
+      }
+  }
+  const double t = block_sum_d(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// P = i sum_a p^a T^a from normals [link l = site + V*mu][8] (canonical order)
+__global__ void mom_set_kernel(Geom g, const double *__restrict__ normals, double2 *__restrict__ P) {
+  const int64_t V = 2 * g.vh;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= 4 * V) return;
+  const int mu = (int)(l / V);
+  const int64_t s = l % V;
+  const int x = (int)(s % g.nx);
+  int64_t r = s / g.nx;
+  const int y = (int)(r % g.ny);
+  r /= g.ny;
+  const int z = (int)(r % g.nz);
+  const int t = (int)(r / g.nz);
+  const int p = (x + y + z + t) & 1;
+  const int64_t cb = s >> 1;
+  const double *a = normals + 8 * l;
+  const double r3 = 0.5773502691896258;  // 1/sqrt(3)
+  // i * (1/2) * sum_a p^a lambda^a  (Gell-Mann matrices)
+  m3 M;
+  M.e[0][0] = make_double2(0.0, 0.5 * (a[2] + r3 * a[7]));
+  M.e[1][1] = make_double2(0.0, 0.5 * (-a[2] + r3 * a[7]));
+  M.e[2][2] = make_double2(0.0, 0.5 * (-2.0 * r3 * a[7]));
+  M.e[0][1] = make_double2(0.5 * a[1], 0.5 * a[0]);
+  M.e[1][0] = make_double2(-0.5 * a[1], 0.5 * a[0]);
+  M.e[0][2] = make_double2(0.5 * a[4], 0.5 * a[3]);
+  M.e[2][0] = make_double2(-0.5 * a[4], 0.5 * a[3]);
+  M.e[1][2] = make_double2(0.5 * a[6], 0.5 * a[5]);
+  M.e[2][1] = make_double2(-0.5 * a[6], 0.5 * a[5]);
+  m3_store(P, g.vh, p, mu, cb, M);
+}
+
+// per-block partials of sum over links of -Tr P^2
+__global__ void kinetic_kernel(Geom g, const double2 *__restrict__ P, double *partials) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s = 0.0;
+  if (q < 8 * g.vh) {
+    const int mu = (int)(q / (2 * g.vh));
+    const int64_t r = q % (2 * g.vh);
+    const int p = (int)(r / g.vh);
+    const m3 A = m3_load(P, g.vh, p, mu, r - (int64_t)p * g.vh);
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) s -= A.e[a][k].x * A.e[k][a].x - A.e[a][k].y * A.e[k][a].y;
+  }
+  const double t = block_sum_d(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+// P += coef * TA(Gg + Gf); Gf: double-word link field or null
+__global__ void mom_update_kernel(Geom g, double2 *__restrict__ P, const double2 *__restrict__ Gg,
+                                  const float4 *__restrict__ Gf, double coef) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 8 * g.vh) return;
+  const int mu = (int)(q / (2 * g.vh));
+  const int64_t r = q % (2 * g.vh);
+  const int p = (int)(r / g.vh);
+  const int64_t cb = r - (int64_t)p * g.vh;
+  m3 G = m3_load(Gg, g.vh, p, mu, cb);
+  if (Gf) {
+    const float4 *F = Gf + (size_t)((p * 4 + mu) * 9) * g.vh + cb;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const float4 v = F[k * g.vh];
+      G.e[k / 3][k % 3].x += (double)v.x + (double)v.z;
+      G.e[k / 3][k % 3].y += (double)v.y + (double)v.w;
+    }
+  }
+  // TA(G) = (G - G^dag)/2 - i Im Tr(G)/3 on the diagonal
+  const double tr = (G.e[0][0].y + G.e[1][1].y + G.e[2][2].y) / 3.0;
+  m3 A = m3_load(P, g.vh, p, mu, cb);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      double re = 0.5 * (G.e[a][b].x - G.e[b][a].x);
+      double im = 0.5 * (G.e[a][b].y + G.e[b][a].y);
+      if (a == b) im -= tr;
+      A.e[a][b] = make_double2(A.e[a][b].x + coef * re, A.e[a][b].y + coef * im);
+    }
+  m3_store(P, g.vh, p, mu, cb, A);
+}
+
+// U <- exp(eps P) U: Taylor series of exp(eps P / 2^k) to double precision, squared k times
+__global__ void exp_update_kernel(Geom g, double2 *__restrict__ U, const double2 *__restrict__ P, double eps) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 8 * g.vh) return;
+  const int mu = (int)(q / (2 * g.vh));
+  const int64_t r = q % (2 * g.vh);
+  const int p = (int)(r / g.vh);
+  const int64_t cb = r - (int64_t)p * g.vh;
+  m3 A = m3_load(P, g.vh, p, mu, cb);
+  double nrm = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) nrm += A.e[a][b].x * A.e[a][b].x + A.e[a][b].y * A.e[a][b].y;
+  nrm = fabs(eps) * sqrt(nrm);  // Frobenius norm of eps P
+  int k = 0;
+  double sc = eps;
+  while (nrm > 0.25 && k < 40) {
+    nrm *= 0.5;
+    sc *= 0.5;
+    ++k;
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) A.e[a][b] = make_double2(sc * A.e[a][b].x, sc * A.e[a][b].y);
+  // E = sum_{n <= 16} A^n / n!   (|A| <= 1/4: remainder below 1e-20)
+  m3 E, T;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) E.e[a][b] = T.e[a][b] = make_double2(a == b ? 1.0 : 0.0, 0.0);
+  for (int n = 1; n <= 16; ++n) {
+    T = m3_mul(T, A);
+    const double inv = 1.0 / n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        T.e[a][b] = make_double2(T.e[a][b].x * inv, T.e[a][b].y * inv);
+        E.e[a][b] = cadd_d(E.e[a][b], T.e[a][b]);
+      }
+  }
+  for (int i = 0; i < k; ++i) E = m3_mul(E, E);
+  m3_store(U, g.vh, p, mu, cb, m3_mul(E, m3_load(U, g.vh, p, mu, cb)));
+}
+
+// FP64 links -> double-word and 12-real FP32 copies (same per-link layout as gauge_pack)
+__global__ void links_refresh_kernel(Geom g, const double2 *__restrict__ U, float4 *__restrict__ dwo,
+                                     float4 *__restrict__ f32o) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 8 * g.vh) return;
+  const int mu = (int)(q / (2 * g.vh));
+  const int64_t r = q % (2 * g.vh);
+  const int p = (int)(r / g.vh);
+  const int64_t cb = r - (int64_t)p * g.vh;
+  const m3 A = m3_load(U, g.vh, p, mu, cb);
+  const int64_t blk = (int64_t)(p * 4 + mu);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const double2 v = A.e[k / 3][k % 3];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    dwo[(blk * 9 + k) * g.vh + cb] =
+        make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+  }
+  const double2 e[6] = {A.e[0][0], A.e[0][1], A.e[0][2], A.e[1][0], A.e[1][1], A.e[1][2]};
+#pragma unroll
+  for (int j = 0; j < 3; ++j)
+    f32o[(blk * 3 + j) * g.vh + cb] = make_float4((float)e[2 * j].x, (float)e[2 * j].y, (float)e[2 * j + 1].x,
+                                                  (float)e[2 * j + 1].y);
+}
+
+// FP64 link field -> canonical host layout a + 3(b + 3(site + V mu))
+__global__ void links_unpack_kernel(Geom g, const double2 *__restrict__ U, double2 *__restrict__ canon) {
+  const int64_t V = 2 * g.vh;
+  const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= 4 * V) return;
+  const int mu = (int)(l / V);
+  const int64_t s = l % V;
+  const int x = (int)(s % g.nx);
+  int64_t r = s / g.nx;
+  const int y = (int)(r % g.ny);
+  r /= g.ny;
+  const int z = (int)(r % g.nz);
+  const int t = (int)(r / g.nz);
+  const m3 A = m3_load(U, g.vh, (x + y + z + t) & 1, mu, s >> 1);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) canon[9 * l + a + 3 * b] = A.e[a][b];
+}
+
+unsigned link_blocks(int64_t vh) { return (unsigned)((8 * vh + kHmcThreads - 1) / kHmcThreads); }
+unsigned site_blocks2(int64_t vh) { return (unsigned)((2 * vh + kHmcThreads - 1) / kHmcThreads); }
+
+}  // namespace
+
+cudaError_t GaugeEntry::ensure_hmc() {
+  cudaError_t e = ensure_reduce();
+  const size_t lf = (size_t)72 * 16 * g.vh;  // FP64 link field, double2[2][4][9][vh]
+  double2 **vs[] = {&hP, &hG, &hUbak};
+  for (double2 **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc_t(v, lf);
+  if (e == cudaSuccess && !hNormals) e = alloc_t(&hNormals, sizeof(double) * 8 * 4 * (size_t)(2 * g.vh));
+  if (e == cudaSuccess && !hPart) e = alloc_t(&hPart, sizeof(double) * (link_blocks(g.vh) + 2));
+  return e;
+}
+
+cudaError_t launch_hmc_links_refresh(GaugeEntry &G, cudaStream_t s) {
+  note_launch();
+  links_refresh_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (const double2 *)G.gauge_f64,
+                                                                      (float4 *)G.gauge_dw, (float4 *)G.gauge_f32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_links_unpack(const GaugeEntry &G, double *canon, cudaStream_t s) {
+  note_launch();
+  links_unpack_kernel<<<(unsigned)((8 * G.g.vh + 255) / 256), 256, 0, s>>>(G.g, (const double2 *)G.gauge_f64,
+                                                                             (double2 *)canon);
+  return cudaGetLastError();
+}
+
+namespace {
+
+// sum of the per-block partials in G.hPart into its last slot, then to the host
+cudaError_t reduce_to_host(GaugeEntry &G, int nblocks, double *host, cudaStream_t s) {
+  double *dev = G.hPart + link_blocks(G.g.vh) + 1;
+  cudaError_t e = launch_finalize_sum(G.hPart, nblocks, dev, s);
+  if (!e) e = cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (!e) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t hmc_plaquette_sum(GaugeEntry &G, double *out, cudaStream_t s) {
+  const unsigned nb = site_blocks2(G.g.vh);
+  note_launch();
+  plaquette_kernel<<<nb, kHmcThreads, 0, s>>>(G.g, (const double2 *)G.gauge_f64, G.hPart);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = reduce_to_host(G, (int)nb, out, s);
+  return e;
+}
+
+cudaError_t hmc_kinetic(GaugeEntry &G, double *out, cudaStream_t s) {
+  const unsigned nb = link_blocks(G.g.vh);
+  note_launch();
+  kinetic_kernel<<<nb, kHmcThreads, 0, s>>>(G.g, G.hP, G.hPart);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = reduce_to_host(G, (int)nb, out, s);
+  return e;
+}
+
+cudaError_t hmc_momenta_set(GaugeEntry &G, const double *normals_dev, cudaStream_t s) {
+  note_launch();
+  mom_set_kernel<<<(unsigned)((8 * G.g.vh + 255) / 256), 256, 0, s>>>(G.g, normals_dev, G.hP);
+  return cudaGetLastError();
+}
+
+cudaError_t hmc_gauge_force(GaugeEntry &G, double beta, cudaStream_t s) {
+  note_launch();
+  gauge_force_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (const double2 *)G.gauge_f64, beta, G.hG);
+  return cudaGetLastError();
+}
+
+cudaError_t hmc_momenta_update(GaugeEntry &G, const float4 *Gf, double coef, cudaStream_t s) {
+  note_launch();
+  mom_update_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, G.hP, G.hG, Gf, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t hmc_links_update(GaugeEntry &G, double eps, cudaStream_t s) {
+  note_launch();
+  exp_update_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (double2 *)G.gauge_f64, G.hP, eps);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = launch_hmc_links_refresh(G, s);
+  return e;
+}
+
+}  // namespace jqcd

@@ -43,6 +43,11 @@ struct GaugeEntry {
   // staggered workspace (double-word, whole lattice: even half then odd half)
   float4 *sb = nullptr, *sx = nullptr, *sr = nullptr, *sp = nullptr, *sAp = nullptr, *st = nullptr,
          *srhs = nullptr;
+  // HMC workspace: momenta, gauge force, backup of the FP64 links (FP64 link
+  // fields) and the momentum normals of one refresh
+  double2 *hP = nullptr, *hG = nullptr, *hUbak = nullptr;
+  double *hNormals = nullptr;
+  double *hPart = nullptr;  // per-block partials of the HMC reductions
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<void *> device_allocs;
 
@@ -64,6 +69,7 @@ struct GaugeEntry {
   cudaError_t ensure_force();
   cudaError_t ensure_multishift(int nshift);
   cudaError_t ensure_staggered();
+  cudaError_t ensure_hmc();
   size_t linkfield_bytes() const { return (size_t)72 * 16 * g.vh; }  // [2][4][9][vh] float4
   size_t link_canon_bytes() const { return sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh); }
   int n_partials() const;

@@ -69,6 +69,21 @@ class jqcd_solve_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class jqcd_hmc_params(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("kappa", ctypes.c_double), ("tau", ctypes.c_double),
+                ("tol", ctypes.c_double), ("n_md", ctypes.c_int32), ("fermions", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("maxiter", ctypes.c_int32)]
+
+
+class jqcd_hmc_info(ctypes.Structure):
+    _fields_ = [("H_old", ctypes.c_double), ("H_new", ctypes.c_double), ("dH", ctypes.c_double),
+                ("plaquette", ctypes.c_double), ("seconds", ctypes.c_double), ("accepted", ctypes.c_int32),
+                ("cg_iters", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _st = ctypes.c_int32
@@ -122,6 +137,10 @@ _SIGNATURES = {
                                    ctypes.POINTER(jqcd_solve_info)]),
     "jqcd_staggered_solve_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_double, _vp, _vp,
                                        _vp, _vp, ctypes.POINTER(jqcd_solve_info), _vp]),
+    "jqcd_hmc_trajectory": (_st, [_vp, _u64, ctypes.POINTER(jqcd_hmc_params), _dp, _dp, ctypes.c_double,
+                                  ctypes.POINTER(jqcd_hmc_info)]),
+    "jqcd_gauge_plaquette": (_st, [_vp, _u64, _dp]),
+    "jqcd_gauge_download": (_st, [_vp, _u64, _dp]),
     "jqcd_cg_multishift": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp, _dp,
                                  ctypes.POINTER(_dp), ctypes.POINTER(jqcd_solve_info)]),
     "jqcd_cg_multishift_dev": (_st, [_vp, _u64, ctypes.POINTER(jqcd_solve_params), ctypes.c_int32, _dp,
@@ -351,6 +370,35 @@ class Gauge:
         if check:
             self.ctx.check(st, "jqcd_cg_solve")
         return x, info.as_dict(), st
+
+    # ---- hybrid Monte Carlo (paper: MDstep!) -------------------------------------
+    def plaquette(self) -> float:
+        v = ctypes.c_double(0.0)
+        self.ctx.check(jqcd_gauge_plaquette(self.ctx.h, self.id, ctypes.byref(v)), "jqcd_gauge_plaquette")
+        return v.value
+
+    def download(self) -> np.ndarray:
+        out = np.empty(self.link_shape(), dtype=np.complex128)
+        self.ctx.check(jqcd_gauge_download(self.ctx.h, self.id, _host_ptr(out)), "jqcd_gauge_download")
+        return out
+
+    def hmc_trajectory(self, normals, xi, u, beta, kappa=0.12, tau=1.0, n_md=10, tol=1e-10, mode=CG_DW,
+                       maxiter=20000, check=True):
+        """One trajectory on this field; normals: [mu, t, z, y, x, 8] (or flat, link-major),
+        xi: host spinor or None (pure gauge); u: Metropolis uniform.  Returns (info, status)."""
+        nrm = np.ascontiguousarray(normals, dtype=np.float64)
+        p = jqcd_hmc_params(float(beta), float(kappa), float(tau), float(tol), int(n_md), int(xi is not None),
+                            int(mode), int(maxiter))
+        xp = None
+        if xi is not None:
+            xi = np.ascontiguousarray(xi, dtype=np.complex128)
+            xp = _host_ptr(xi)
+        info = jqcd_hmc_info()
+        st = jqcd_hmc_trajectory(self.ctx.h, self.id, ctypes.byref(p), nrm.ctypes.data_as(_dp), xp, float(u),
+                                 ctypes.byref(info))
+        if check:
+            self.ctx.check(st, "jqcd_hmc_trajectory")
+        return info.as_dict(), st
 
     # ---- staggered fermions (paper: Dirac_operator "staggered") ----------------------
     def colour_shape(self):
