@@ -59,9 +59,12 @@ __device__ __forceinline__ void lp_stage_issue(float4 *st, const void *in, const
   for (int k = 0; k < 3; ++k) cp_async16(st + (S::kSpin + k) * kHopThreads + tid, L + k * vh, LINK_L1);
 }
 
-// Spinor and link of one stage slot (st already offset by the thread).
+// Spinor and link of one stage slot (st already offset by the thread).  For
+// FP16 the spinor comes back unscaled and *norm holds the site norm (the
+// caller scales the projected half-spinor: 12 multiplies instead of 24);
+// for FP32 *norm = 1.
 template <int PREC>
-__device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3], cf (&u)[3][3]) {
+__device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3], cf (&u)[3][3], float *norm) {
   typedef LpStage<PREC> S;
   if (PREC == PREC_F32) {
 #pragma unroll
@@ -70,8 +73,9 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
       psi[(2 * j) / 3][(2 * j) % 3] = cf{v.x, v.y};
       psi[(2 * j + 1) / 3][(2 * j + 1) % 3] = cf{v.z, v.w};
     }
+    *norm = 1.f;
   } else {
-    const float n = reinterpret_cast<const float *>(st + 3 * kHopThreads)[0];
+    *norm = reinterpret_cast<const float *>(st + 3 * kHopThreads)[0];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const uint4 v = reinterpret_cast<const uint4 *>(st)[j * kHopThreads];
@@ -80,7 +84,7 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
       for (int q = 0; q < 4; ++q) {
         const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w[q]));
         const int k = 4 * j + q;
-        psi[k / 3][k % 3] = cf{f.x * n, f.y * n};
+        psi[k / 3][k % 3] = cf{f.x, f.y};
       }
     }
   }
@@ -88,14 +92,23 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
                                 st[(S::kSpin + 2) * kHopThreads], u);
 }
 
-// One hop: project, boundary sign, link multiply, reconstruct into acc.
-template <int MU, bool BWD, bool DAG>
-__device__ __forceinline__ void lp_apply(const cf (&psi)[4][3], const cf (&u)[3][3], bool neg,
+// One hop: project, site norm (FP16) and boundary sign, link multiply,
+// reconstruct into acc.
+template <int PREC, int MU, bool BWD, bool DAG>
+__device__ __forceinline__ void lp_apply(const cf (&psi)[4][3], const cf (&u)[3][3], float norm, bool neg,
                                          cf (&acc)[4][3]) {
   constexpr int S = (BWD != DAG) ? 1 : -1;
   cf h[2][3], r[2][3];
   project<MU, S>(psi, h);
-  if (MU == 3) PT_F32Links::negate_if(h, neg);  // only time hops cross the boundary
+  if (PREC == PREC_F16N) {
+    const float f = (MU == 3 && neg) ? -norm : norm;
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) h[a][c] = cf{h[a][c].re * f, h[a][c].im * f};
+  } else if (MU == 3) {
+    PT_F32Links::negate_if(h, neg);  // only time hops cross the boundary
+  }
   matvec2<BWD>(u, h, r);
   reconstruct<MU, S>(r, acc);
 }
@@ -128,16 +141,17 @@ __device__ __forceinline__ void lp_hop_site(float4 *smem, const void *in, const 
     cp_async_commit();
     cp_async_wait1();  // this thread's copies of hop d have landed
     cf psi[4][3], u[3][3];
-    lp_stage_read<PREC>(smem + (d & 1) * C * kHopThreads + tid, psi, u);
+    float nrm;
+    lp_stage_read<PREC>(smem + (d & 1) * C * kHopThreads + tid, psi, u, &nrm);
     switch (d) {  // d is a constant after unrolling
-      case 0: lp_apply<0, false, DAG>(psi, u, neg, acc); break;
-      case 1: lp_apply<0, true, DAG>(psi, u, neg, acc); break;
-      case 2: lp_apply<1, false, DAG>(psi, u, neg, acc); break;
-      case 3: lp_apply<1, true, DAG>(psi, u, neg, acc); break;
-      case 4: lp_apply<2, false, DAG>(psi, u, neg, acc); break;
-      case 5: lp_apply<2, true, DAG>(psi, u, neg, acc); break;
-      case 6: lp_apply<3, false, DAG>(psi, u, neg, acc); break;
-      default: lp_apply<3, true, DAG>(psi, u, neg, acc);
+      case 0: lp_apply<PREC, 0, false, DAG>(psi, u, nrm, neg, acc); break;
+      case 1: lp_apply<PREC, 0, true, DAG>(psi, u, nrm, neg, acc); break;
+      case 2: lp_apply<PREC, 1, false, DAG>(psi, u, nrm, neg, acc); break;
+      case 3: lp_apply<PREC, 1, true, DAG>(psi, u, nrm, neg, acc); break;
+      case 4: lp_apply<PREC, 2, false, DAG>(psi, u, nrm, neg, acc); break;
+      case 5: lp_apply<PREC, 2, true, DAG>(psi, u, nrm, neg, acc); break;
+      case 6: lp_apply<PREC, 3, false, DAG>(psi, u, nrm, neg, acc); break;
+      default: lp_apply<PREC, 3, true, DAG>(psi, u, nrm, neg, acc);
     }
   }
 }
