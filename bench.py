@@ -305,6 +305,29 @@ def bench_force(ctx, jqcd, synth, np, torch, stream, g, b):
     return res
 
 
+def bench_hmc(ctx, jqcd, synth, np):
+    """One HMC trajectory (the paper's MD step: 10 leapfrog steps of length
+    1/10, plaquette action beta 5.5, two-flavour Wilson fermions kappa 0.12,
+    solves to 1e-10) on a 16^4 exp(i 0.3 H) field, double-word and mixed-FP16
+    solves; random numbers seeded on the host."""
+    d = (16, 16, 16, 16)
+    U = synth.gauge(d, "expi", eps=EPS, seed=61)
+    rng = np.random.default_rng(62)
+    normals = rng.normal(size=(4,) + tuple(reversed(d)) + (8,))
+    xi = synth.gaussian_spinor(d, seed=63)
+    out = {"workload": "16^4, beta 5.5, kappa 0.12, 10 MD steps, tau 1, tol 1e-10"}
+    for name, mode in [("dw", jqcd.CG_DW), ("mixed_f16", jqcd.CG_MIXED_F16)]:
+        g = ctx.gauge_upload(d, U)
+        g.hmc_trajectory(normals, xi, 0.0, 5.5, kappa=KAPPA, n_md=2, tol=TOL, mode=mode)  # warm-up
+        g.free()
+        g = ctx.gauge_upload(d, U)
+        info, st = g.hmc_trajectory(normals, xi, 0.0, 5.5, kappa=KAPPA, n_md=10, tol=TOL, mode=mode)
+        out[name] = {"s": round(info["seconds"], 4), "cg_iters": info["cg_iters"], "dH": info["dH"],
+                     "plaquette": info["plaquette"], "status": st}
+        g.free()
+    return out
+
+
 def bench_staggered(jqcd, synth, torch, stream, g):
     """Staggered operator on the workload lattice and links: the double-word
     hop alone (algorithmic bytes per output site: colour vector in once, 8
@@ -624,6 +647,7 @@ def run_gpu(args):
     force = bench_force(ctx, jqcd, synth, np, torch, stream, g, b)
     multishift = bench_multishift(jqcd, g, stream, be)
     staggered = bench_staggered(jqcd, synth, torch, stream, g)
+    hmc = bench_hmc(ctx, jqcd, synth, np)
     batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
     serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
 
@@ -671,6 +695,7 @@ def run_gpu(args):
             "force": force,
             "multishift": multishift,
             "staggered": staggered,
+            "hmc": hmc,
             "batch": batch,
             "serve": serve,
         }
