@@ -1,9 +1,12 @@
-"""Time the even-odd hop kernel alone: python -m paper_2409_03030_gb300.hopbench.
+"""Time one operator kernel alone: python -m paper_2409_03030_gb300.hopbench.
 
-Prints one JSON line with the mean launch time (CUDA events on the launching
-stream, after warm-up) and the algorithmic bandwidth (bytes per output site:
-double-word/FP64 1536, FP32 576, FP16+norm 488, plus one spinor when the
-axpy operand is read)."""
+--op wilson (default): the even-odd Wilson hop in --prec; --op staggered: the
+double-word staggered hop; --op force: the U dS/dU kernel of the fermion
+force.  Prints one JSON line with the mean launch time (CUDA events on the
+launching stream, after warm-up) and the algorithmic bandwidth (bytes per
+output site: Wilson double-word/FP64 1536, FP32 576, FP16+norm 488, plus one
+spinor when the axpy operand is read; staggered 1248 (+48); force 1536 per
+site of the whole lattice)."""
 from __future__ import annotations
 
 import argparse
@@ -24,29 +27,48 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--axpy", action="store_true")
     ap.add_argument("--dagger", action="store_true")
+    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force"])
     a = ap.parse_args()
     dims = tuple(a.dims)
     prec = jqcd.PRECS[a.prec]
     ctx = jqcd.Context(0)
     g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=0.3, seed=1))
     stream = torch.cuda.Stream()
-    with torch.cuda.stream(stream):
-        pe, po = g.pack(synth.gaussian_spinor(dims, seed=2), prec, stream=stream)
-        out = g.empty(prec)
-    x = pe if a.axpy else None
+    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    if a.op == "wilson":
+        with torch.cuda.stream(stream):
+            pe, po = g.pack(synth.gaussian_spinor(dims, seed=2), prec, stream=stream)
+            out = g.empty(prec)
+        x = pe if a.axpy else None
+        launch = lambda: g.dslash_eo(prec, 0, int(a.dagger), po, x, out, 1.0, -0.12, stream=stream)  # noqa: E731
+        per_site = HOP_BYTES[a.prec][0] + (HOP_BYTES[a.prec][1] if a.axpy else 0)
+        n_sites = vh
+    elif a.op == "staggered":
+        with torch.cuda.stream(stream):
+            pe, po = g.stag_pack(synth.gaussian_colour(dims, seed=2), stream=stream)
+            out = g.stag_empty()
+        x = pe if a.axpy else None
+        launch = lambda: g.stag_dslash_eo(0, int(a.dagger), po, x, out, 1.0, -0.5, stream=stream)  # noqa: E731
+        per_site, n_sites = 1248 + (48 if a.axpy else 0), vh
+    else:
+        with torch.cuda.stream(stream):
+            xe, xo = g.pack(synth.gaussian_spinor(dims, seed=2), 0, stream=stream)
+            ye, yo = g.pack(synth.gaussian_spinor(dims, seed=3), 0, stream=stream)
+            out = torch.empty(g.linkfield_bytes(), dtype=torch.uint8, device=xe.device)
+        launch = lambda: g.fermi_force_dev(0.12, xe, xo, ye, yo, out, stream=stream)  # noqa: E731
+        per_site, n_sites = 1536, 2 * vh
     for _ in range(a.warmup):
-        g.dslash_eo(prec, 0, int(a.dagger), po, x, out, 1.0, -0.12, stream=stream)
+        launch()
     stream.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(a.iters):
-        g.dslash_eo(prec, 0, int(a.dagger), po, x, out, 1.0, -0.12, stream=stream)
+        launch()
     e1.record(stream)
     stream.synchronize()
     ms = e0.elapsed_time(e1) / a.iters
-    vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
-    per_site = HOP_BYTES[a.prec][0] + (HOP_BYTES[a.prec][1] if a.axpy else 0)
-    print(json.dumps({"dims": dims, "prec": a.prec, "axpy": a.axpy, "dagger": a.dagger,
+    vh = n_sites
+    print(json.dumps({"op": a.op, "dims": dims, "prec": a.prec, "axpy": a.axpy, "dagger": a.dagger,
                       "us_per_launch": round(ms * 1e3, 2), "bytes_per_launch": vh * per_site,
                       "gbs": round(vh * per_site / (ms * 1e-3) / 1e9, 1)}))
     g.free()
