@@ -31,7 +31,7 @@ __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
 // STAGE 3: Ap = w - kappa^2 H^dag_eo t, then (UPDATE) x_s += alpha p,
 //          r_s -= alpha Ap, ||r_s||^2 without storing Ap.
 template <int PREC, int STAGE, bool UPDATE>
-__global__ void __launch_bounds__(kLpThreads, 5) batch_lp_hop_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
   extern __shared__ float4 lsm[];
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
