@@ -76,42 +76,26 @@ __device__ __forceinline__ void load_dw_spinor_p(const float4 *base, int64_t vh,
 __device__ __forceinline__ mul2 conj_re(p2 z) { return mul2{f2_lo(z.h), f2_lo(z.l)}; }
 __device__ __forceinline__ mul2 conj_im(p2 z) { return mul2{f2_neg(f2_hi(z.h)), f2_neg(f2_hi(z.l))}; }
 
-// One part of M: P_ba = sum_s v_sb conj(c_sa) with, for the A part
-// (SWAP = false), v = projected (1 + S gamma_mu) Z at site iz and c = adjoint
-// half of W at site iw; for the B^dag part (SWAP = true) the roles swap:
-// v = adjoint half of Z (Y(x+mu)), c = projected W (X(x)).  M = P (first
-// part) or M + P.
-template <int MU, int S>
-__device__ __forceinline__ void outer_part(const float4 *Zf, int64_t iz, const float4 *Wf, int64_t iw,
-                                           int64_t vh, p2 (&M)[3][3], bool SWAP) {
-  p2 v[2][3], c[2][3];
-  {
-    p2 s4[4][3];
-    if (!SWAP) {
-      load_dw_spinor_p(Zf, vh, iz, s4);
-      project_p<MU>(s4, v, (float)S);
-      load_dw_spinor_p(Wf, vh, iw, s4);
-      adjoint_half_p<MU, S>(s4, c);
-    } else {
-      load_dw_spinor_p(Zf, vh, iz, s4);
-      adjoint_half_p<MU, S>(s4, v);
-      load_dw_spinor_p(Wf, vh, iw, s4);
-      project_p<MU>(s4, c, (float)S);
-    }
+// Projected half-spinor (rows 0, 1 of (1 + S gamma_mu) psi) with a runtime
+// direction: only this small step exists once per direction in the code.
+__device__ __forceinline__ void project_rt(int mu, const p2 (&s4)[4][3], p2 (&h)[2][3], float S) {
+  switch (mu) {
+    case 0: project_p<0>(s4, h, S); break;
+    case 1: project_p<1>(s4, h, S); break;
+    case 2: project_p<2>(s4, h, S); break;
+    default: project_p<3>(s4, h, S);
   }
-  constexpr f2 kLane0 = 0x0000000080000000ull;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const mul2 r0 = conj_re(c[0][a]), r1 = conj_re(c[1][a]);
-    const mul2 i0 = conj_im(c[0][a]), i1 = conj_im(c[1][a]);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      acc2 A = acc2_first(r0, v[0][b]), B = acc2_first(i0, v[0][b]);
-      acc2_mad(A, r1, v[1][b]);
-      acc2_mad(B, i1, v[1][b]);
-      const p2 P = p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0});
-      M[b][a] = p2_norm(SWAP ? p2_add(M[b][a], p2_norm(P)) : P);
-    }
+}
+__device__ __forceinline__ void adjoint_rt(int mu, int S, const p2 (&s4)[4][3], p2 (&w)[2][3]) {
+  switch (mu + (S > 0 ? 4 : 0)) {
+    case 0: adjoint_half_p<0, -1>(s4, w); break;
+    case 1: adjoint_half_p<1, -1>(s4, w); break;
+    case 2: adjoint_half_p<2, -1>(s4, w); break;
+    case 3: adjoint_half_p<3, -1>(s4, w); break;
+    case 4: adjoint_half_p<0, 1>(s4, w); break;
+    case 5: adjoint_half_p<1, 1>(s4, w); break;
+    case 6: adjoint_half_p<2, 1>(s4, w); break;
+    default: adjoint_half_p<3, 1>(s4, w);
   }
 }
 
@@ -120,28 +104,55 @@ struct FieldPair {
   const float4 *xe, *xo, *ye, *yo;
 };
 
-// U dS/dU of direction MU for the link at site (p, cb), packed double-word
-// arithmetic.  M_ba = A_ba + conj(B_ab) = sum_s [h_sb conj(w_sa) + wp_sb conj(hp_sa)],
-// each element as complex scalars times vector components split into the
-// real and imaginary parts of the scalars; then G = 2 kappa s U M, column by
-// column through the hop's mat-vec.
-template <int MU>
-__device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int x, int y, int z, int t,
+// U dS/dU of direction mu for the link at site (p, cb), packed double-word
+// arithmetic.  M_ba = A_ba + conj(B_ab) is built in two parts, each
+// P_ba = sum_s v_sb conj(c_sa) (complex scalars conj(c) times the vector
+// components v, split into the scalars' real and imaginary parts):
+//   part 0 (A):      v = projected (1 - gamma_mu) X(x+mu), c = adjoint half of Y(x);
+//   part 1 (B^dag):  v = adjoint half of Y(x+mu), c = projected (1 + gamma_mu) X(x).
+// Then G = 2 kappa s U M column by column through the hop's mat-vec.  The
+// direction and the part are runtime values, so the heavy arithmetic exists
+// once in the instruction stream (the per-direction copies overflowed the
+// instruction cache).
+__device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int x, int y, int z, int t, int mu,
                                            const FieldPair &F, const float4 *gauge, float2 two_kappa,
                                            float4 *out) {
   const int64_t vh = g.vh;
   bool neg;
-  const int64_t nb = hop_neighbour(g, x, y, z, t, 2 * MU, neg);  // x + mu, parity 1-p
+  const int64_t nb = hop_neighbour(g, x, y, z, t, 2 * mu, neg);  // x + mu, parity 1-p
   const float4 *Xh = p ? F.xo : F.xe, *Yh = p ? F.yo : F.ye;
   const float4 *Xn = p ? F.xe : F.xo, *Yn = p ? F.ye : F.yo;
+  constexpr f2 kLane0 = 0x0000000080000000ull;
   p2 M[3][3];
-  // A part, sum_s h_sb conj(w_sa), then the B^dag part, sum_s wp_sb conj(hp_sa),
-  // added in: only one pair of half-spinor fields is live at a time
-  outer_part<MU, -1>(Xn, nb, Yh, cb, vh, M, false);  // (1 - gamma_mu) X(x+mu), Y(x)
-  outer_part<MU, 1>(Yn, nb, Xh, cb, vh, M, true);    // (1 + gamma_mu) X(x), Y(x+mu), swapped roles
+#pragma unroll 1
+  for (int part = 0; part < 2; ++part) {
+    p2 v[2][3], c[2][3];
+    {
+      p2 s4[4][3];
+      load_dw_spinor_p(part ? Yn : Xn, vh, nb, s4);
+      if (part) adjoint_rt(mu, 1, s4, v);
+      else project_rt(mu, s4, v, -1.f);
+      load_dw_spinor_p(part ? Xh : Yh, vh, cb, s4);
+      if (part) project_rt(mu, s4, c, 1.f);
+      else adjoint_rt(mu, -1, s4, c);
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const mul2 r0 = conj_re(c[0][a]), r1 = conj_re(c[1][a]);
+      const mul2 i0 = conj_im(c[0][a]), i1 = conj_im(c[1][a]);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        acc2 A = acc2_first(r0, v[0][b]), B = acc2_first(i0, v[0][b]);
+        acc2_mad(A, r1, v[1][b]);
+        acc2_mad(B, i1, v[1][b]);
+        const p2 P = p2_norm(p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0}));
+        M[b][a] = part ? p2_norm(p2_add(M[b][a], P)) : P;
+      }
+    }
+  }
   p2 U[3][3];
   {
-    const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(gauge) + (size_t)((p * 4 + MU) * 9) * vh + cb;
+    const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(gauge) + (size_t)((p * 4 + mu) * 9) * vh + cb;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const ulonglong2 v = __ldcs(L + k * vh);
@@ -151,7 +162,7 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
   const float fs = neg ? -1.f : 1.f;  // boundary sign, exact
   const f2 fh = f2_make(fs * two_kappa.x, fs * two_kappa.x);
   const mul2 Fm{fh, f2_make(fs * two_kappa.y, fs * two_kappa.y)};
-  ulonglong2 *o = reinterpret_cast<ulonglong2 *>(out) + (size_t)((p * 4 + MU) * 9) * vh + cb;
+  ulonglong2 *o = reinterpret_cast<ulonglong2 *>(out) + (size_t)((p * 4 + mu) * 9) * vh + cb;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const p2 col[3] = {M[0][a], M[1][a], M[2][a]};
@@ -175,14 +186,7 @@ __global__ void __launch_bounds__(kForceThreads, 3) force_kernel(Geom g, FieldPa
   int x, y, z, t;
   cb_coords(g, cb, p, x, y, z, t);
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {  // one direction's code live at a time
-    switch (mu) {
-      case 0: force_link<0>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
-      case 1: force_link<1>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
-      case 2: force_link<2>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out); break;
-      default: force_link<3>(g, p, cb, x, y, z, t, F, gauge, two_kappa, out);
-    }
-  }
+  for (int mu = 0; mu < 4; ++mu) force_link(g, p, cb, x, y, z, t, mu, F, gauge, two_kappa, out);
 }
 
 // out = gamma5 in on a whole-lattice double-word spinor (chunks k = 3*spin + c;
