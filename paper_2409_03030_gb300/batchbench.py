@@ -27,6 +27,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--mode", default="mixed_f16", choices=["mixed_f16", "mixed_f32"])
+    ap.add_argument("--verbose", action="store_true", help="phase times of each batch on stderr")
     a = ap.parse_args()
     ctx = jqcd.Context(0)
     dA, dB = (24, 24, 24, 48), (16, 16, 16, 16)
@@ -38,7 +39,7 @@ def main():
     for rep in range(a.reps):
         t0 = time.perf_counter()
         xs, infos, st = ctx.cg_solve_batch(gauges, bs, [0.12] * 24, [1e-10] * 24,
-                                           mode=jqcd.MODES[a.mode])
+                                           mode=jqcd.MODES[a.mode], verbose=2 if a.verbose else 0)
         dt = time.perf_counter() - t0
         print(json.dumps({"rep": rep, "seconds": round(dt, 4), "status": st,
                           "iters": [infos[0]["iters"], infos[12]["iters"]],

@@ -391,22 +391,41 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
     E.reset(new BatchEngine(hp, n, ctx->stream, ctx->sm_count));
     CK(E->init(), "batch engine init");
   }
+  const bool timing = params[0].verbose >= 2;  // phase times on stderr
+  auto tnow = [&]() {
+    if (timing) cudaStreamSynchronize(ctx->stream);
+    return std::chrono::steady_clock::now();
+  };
+  const auto t0 = tnow();
   for (int i = 0; i < n; ++i) CK(E->admit(i, G[i], params[i], b[i]), "batch admit");
+  const auto t1 = tnow();
   CK(E->autotune(), "batch autotune");
+  const auto t2 = tnow();
   int left = n;
   std::vector<int> done;
   jqcd_status worst = JQCD_OK;
+  double t_collect = 0.0;
   while (left > 0) {
     CK(E->run(8), "batch iterations");
     done.clear();
     CK(E->poll(&done), "batch poll");
     for (int i : done) {
+      const auto c0 = std::chrono::steady_clock::now();
       jqcd_solve_info inf;
       CK(E->collect(i, x[i], &inf), "batch collect");
+      t_collect += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
       if (infos) infos[i] = inf;
       if (inf.status != JQCD_OK && worst == JQCD_OK) worst = inf.status;
       --left;
     }
+  }
+  if (timing) {
+    const auto t3 = tnow();
+    auto sec = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
+      return std::chrono::duration<double>(b - a).count();
+    };
+    fprintf(stderr, "jqcd batch: admit %.4f s, autotune %.4f s, iterate+collect %.4f s (collect %.4f s)\n",
+            sec(t0, t1), sec(t1, t2), sec(t2, t3), t_collect);
   }
   if (worst != JQCD_OK) return fail(ctx, worst, "cg_solve_batch: a solve did not converge");
   return JQCD_OK;

@@ -234,7 +234,7 @@ class Context:
         return st
 
     def cg_solve_batch(self, gauges, bs, kappas, tols, mode=CG_MIXED_F16, maxiter=20000,
-                       delta=0.0, check=True):
+                       delta=0.0, check=True, verbose=0):
         """jqcd_cg_solve_batch: solve D_i x_i = b_i for all i together.
         gauges: list of Gauge; bs: host spinors; kappas, tols: per solve.
         Returns (list of x, list of info dicts, status)."""
@@ -243,7 +243,7 @@ class Context:
         xs = [np.zeros_like(b) for b in bs]
         ids = (ctypes.c_uint64 * n)(*[g.id for g in gauges])
         params = (jqcd_solve_params * n)(*[
-            Gauge.params(kappas[i], tols[i], maxiter, True, mode, 0, delta, False)
+            Gauge.params(kappas[i], tols[i], maxiter, True, mode, verbose, delta, False)
             for i in range(n)])
         bp = (_dp * n)(*[_host_ptr(b) for b in bs])
         xp = (_dp * n)(*[_host_ptr(x) for x in xs])
