@@ -240,7 +240,7 @@ class Context:
         Returns (list of x, list of info dicts, status)."""
         n = len(bs)
         bs = [np.ascontiguousarray(b, dtype=np.complex128) for b in bs]
-        xs = [np.zeros_like(b) for b in bs]
+        xs = [np.empty_like(b) for b in bs]  # written in full by the library
         ids = (ctypes.c_uint64 * n)(*[g.id for g in gauges])
         params = (jqcd_solve_params * n)(*[
             Gauge.params(kappas[i], tols[i], maxiter, True, mode, verbose, delta, False)
@@ -362,7 +362,7 @@ class Gauge:
                  verbose=0, delta=0.0, x0=None, check=True):
         """Solve D x = b from host arrays; returns (x, info dict, status)."""
         b = np.ascontiguousarray(b, dtype=np.complex128)
-        x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
+        x = np.empty_like(b) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
         p = self.params(kappa, tol, maxiter, eo, mode, verbose, delta, x0 is not None)
         info = jqcd_solve_info()
         st = jqcd_cg_solve(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(b), _host_ptr(x),
@@ -441,7 +441,7 @@ class Gauge:
     def stag_solve(self, b, mass, tol=1e-10, maxiter=20000, check=True):
         """Solve the staggered D x = b from host arrays; returns (x, info dict, status)."""
         b = np.ascontiguousarray(b, dtype=np.complex128)
-        x = np.zeros_like(b)
+        x = np.empty_like(b)
         p = self.params(0.0, tol, maxiter, True, CG_DW)
         info = jqcd_solve_info()
         st = jqcd_staggered_solve(self.ctx.h, self.id, ctypes.byref(p), float(mass), _host_ptr(b), _host_ptr(x),
@@ -466,7 +466,7 @@ class Gauge:
         rhs = np.ascontiguousarray(rhs, dtype=np.complex128)
         n = len(shifts)
         sh = (ctypes.c_double * n)(*[float(v) for v in shifts])
-        xs = [np.zeros_like(rhs) for _ in range(n)]
+        xs = [np.empty_like(rhs) for _ in range(n)]
         xp = (_dp * n)(*[_host_ptr(x) for x in xs])
         infos = (jqcd_solve_info * n)()
         p = self.params(kappa, tol, maxiter, True, CG_DW)
@@ -509,7 +509,7 @@ class Gauge:
         """(S, U dS/dU as links [mu,t,z,y,x,b,a], info dict, status)."""
         eta = np.ascontiguousarray(eta, dtype=np.complex128)
         p = self.params(kappa, tol, maxiter, True, mode)
-        G = np.zeros(self.link_shape(), dtype=np.complex128)
+        G = np.empty(self.link_shape(), dtype=np.complex128)
         S = ctypes.c_double(0.0)
         info = jqcd_solve_info()
         st = jqcd_fermi_force(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(eta), _host_ptr(G),
@@ -522,7 +522,7 @@ class Gauge:
         """U dS/dU from given X = (D^dag D)^-1 eta and Y = D X (host spinors)."""
         X = np.ascontiguousarray(X, dtype=np.complex128)
         Y = np.ascontiguousarray(Y, dtype=np.complex128)
-        G = np.zeros(self.link_shape(), dtype=np.complex128)
+        G = np.empty(self.link_shape(), dtype=np.complex128)
         self.ctx.check(jqcd_fermi_force_xy(self.ctx.h, self.id, float(kappa), _host_ptr(X), _host_ptr(Y),
                                            _host_ptr(G)), "jqcd_fermi_force_xy")
         return G
