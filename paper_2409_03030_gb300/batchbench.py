@@ -36,10 +36,12 @@ def main():
     bs = [pinned(synth.point_source(dA, s, c)) for s in range(4) for c in range(3)]
     bs += [pinned(synth.gaussian_spinor(dB, seed=100 + i)) for i in range(12)]
     gauges = [gA] * 12 + [gB] * 12
+    outs = [pinned(b * 0) for b in bs]
     for rep in range(a.reps):
         t0 = time.perf_counter()
         xs, infos, st = ctx.cg_solve_batch(gauges, bs, [0.12] * 24, [1e-10] * 24,
-                                           mode=jqcd.MODES[a.mode], verbose=2 if a.verbose else 0)
+                                           mode=jqcd.MODES[a.mode], verbose=2 if a.verbose else 0,
+                                           out=outs)
         dt = time.perf_counter() - t0
         print(json.dumps({"rep": rep, "seconds": round(dt, 4), "status": st,
                           "iters": [infos[0]["iters"], infos[12]["iters"]],

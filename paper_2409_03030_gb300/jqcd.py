@@ -234,13 +234,17 @@ class Context:
         return st
 
     def cg_solve_batch(self, gauges, bs, kappas, tols, mode=CG_MIXED_F16, maxiter=20000,
-                       delta=0.0, check=True, verbose=0):
+                       delta=0.0, check=True, verbose=0, out=None):
         """jqcd_cg_solve_batch: solve D_i x_i = b_i for all i together.
         gauges: list of Gauge; bs: host spinors; kappas, tols: per solve.
         Returns (list of x, list of info dicts, status)."""
         n = len(bs)
         bs = [np.ascontiguousarray(b, dtype=np.complex128) for b in bs]
-        xs = [np.empty_like(b) for b in bs]  # written in full by the library
+        # written in full by the library; out: caller's C-contiguous complex128 arrays to reuse
+        xs = list(out) if out is not None else [np.empty_like(b) for b in bs]
+        for x, b in zip(xs, bs):
+            if x.shape != b.shape or x.dtype != np.complex128 or not x.flags.c_contiguous:
+                raise ValueError("out arrays must match b (C-contiguous complex128)")
         ids = (ctypes.c_uint64 * n)(*[g.id for g in gauges])
         params = (jqcd_solve_params * n)(*[
             Gauge.params(kappas[i], tols[i], maxiter, True, mode, verbose, delta, False)
@@ -359,10 +363,18 @@ class Gauge:
                                  int(verbose), float(delta), int(bool(use_x0)), 0)
 
     def cg_solve(self, b: np.ndarray, kappa, tol=1e-10, maxiter=20000, eo=True, mode=CG_DW,
-                 verbose=0, delta=0.0, x0=None, check=True):
-        """Solve D x = b from host arrays; returns (x, info dict, status)."""
+                 verbose=0, delta=0.0, x0=None, check=True, out=None):
+        """Solve D x = b from host arrays; returns (x, info dict, status).  out: a
+        C-contiguous complex128 array to write x into (reused, no allocation)."""
         b = np.ascontiguousarray(b, dtype=np.complex128)
-        x = np.empty_like(b) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
+        if out is not None:
+            if out.shape != b.shape or out.dtype != np.complex128 or not out.flags.c_contiguous:
+                raise ValueError("out must match b (C-contiguous complex128)")
+            x = out
+            if x0 is not None:
+                x[...] = x0
+        else:
+            x = np.empty_like(b) if x0 is None else np.array(x0, dtype=np.complex128, order="C")
         p = self.params(kappa, tol, maxiter, eo, mode, verbose, delta, x0 is not None)
         info = jqcd_solve_info()
         st = jqcd_cg_solve(self.ctx.h, self.id, ctypes.byref(p), _host_ptr(b), _host_ptr(x),
