@@ -1,0 +1,156 @@
+// Last hop of the double-word even-odd normal operator fused with the CG
+// update (conjugate gradient on Mhat^dag Mhat, Sec. 3 of the paper), for the
+// double-word solver and for the FP32 / FP16-with-norm inner solver of the
+// mixed-precision CG.
+//
+// In one CG iteration alpha = ||r||^2 / <p, Mhat^dag Mhat p> and
+// <p, Mhat^dag Mhat p> = ||Mhat p||^2 are known once the second hop has
+// formed w = Mhat p.  The fourth hop, Ap = w - k^2 H^dag_eo t, therefore
+// applies x += alpha p and r -= alpha Ap at its own site and forms the
+// block partial of ||r||^2: Ap never reaches memory and the separate update
+// kernel (which read x, r, p, Ap and wrote x, r) is gone.
+#include <cuda_runtime.h>
+
+#include "fields.cuh"
+#include "hop_dwp.cuh"
+#include "hop_lp.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+#include "solver.h"
+
+namespace jqcd {
+
+namespace {
+
+// q = a*w + b*acc is (Ap)(idx); x += alpha p, r -= alpha q in place; returns
+// this thread's ||r||^2.  Every operand is a 16-byte double-word chunk.
+__device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float4 *__restrict__ w_base,
+                                              const float4 *__restrict__ p_base,
+                                              float4 *__restrict__ x_base, float4 *__restrict__ r_base,
+                                              int64_t vh, int64_t idx, float2 a_split, float2 b_split,
+                                              float2 alpha) {
+  const mul2 Bm{f2_make(b_split.x, b_split.x), f2_make(b_split.y, b_split.y)};
+  const mul2 Am{f2_make(a_split.x, a_split.x), f2_make(a_split.y, a_split.y)};
+  const mul2 Al{f2_make(alpha.x, alpha.x), f2_make(alpha.y, alpha.y)};
+  const mul2 Ml{f2_neg(Al.h), f2_neg(Al.l)};
+  const ulonglong2 *__restrict__ wp = reinterpret_cast<const ulonglong2 *>(w_base) + idx;
+  const ulonglong2 *__restrict__ pp = reinterpret_cast<const ulonglong2 *>(p_base) + idx;
+  ulonglong2 *__restrict__ xp = reinterpret_cast<ulonglong2 *>(x_base) + idx;
+  ulonglong2 *__restrict__ rp = reinterpret_cast<ulonglong2 *>(r_base) + idx;
+  acc2 nq{0ull, 0ull};
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const ulonglong2 wv = __ldg(wp + k * vh), pv = __ldg(pp + k * vh);
+    const ulonglong2 xv = xp[k * vh], rv = rp[k * vh];
+    acc2 R = acc2_first(Bm, p2_norm(acc[k / 3][k % 3]));
+    acc2_mad(R, Am, p2{wv.x, wv.y});
+    const p2 q = p2_norm(acc2_get(R));
+    const p2 xn = p2_norm(p2_add(p2{xv.x, xv.y}, acc2_get(acc2_first(Al, p2{pv.x, pv.y}))));
+    const p2 rn = p2_norm(p2_add(p2{rv.x, rv.y}, acc2_get(acc2_first(Ml, q))));
+    xp[k * vh] = make_ulonglong2(xn.h, xn.l);
+    rp[k * vh] = make_ulonglong2(rn.h, rn.l);
+    const mul2 Q{rn.h, rn.l};
+    if (k == 0) nq = acc2_first(Q, rn);
+    else acc2_mad(nq, Q, rn);
+  }
+  float s0, s1, c0, c1;
+  f2_split(nq.s, s0, s1);
+  f2_split(nq.c, c0, c1);
+  float s, e;
+  two_sum(s0, s1, s, e);
+  return dwacc{s, __fadd_rn(__fadd_rn(c0, c1), e)};
+}
+
+__global__ void __launch_bounds__(kHopThreads, 3)
+    hop_dwp_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
+                      float4 *__restrict__ r, const SolverScalars *__restrict__ S) {
+  extern __shared__ float4 dsm[];
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  dwacc nrm{0.f, 0.f};
+  if (idx < P.g.vh) {
+    p2 acc[4][3];
+    dwp_hop_site<true>(dsm, reinterpret_cast<const float4 *>(P.in),
+                       reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
+    nrm = dwp_store_cg(acc, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx, P.a_split,
+                       P.b_split, S->alpha_dw);
+  }
+  const double s = block_sum_dw(nrm);
+  if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+}
+
+// Low-precision form for the inner CG: Ap = a w + b H^dag t in FP32 registers
+// (never rounded to the storage precision), then the FP32 update of the
+// inner solution xs and residual rs with alpha_f, as the unfused update
+// kernel does, and ||rs||^2 per hop block.
+template <int PREC>
+__global__ void __launch_bounds__(kHopThreads)
+    hop_lp_cg_kernel(const HopParams P, const void *__restrict__ p, float4 *__restrict__ xs,
+                     float4 *__restrict__ rs, const SolverScalars *__restrict__ S) {
+  typedef PT<PREC> T;
+  extern __shared__ float4 lsm[];
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float n2 = 0.f;
+  if (idx < P.g.vh) {
+    cf acc[4][3];
+    lp_hop_site<PREC, true, false>(lsm, P.in, reinterpret_cast<const float4 *>(P.gauge), P.g,
+                                   P.out_parity, idx, acc);
+    const float a = (float)P.a, b = (float)P.b, al = S->alpha_f;
+    cf w[4][3], pv[4][3], xv[4][3], rv[4][3];
+    T::load_spinor(P.x, P.g.vh, idx, w);
+    T::load_spinor(p, P.g.vh, idx, pv);
+    PT<PREC_F32>::load_spinor(xs, P.g.vh, idx, xv);
+    PT<PREC_F32>::load_spinor(rs, P.g.vh, idx, rv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const cf q = T::axpby(a, w[k / 3][k % 3], b, acc[k / 3][k % 3]);
+      cf &x = xv[k / 3][k % 3], &r = rv[k / 3][k % 3];
+      const cf pp = pv[k / 3][k % 3];
+      x.re = fmaf(al, pp.re, x.re);
+      x.im = fmaf(al, pp.im, x.im);
+      r.re = fmaf(-al, q.re, r.re);
+      r.im = fmaf(-al, q.im, r.im);
+      n2 = fmaf(r.re, r.re, fmaf(r.im, r.im, n2));
+    }
+    PT<PREC_F32>::store_spinor(xs, P.g.vh, idx, xv);
+    PT<PREC_F32>::store_spinor(rs, P.g.vh, idx, rv);
+  }
+  const double s = block_sum_f(n2);
+  if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+}
+
+template <int PREC>
+cudaError_t launch_lp_cg_t(const HopParams &P, const void *p, float4 *xs, float4 *rs,
+                           const SolverScalars *S, cudaStream_t s) {
+  hop_lp_cg_kernel<PREC><<<hop_blocks(P.g.vh), kHopThreads, lp_stage_smem<PREC>(), s>>>(P, p, xs, rs, S);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_hop_lp_cg(int prec, const HopParams &P, const void *p, float4 *xs, float4 *rs,
+                             const SolverScalars *S, cudaStream_t s) {
+  note_launch();
+  switch (prec) {
+    case PREC_F32: return launch_lp_cg_t<PREC_F32>(P, p, xs, rs, S, s);
+    case PREC_F16N: return launch_lp_cg_t<PREC_F16N>(P, p, xs, rs, S, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
+                             const SolverScalars *S, cudaStream_t s) {
+  note_launch();
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDwpSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  hop_dwp_cg_kernel<<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P, p, x, r, S);
+  return cudaGetLastError();
+}
+
+}  // namespace jqcd

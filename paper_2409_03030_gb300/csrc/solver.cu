@@ -98,7 +98,7 @@ cudaError_t GaugeEntry::ensure_mixed(int hop_prec) {
   cudaError_t e = cudaSuccess;
   if (!mx) e = alloc(&mx, f32);
   if (e == cudaSuccess && !mr) e = alloc(&mr, f32);
-  void **vs[] = {&mp[k], &mAp[k], &mw[k], &mt[k]};
+  void **vs[] = {&mp[k], &mw[k], &mt[k]};
   for (void **v : vs)
     if (e == cudaSuccess && !*v) e = alloc(v, hb);
   return e;
@@ -200,11 +200,71 @@ struct DwSystem {
   }
 };
 
-}  // namespace
-
-static unsigned site_blocks_host(int64_t vh) {
-  return (unsigned)((vh + kBlasThreads - 1) / kBlasThreads);
+// One double-word CG iteration on the even-odd system, p -> (x, r, p):
+// w = Mhat p with ||w||^2 = <p, Mhat^dag Mhat p> fused into the second hop,
+// alpha, then the last hop of Mhat^dag w applies x += alpha p, r -= alpha Ap
+// and forms ||r||^2 itself (Ap is never stored), beta, p = r + beta p.
+cudaError_t dw_eo_cg_iteration(GaugeEntry &G, double kappa, SolverScalars *S, cudaStream_t s) {
+  const double k2 = -kappa * kappa;
+  const int nb = (int)hop_blocks(G.g.vh);
+  const int *guard = &S->halt;
+  float4 *t = G.vec_odd(G.vt), *w = G.vec_even(G.vw);
+  HopParams P = G.hop_params(PREC_DW, 1, G.vp, nullptr, t, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  cudaError_t e = launch_hop(PREC_DW, P, false, false, false, s);  // t = H_oe p
+  if (e) return e;
+  P = G.hop_params(PREC_DW, 0, t, G.vp, w, 1.0, k2, G.partials);
+  P.guard = guard;
+  e = launch_hop(PREC_DW, P, false, true, true, s);  // w = p - k^2 H_eo t, ||w||^2
+  if (e) return e;
+  e = launch_cg_alpha(G.partials, nb, S, s);
+  if (e) return e;
+  P = G.hop_params(PREC_DW, 1, w, nullptr, t, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  e = launch_hop(PREC_DW, P, true, false, false, s);  // t = H^dag_oe w
+  if (e) return e;
+  P = G.hop_params(PREC_DW, 0, t, w, nullptr, 1.0, k2, G.partials);
+  P.guard = guard;
+  e = launch_hop_dw_cg(P, G.vp, G.vsol, G.vr, S, s);  // Ap = w - k^2 H^dag_eo t; x, r, ||r||^2
+  if (e) return e;
+  e = launch_cg_beta(G.partials, nb, S, s);
+  if (e) return e;
+  return launch_dw_xpay(G.vp, G.vr, 12 * G.g.vh, S, s);
 }
+
+// One iteration of the inner CG of the mixed solver in hop precision hp on
+// the vectors p, t, w of that precision (FP32 xs and rs): the same order as
+// the double-word iteration, the update fused into the last hop.
+cudaError_t lp_eo_cg_iteration(GaugeEntry &G, int hp, int mk, double kappa, SolverScalars *S,
+                               cudaStream_t s) {
+  const double k2 = -kappa * kappa;
+  const int nb = (int)hop_blocks(G.g.vh);
+  const int *guard = &S->halt;
+  void *p = G.mp[mk], *t = G.mt[mk], *w = G.mw[mk];
+  HopParams P = G.hop_params(hp, 1, p, nullptr, t, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  cudaError_t e = launch_hop(hp, P, false, false, false, s);  // t = H_oe p
+  if (e) return e;
+  P = G.hop_params(hp, 0, t, p, w, 1.0, k2, G.partials);
+  P.guard = guard;
+  e = launch_hop(hp, P, false, true, true, s);  // w = p - k^2 H_eo t, ||w||^2
+  if (e) return e;
+  e = launch_cg_alpha(G.partials, nb, S, s);
+  if (e) return e;
+  P = G.hop_params(hp, 1, w, nullptr, t, 0.0, 1.0, nullptr);
+  P.guard = guard;
+  e = launch_hop(hp, P, true, false, false, s);  // t = H^dag_oe w
+  if (e) return e;
+  P = G.hop_params(hp, 0, t, w, nullptr, 1.0, k2, G.partials);
+  P.guard = guard;
+  e = launch_hop_lp_cg(hp, P, p, (float4 *)G.mx, (float4 *)G.mr, S, s);
+  if (e) return e;
+  e = launch_mixed_beta(G.partials, nb, S, s);
+  if (e) return e;
+  return launch_mixed_xpay(hp, p, (const float4 *)G.mr, G.g.vh, S, s);
+}
+
+}  // namespace
 
 // Bytes per output site of one hop in precision `prec` (+ the axpy operand).
 static double hop_site_bytes(int prec, bool axpy) {
@@ -292,20 +352,16 @@ static jqcd_status solve_cg(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
     // main loop: poll the device scalars every kCheckEvery iterations
     for (;;) {
       for (int k = 0; k < kCheckEvery; ++k) {
-        if (!mixed) {
+        if (!mixed && eo) {
+          CKS(dw_eo_cg_iteration(G, P.kappa, S, s));
+        } else if (!mixed) {
           CKS(A.apply(G.vp, G.vAp, G.partials, &S->halt));
           CKS(launch_cg_alpha(G.partials, A.n_hop_partials, S, s));
           CKS(launch_dw_cg_update(G.vsol, G.vr, G.vp, G.vAp, A.n, S, G.partials, s));
           CKS(launch_cg_beta(G.partials, nblas, S, s));
           CKS(launch_dw_xpay(G.vp, G.vr, A.n, S, s));
         } else {
-          CKS(apply_mdagm(G, hp, P.kappa, G.mp[mk], G.mAp[mk], G.mt[mk], G.mw[mk], G.partials,
-                          &S->halt, s));
-          CKS(launch_cg_alpha(G.partials, (int)hop_blocks(vh), S, s));
-          CKS(launch_mixed_update(hp, (float4 *)G.mx, (float4 *)G.mr, G.mp[mk], G.mAp[mk], vh, S,
-                                  G.partials, s));
-          CKS(launch_mixed_beta(G.partials, (int)site_blocks_host(vh), S, s));
-          CKS(launch_mixed_xpay(hp, G.mp[mk], (const float4 *)G.mr, vh, S, s));
+          CKS(lp_eo_cg_iteration(G, hp, mk, P.kappa, S, s));
         }
       }
       CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));

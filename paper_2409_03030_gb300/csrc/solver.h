@@ -25,10 +25,10 @@ struct GaugeEntry {
   // whole-lattice double-word solver vectors (even half first, then odd)
   float4 *vb = nullptr, *vsol = nullptr, *vr = nullptr, *vp = nullptr, *vAp = nullptr,
          *vw = nullptr, *vt = nullptr, *vrhs = nullptr;
-  // mixed-precision inner vectors (even parity): x, r in FP32; p, Ap, w in the
+  // mixed-precision inner vectors (even parity): x, r in FP32; p, w in the
   // hop precision; t odd in the hop precision
-  void *mx = nullptr, *mr = nullptr, *mp[2] = {nullptr, nullptr}, *mAp[2] = {nullptr, nullptr},
-       *mw[2] = {nullptr, nullptr}, *mt[2] = {nullptr, nullptr};
+  void *mx = nullptr, *mr = nullptr, *mp[2] = {nullptr, nullptr}, *mw[2] = {nullptr, nullptr},
+       *mt[2] = {nullptr, nullptr};
   // native FP64 solver vectors (whole lattice)
   double2 *fb = nullptr, *fsol = nullptr, *fr = nullptr, *fp = nullptr, *fAp = nullptr,
           *fw = nullptr, *ft = nullptr, *frhs = nullptr;
@@ -85,6 +85,19 @@ struct GaugeEntry {
 cudaError_t apply_mdagm(const GaugeEntry &G, int prec, double kappa, const void *in, void *out,
                         void *t_odd, void *w_even, double *partials, const int *guard,
                         cudaStream_t s);
+
+// Last hop of the double-word even-odd normal operator fused with the CG
+// update: P as for out = w - k^2 H^dag_eo t (P.x = w, P.in = t, P.out unused);
+// x += alpha p and r -= alpha Ap in place (alpha = S->alpha_dw), P.partials
+// gets one ||r||^2 per hop block.  Returns at once while *P.guard != 0.
+cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
+                             const SolverScalars *S, cudaStream_t s);
+
+// The same for the inner CG of the mixed solver in hop precision prec (FP32 or
+// FP16 with norm): p, t and w in that precision, xs and rs FP32, alpha =
+// S->alpha_f.
+cudaError_t launch_hop_lp_cg(int prec, const HopParams &P, const void *p, float4 *xs, float4 *rs,
+                             const SolverScalars *S, cudaStream_t s);
 
 // Run the solve of D x = b for the double-word b in G.vb; the solution is
 // left in G.vsol (whole lattice, double-word).
