@@ -2,7 +2,9 @@
 
 --op wilson (default): the even-odd Wilson hop in --prec; --op staggered: the
 double-word staggered hop; --op force: the U dS/dU kernel of the fermion
-force.  Prints one JSON line with the mean launch time (CUDA events on the
+force; --op cg: --iters whole even-odd CG solves (--mode, tolerance 1e-10,
+kappa 0.12) from one Gaussian source, timed by the library's own events
+(gpu_seconds), for launch lists of a complete solve.  Prints one JSON line with the mean launch time (CUDA events on the
 launching stream, after warm-up) and the algorithmic bandwidth (bytes per
 output site: Wilson double-word/FP64 1536, FP32 576, FP16+norm 488, plus one
 spinor when the axpy operand is read; staggered 1248 (+48); force 1536 per
@@ -27,7 +29,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--axpy", action="store_true")
     ap.add_argument("--dagger", action="store_true")
-    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force"])
+    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg"])
+    ap.add_argument("--mode", default="mixed_f16", choices=sorted(jqcd.MODES))
     a = ap.parse_args()
     dims = tuple(a.dims)
     prec = jqcd.PRECS[a.prec]
@@ -35,6 +38,23 @@ def main():
     g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=0.3, seed=1))
     stream = torch.cuda.Stream()
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    if a.op == "cg":
+        import numpy as np
+        b = synth.gaussian_spinor(dims, seed=2)
+        x = np.empty_like(b)
+        for _ in range(a.warmup):
+            g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[a.mode], out=x)
+        secs, iters = [], 0
+        for _ in range(a.iters):
+            _, info, _ = g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[a.mode], out=x)
+            secs.append(info["gpu_seconds"])
+            iters = info["iters"]
+        print(json.dumps({"op": "cg", "dims": dims, "mode": a.mode, "iters": iters,
+                          "ms_per_solve": round(1e3 * sum(secs) / len(secs), 3),
+                          "true_rel_resid": info["true_rel_resid"]}))
+        g.free()
+        ctx.close()
+        return
     if a.op == "wilson":
         with torch.cuda.stream(stream):
             pe, po = g.pack(synth.gaussian_spinor(dims, seed=2), prec, stream=stream)
