@@ -2,13 +2,16 @@
 
 --op wilson (default): the even-odd Wilson hop in --prec; --op staggered: the
 double-word staggered hop; --op force: the U dS/dU kernel of the fermion
-force; --op cg: --iters whole even-odd CG solves (--mode, tolerance 1e-10,
-kappa 0.12) from one Gaussian source, timed by the library's own events
-(gpu_seconds), for launch lists of a complete solve.  Prints one JSON line with the mean launch time (CUDA events on the
+force.  Prints one JSON line with the mean launch time (CUDA events on the
 launching stream, after warm-up) and the algorithmic bandwidth (bytes per
 output site: Wilson double-word/FP64 1536, FP32 576, FP16+norm 488, plus one
 spinor when the axpy operand is read; staggered 1248 (+48); force 1536 per
-site of the whole lattice)."""
+site of the whole lattice).
+
+--op cg: --iters whole even-odd CG solves (--mode, tolerance 1e-10) from one
+Gaussian source, timed by the library's own events (gpu_seconds), for launch
+lists of a complete solve; --delta, --eps and --kappa set the reliable-update
+threshold, the links and the hopping parameter."""
 from __future__ import annotations
 
 import argparse
@@ -31,11 +34,14 @@ def main():
     ap.add_argument("--dagger", action="store_true")
     ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg"])
     ap.add_argument("--mode", default="mixed_f16", choices=sorted(jqcd.MODES))
+    ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
+    ap.add_argument("--eps", type=float, default=0.3, help="link generator exp(i eps H)")
+    ap.add_argument("--kappa", type=float, default=0.12, help="hopping parameter of --op cg")
     a = ap.parse_args()
     dims = tuple(a.dims)
     prec = jqcd.PRECS[a.prec]
     ctx = jqcd.Context(0)
-    g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=0.3, seed=1))
+    g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=a.eps, seed=1))
     stream = torch.cuda.Stream()
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
     if a.op == "cg":
@@ -43,13 +49,14 @@ def main():
         b = synth.gaussian_spinor(dims, seed=2)
         x = np.empty_like(b)
         for _ in range(a.warmup):
-            g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[a.mode], out=x)
+            g.cg_solve(b, a.kappa, tol=1e-10, mode=jqcd.MODES[a.mode], delta=a.delta, out=x)
         secs, iters = [], 0
         for _ in range(a.iters):
-            _, info, _ = g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[a.mode], out=x)
+            _, info, _ = g.cg_solve(b, a.kappa, tol=1e-10, mode=jqcd.MODES[a.mode], delta=a.delta, out=x)
             secs.append(info["gpu_seconds"])
             iters = info["iters"]
-        print(json.dumps({"op": "cg", "dims": dims, "mode": a.mode, "iters": iters,
+        print(json.dumps({"op": "cg", "dims": dims, "mode": a.mode, "delta": a.delta, "eps": a.eps,
+                          "kappa": a.kappa, "iters": iters, "reliable_updates": info["reliable_updates"],
                           "ms_per_solve": round(1e3 * sum(secs) / len(secs), 3),
                           "true_rel_resid": info["true_rel_resid"]}))
         g.free()
