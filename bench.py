@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-config2", action="store_true",
                     help="skip the 32^3x64 mixed-vs-double-word CG comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-solve batch")
+    ap.add_argument("--serve-host", default="pinned", choices=["pinned", "pageable"],
+                    help="host memory of the serving stream's sources and solutions")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the serving run (0 skips it)")
     return ap.parse_args()
@@ -395,14 +397,8 @@ def bench_batch(ctx, jqcd, synth, np):
     gauges = [gA] * 12 + [gB] * 12
     mode = jqcd.CG_MIXED_F16
     # pinned host buffers, reused by both ways of solving (no page faults in the timing)
-    import torch
-
-    def pinned(a):
-        t = torch.empty(a.shape, dtype=torch.complex128, pin_memory=True)
-        t.numpy()[...] = a
-        return t.numpy()
-    bs = [pinned(b) for b in bs]
-    outs = [pinned(np.zeros_like(b)) for b in bs]
+    bs = [pinned_copy(b) for b in bs]
+    outs = [pinned_copy(np.zeros_like(b)) for b in bs]
     ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode, out=outs)  # warm-up + autotune
     t0 = time.perf_counter()
     xs, infos, st = ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode, out=outs)
@@ -423,18 +419,29 @@ def bench_batch(ctx, jqcd, synth, np):
     return out
 
 
-def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
+def pinned_copy(a):
+    """Copy of a complex128 array in pinned (page-locked) host memory."""
+    import torch
+    t = torch.empty(a.shape, dtype=torch.complex128, pin_memory=True)
+    t.numpy()[...] = a
+    return t.numpy()
+
+
+def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0, host="pinned"):
     """Poisson arrivals (seeded, mean `rate`/s) of solves with volume drawn from
     {8^4, 16^4, 24^3x48, 32^3x64}, kappa ~ U[0.10, 0.122], tol in {1e-8,
     1e-10, 1e-12}, Gaussian sources, gauge fields pre-generated (eps 0.3).
-    Latency = scheduled arrival -> completion seen by the client."""
+    Latency = scheduled arrival -> completion seen by the client.  host:
+    "pinned" (sources and solution buffers page-locked, as a serving front
+    end holds them) or "pageable" (plain numpy arrays)."""
     vols = [(8, 8, 8, 8), (16, 16, 16, 16), (24, 24, 24, 48), (32, 32, 32, 64)]
     gauges = [ctx.gauge_upload(d, synth.gauge(d, "expi", eps=EPS, seed=70 + i))
               for i, d in enumerate(vols)]
     n_src, n_x = 3, 8
-    srcs = [[synth.gaussian_spinor(d, seed=800 + 10 * i + j) for j in range(n_src)]
+    keep = pinned_copy if host == "pinned" else (lambda a: a)
+    srcs = [[keep(synth.gaussian_spinor(d, seed=800 + 10 * i + j)) for j in range(n_src)]
             for i, d in enumerate(vols)]
-    xpool = [[np.zeros(synth.spinor_shape(d), np.complex128) for _ in range(n_x)] for d in vols]
+    xpool = [[keep(np.zeros(synth.spinor_shape(d), np.complex128)) for _ in range(n_x)] for d in vols]
     free = [list(range(n_x)) for _ in vols]
     rng = np.random.default_rng(20261202)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
@@ -446,6 +453,7 @@ def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
     ctx.serve_start(64 << 30, max_slots=32, mode=mode)
     inflight = {}  # ticket -> (request index, volume, x index)
     lat, done, nxt, worst_res = [], 0, 0, 0.0
+    lat_vol = [[] for _ in vols]
     t0 = time.perf_counter()
     while done < n_req:
         now = time.perf_counter() - t0
@@ -466,6 +474,7 @@ def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
             if st != 0:
                 raise RuntimeError(f"request {i} finished with status {st}")
             lat.append(time.perf_counter() - t0 - arrivals[i])
+            lat_vol[v].append(lat[-1])
             worst_res = max(worst_res, info["true_rel_resid"] / tol[i])
             free[v].append(xi)
             done += 1
@@ -474,7 +483,8 @@ def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
     stats = ctx.serve_stop()
     lat = np.sort(np.array(lat))
     out = {"workload": f"{n_req} Poisson requests at {rate}/s, volumes 8^4/16^4/24^3x48/32^3x64, "
-                       "kappa U[0.10,0.122], tol {1e-8,1e-10,1e-12}, mixed FP16, budget 64 GiB",
+                       "kappa U[0.10,0.122], tol {1e-8,1e-10,1e-12}, mixed FP16, budget 64 GiB, "
+                       f"{host} host buffers",
            "p50_s": round(float(np.percentile(lat, 50)), 5),
            "p99_s": round(float(np.percentile(lat, 99)), 5),
            "mean_s": round(float(lat.mean()), 5),
@@ -483,7 +493,11 @@ def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0):
            "stable": bool(wall < arrivals[-1] + 2.0),
            "server_p50_s": round(stats["p50_s"], 5), "server_p99_s": round(stats["p99_s"], 5),
            "peak_active": stats["peak_active"], "peak_slot_bytes": stats["peak_hbm_bytes"],
-           "max_true_resid_over_tol": worst_res}
+           "max_true_resid_over_tol": worst_res,
+           "by_volume": {"x".join(map(str, d)): {
+               "n": len(lv), "p50_s": round(float(np.percentile(lv, 50)), 5) if lv else None,
+               "p99_s": round(float(np.percentile(lv, 99)), 5) if lv else None}
+               for d, lv in zip(vols, lat_vol)}}
     for g in gauges:
         g.free()
     return out
@@ -658,7 +672,8 @@ def run_gpu(args):
     staggered = bench_staggered(jqcd, synth, torch, stream, g)
     hmc = bench_hmc(ctx, jqcd, synth, np)
     batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
-    serve = bench_serve(ctx, jqcd, synth, np, args.serve_requests) if args.serve_requests > 0 else None
+    serve = (bench_serve(ctx, jqcd, synth, np, args.serve_requests, host=args.serve_host)
+             if args.serve_requests > 0 else None)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

@@ -244,8 +244,11 @@ JQCD_API jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const j
  * batch shape.  Each solve has its own kappa, tol and maxiter (params[i]);
  * all must use the same mixed mode (JQCD_CG_MIXED_F32 or _F16) and eo = 1.
  * b[i], x[i]: host canonical spinors of solve i's lattice (b copied, x
- * written before return).  infos: NULL or n entries.  Returns JQCD_OK when
- * every solve converged, else the first failing status (all infos filled). */
+ * written before return).  Page-locked (pinned) b and x are copied on a
+ * second stream: a solution goes to the host while the other solves iterate;
+ * pageable ones are copied in order on the compute stream.  infos:
+ * NULL or n entries.  Returns JQCD_OK when every solve converged, else the
+ * first failing status (all infos filled). */
 JQCD_API jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_ids,
                                          const jqcd_solve_params *params, const double *const *b,
                                          double *const *x, jqcd_solve_info *infos);
@@ -259,6 +262,9 @@ JQCD_API jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_
  * served, by HBM footprint: a request is admitted when a slot is free and the
  * device memory held by all slot buffers, plus what this request adds, stays
  * within hbm_budget_bytes (resident gauge fields are not counted).
+ * Sources and solutions move on a copy stream of their own, so with pinned
+ * (page-locked) host buffers they overlap the iterations of other requests;
+ * pageable buffers work too, copied in order on the compute stream.
  * This mode of operation has no counterpart in the paper; it serves the
  * paper's solves (solve_DinvX! with per-request kappa and eps_CG). */
 typedef struct {

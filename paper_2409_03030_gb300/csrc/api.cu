@@ -405,20 +405,32 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
   std::vector<int> done;
   jqcd_status worst = JQCD_OK;
   double t_collect = 0.0;
-  while (left > 0) {
+  auto finish_one = [&](int i) {
+    jqcd_solve_info inf;
+    E->finish(i, &inf);
+    if (infos) infos[i] = inf;
+    if (inf.status != JQCD_OK && worst == JQCD_OK) worst = inf.status;
+    --left;
+  };
+  while (E->running() > 0) {
     CK(E->run(8), "batch iterations");
     done.clear();
     CK(E->poll(&done), "batch poll");
-    for (int i : done) {
-      const auto c0 = std::chrono::steady_clock::now();
-      jqcd_solve_info inf;
-      CK(E->collect(i, x[i], &inf), "batch collect");
-      t_collect += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
-      if (infos) infos[i] = inf;
-      if (inf.status != JQCD_OK && worst == JQCD_OK) worst = inf.status;
-      --left;
-    }
+    // solutions of finished solves go to the host while the others iterate
+    const auto c0 = std::chrono::steady_clock::now();
+    for (int i : done) CK(E->collect_async(i, x[i]), "batch collect");
+    for (int i = 0; i < n; ++i)
+      if (E->drained(i)) finish_one(i);
+    t_collect += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
   }
+  const auto c0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < n; ++i)
+    if (E->collecting(i)) {
+      CK(E->wait_collect(i), "batch collect");
+      finish_one(i);
+    }
+  t_collect += std::chrono::duration<double>(std::chrono::steady_clock::now() - c0).count();
+  if (left != 0) return fail(ctx, JQCD_ECUDA, "cg_solve_batch: %d solves not collected", left);
   if (timing) {
     const auto t3 = tnow();
     auto sec = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {

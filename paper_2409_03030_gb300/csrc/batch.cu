@@ -67,6 +67,19 @@ cudaError_t SlotBuffers::ensure(int64_t vh, int hp_) {
 }
 
 // ---- engine -----------------------------------------------------------------------
+// True for page-locked (pinned or registered) host memory.  Only such buffers
+// take the copy stream: a pageable buffer is staged by the driver, which
+// blocks the calling thread and synchronises with the copy stream's queue
+// (measured: serving latencies grew 20x), so it keeps the compute stream.
+static bool page_locked(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
 BatchEngine::BatchEngine(int hp, int max_slots, cudaStream_t s, int sm_count)
     : hp_(hp), sm_count_(sm_count > 0 ? sm_count : 152), s_(s), slots_(max_slots),
       h_slots_(max_slots) {
@@ -92,11 +105,15 @@ BatchArgs BatchEngine::args() const {
 
 BatchEngine::~BatchEngine() {
   cudaStreamSynchronize(s_);
+  if (cs_) cudaStreamSynchronize(cs_);
   if (graph_) cudaGraphExecDestroy(graph_);
   for (void *p : {(void *)d_slots_, (void *)d_S_, (void *)d_groups_, (void *)d_tiles_,
                   (void *)d_ntiles_, (void *)d_lp_tiles_, (void *)d_n_lp_tiles_,
-                  (void *)d_any_update_, (void *)canon_})
+                  (void *)d_any_update_})
     if (p) cudaFree(p);
+  for (auto *v : {&ev_in_, &ev_out_, &ev_done_})
+    for (cudaEvent_t ev : *v) cudaEventDestroy(ev);
+  if (cs_) cudaStreamDestroy(cs_);
   if (h_S_) cudaFreeHost(h_S_);
 }
 
@@ -119,6 +136,11 @@ cudaError_t BatchEngine::init() {
   if (!e) e = cudaMemsetAsync(d_ntiles_, 0, sizeof(int), s_);
   if (!e) e = cudaMemsetAsync(d_any_update_, 0, sizeof(int), s_);
   if (!e) memset(h_S_, 0, sizeof(SolverScalars) * n);
+  if (!e) e = cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking);
+  for (auto *v : {&ev_in_, &ev_out_, &ev_done_}) {
+    v->assign(n, nullptr);
+    for (int i = 0; i < n && !e; ++i) e = cudaEventCreateWithFlags(&(*v)[i], cudaEventDisableTiming);
+  }
   max_groups_ = n;
   return e;
 }
@@ -167,16 +189,6 @@ int BatchEngine::running() const {
   return r;
 }
 
-cudaError_t BatchEngine::ensure_canon(int64_t vh) {
-  if (vh <= canon_vh_) return cudaSuccess;
-  if (canon_) cudaFree(canon_);
-  canon_ = nullptr;
-  canon_vh_ = 0;
-  cudaError_t e = cudaMalloc(&canon_, sizeof(double) * 2 * 12 * (size_t)(2 * vh));
-  if (!e) canon_vh_ = vh;
-  return e;
-}
-
 cudaError_t BatchEngine::admit(int slot, GaugeEntry *G, const jqcd_solve_params &P,
                                const double *b_host) {
   if (slot < 0 || slot >= (int)slots_.size() || slots_[slot].state != 0) return cudaErrorInvalidValue;
@@ -184,7 +196,6 @@ cudaError_t BatchEngine::admit(int slot, GaugeEntry *G, const jqcd_solve_params 
   const Geom &g = G->g;
   const int64_t vh = g.vh;
   cudaError_t e = H.buf.ensure(vh, hp_);
-  if (!e) e = ensure_canon(vh);
   if (e) return e;
   SlotBuffers &B = H.buf;
   SolverScalars *S = d_S_ + slot;
@@ -195,8 +206,19 @@ cudaError_t BatchEngine::admit(int slot, GaugeEntry *G, const jqcd_solve_params 
   const int nb24 = (int)blas_blocks(24 * vh), nb12 = (int)blas_blocks(12 * vh);
 #define CKE(call) do { e = (call); if (e) return e; } while (0)
   CKE(cudaMemsetAsync(S, 0, sizeof(SolverScalars), s_));
-  CKE(cudaMemcpyAsync(canon_, b_host, sizeof(double) * 24 * (size_t)(2 * vh), cudaMemcpyHostToDevice, s_));
-  CKE(launch_spinor_pack(g, PREC_DW, canon_, b_e, b_o, s_));
+  // canonical source staged in the slot's x buffer (same 384 B per site; x is
+  // zeroed below), copied on the copy stream: after any earlier copy of this
+  // slot there, and before the pack on the compute stream
+  double *stage = reinterpret_cast<double *>(B.x);
+  const size_t bytes = sizeof(double) * 24 * (size_t)(2 * vh);
+  if (page_locked(b_host)) {
+    CKE(cudaMemcpyAsync(stage, b_host, bytes, cudaMemcpyHostToDevice, cs_));
+    CKE(cudaEventRecord(ev_in_[slot], cs_));
+    CKE(cudaStreamWaitEvent(s_, ev_in_[slot], 0));
+  } else {
+    CKE(cudaMemcpyAsync(stage, b_host, bytes, cudaMemcpyHostToDevice, s_));
+  }
+  CKE(launch_spinor_pack(g, PREC_DW, stage, b_e, b_o, s_));
   CKE(launch_dw_norm2(B.b, 24 * vh, B.part, s_));
   CKE(launch_finalize_sum(B.part, nb24, &S->b2, s_));
   // bhat_e = b_e + kappa H_eo b_o; rhs = Mhat^dag bhat_e
@@ -366,6 +388,14 @@ cudaError_t BatchEngine::poll(std::vector<int> *finished) {
 }
 
 cudaError_t BatchEngine::collect(int slot, double *x_host, jqcd_solve_info *info) {
+  cudaError_t e = collect_async(slot, x_host);
+  if (!e) e = cudaEventSynchronize(ev_done_[slot]);
+  if (e) return e;
+  finish(slot, info);
+  return cudaSuccess;
+}
+
+cudaError_t BatchEngine::collect_async(int slot, double *x_host) {
   if (slot < 0 || slot >= (int)slots_.size() || slots_[slot].state != 2) return cudaErrorInvalidValue;
   SlotHost &H = slots_[slot];
   GaugeEntry *G = H.G;
@@ -386,14 +416,40 @@ cudaError_t BatchEngine::collect(int slot, double *x_host, jqcd_solve_info *info
   CKE(launch_dw_xmy_norm(B.Adw, b_e, B.wdw, 12 * vh, B.part, s_));
   CKE(launch_dw_xmy_norm(B.r, b_o, B.tdw, 12 * vh, B.part + nb12, s_));
   CKE(launch_finalize_sum(B.part, 2 * nb12, &S->full_rr, s_));
-  if (x_host) {
-    CKE(ensure_canon(vh));
-    CKE(launch_spinor_unpack(g, PREC_DW, x_e, x_o, canon_, s_));
-    CKE(cudaMemcpyAsync(x_host, canon_, sizeof(double) * 24 * (size_t)(2 * vh), cudaMemcpyDeviceToHost, s_));
+  // canonical x unpacked into the slot's b buffer (b is not read after the
+  // residual above), then both copies on the copy stream
+  double *stage = reinterpret_cast<double *>(B.b);
+  if (x_host) CKE(launch_spinor_unpack(g, PREC_DW, x_e, x_o, stage, s_));
+  // pageable x: copied on the compute stream (the copy returns when done)
+  cudaStream_t cs = (!x_host || page_locked(x_host)) ? cs_ : s_;
+  if (cs == cs_) {
+    CKE(cudaEventRecord(ev_out_[slot], s_));
+    CKE(cudaStreamWaitEvent(cs_, ev_out_[slot], 0));
   }
-  CKE(cudaMemcpyAsync(h_S_ + slot, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s_));
-  CKE(cudaStreamSynchronize(s_));
+  if (x_host)
+    CKE(cudaMemcpyAsync(x_host, stage, sizeof(double) * 24 * (size_t)(2 * vh), cudaMemcpyDeviceToHost, cs));
+  CKE(cudaMemcpyAsync(h_S_ + slot, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, cs));
+  CKE(cudaEventRecord(ev_done_[slot], cs));
 #undef CKE
+  H.state = 3;
+  return cudaSuccess;
+}
+
+bool BatchEngine::drained(int slot) const {
+  return slots_[slot].state == 3 && cudaEventQuery(ev_done_[slot]) == cudaSuccess;
+}
+
+cudaError_t BatchEngine::wait_collect(int slot) const { return cudaEventSynchronize(ev_done_[slot]); }
+
+int BatchEngine::draining() const {
+  int r = 0;
+  for (const SlotHost &s : slots_) r += s.state == 3;
+  return r;
+}
+
+void BatchEngine::finish(int slot, jqcd_solve_info *info) {
+  SlotHost &H = slots_[slot];
+  const int64_t vh = H.G->g.vh;
   const SolverScalars &Sh = h_S_[slot];
   if (info) {
     memset(info, 0, sizeof *info);
@@ -414,7 +470,6 @@ cudaError_t BatchEngine::collect(int slot, double *x_host, jqcd_solve_info *info
   H.G = nullptr;
   h_slots_[slot].active = 0;
   dirty_ = true;
-  return cudaSuccess;
 }
 
 std::string BatchEngine::tune_key() const {

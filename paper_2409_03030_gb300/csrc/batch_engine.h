@@ -31,7 +31,8 @@ struct SlotBuffers {
 };
 
 struct SlotHost {
-  int state = 0;  // 0 free, 1 iterating, 2 converged or stopped, waiting for collect
+  int state = 0;  // 0 free, 1 iterating, 2 converged or stopped, waiting for collect,
+                  // 3 result copy to the host in flight (collect_async), waiting for finish
   GaugeEntry *G = nullptr;
   jqcd_solve_params P{};
   SlotBuffers buf;
@@ -49,15 +50,31 @@ class BatchEngine {
   int running() const;
   // Prepare slot `slot` for D x = b (b: host canonical spinor).  Even-odd
   // source, normal-equation right-hand side, start residual; the slot joins
-  // the next iteration.
+  // the next iteration.  b is copied on the engine's copy stream into the
+  // slot's own buffers, so the copy overlaps the iterations of other slots,
+  // when b is page-locked; a pageable b is copied on the compute stream.
   cudaError_t admit(int slot, GaugeEntry *G, const jqcd_solve_params &P, const double *b_host);
   // Run `iters` iterations of every running slot (graph replays).
   cudaError_t run(int iters);
   // Copy the device scalars; slots that finished move to state 2.
   cudaError_t poll(std::vector<int> *finished);
   // Reconstruct x_o, compute ||b - D x||, copy x to the host, fill info and
-  // free the slot.
+  // free the slot (collect_async, then a wait for the copy, then finish).
   cudaError_t collect(int slot, double *x_host, jqcd_solve_info *info);
+  // The same without waiting: the reconstruction and residual are queued on
+  // the compute stream, the copies of x and of the slot's scalars on the copy
+  // stream (compute stream for a pageable x_host); the slot stays in state 3
+  // until finish().  x_host must stay valid and untouched until drained(slot).
+  cudaError_t collect_async(int slot, double *x_host);
+  // True once the copies queued by collect_async(slot) have completed.
+  bool drained(int slot) const;
+  // True while slot is in state 3; wait_collect blocks until it is drained.
+  bool collecting(int slot) const { return slots_[slot].state == 3; }
+  cudaError_t wait_collect(int slot) const;
+  // Fill info from the copied scalars and free the slot; slot must be drained.
+  void finish(int slot, jqcd_solve_info *info);
+  // Slots in state 3.
+  int draining() const;
   // Choose sites per tile and grid size for the current active set.
   cudaError_t autotune();
   const SolverScalars &scalars(int slot) const { return h_S_[slot]; }
@@ -78,7 +95,6 @@ class BatchEngine {
  private:
   cudaError_t rebuild();
   BatchArgs args() const;
-  cudaError_t ensure_canon(int64_t vh);
   cudaError_t ensure_graph();
   std::string tune_key() const;
 
@@ -100,8 +116,10 @@ class BatchEngine {
   int *d_any_update_ = nullptr;
   int max_groups_ = 0;
   int64_t max_tiles_ = 0;
-  double *canon_ = nullptr;
-  int64_t canon_vh_ = 0;
+  cudaStream_t cs_ = nullptr;        // host <-> device copies of sources and solutions
+  std::vector<cudaEvent_t> ev_in_;   // per slot: source copy landed (copy stream)
+  std::vector<cudaEvent_t> ev_out_;  // per slot: solution unpacked (compute stream)
+  std::vector<cudaEvent_t> ev_done_; // per slot: solution and scalars on the host
   int tile_sites_ = 128;
   int grid_ = 0;
   bool dirty_ = true;

@@ -4,8 +4,11 @@
 // One scheduler thread owns a BatchEngine on its own stream and loops:
 //   admit queued requests while a slot is free and the device memory the
 //   request needs (its slot buffers) fits the byte budget -> advance every
-//   admitted solve together by a few batched iterations -> collect the solves
-//   that finished (x written to the caller's buffer, latency recorded).
+//   admitted solve together by a few batched iterations -> queue the
+//   reconstruction of the solves that finished and the copy of x to the
+//   caller's buffer -> report the requests whose copy has completed (latency
+//   recorded).  Sources and solutions move on the engine's copy stream, so
+//   with pinned host buffers they overlap the iterations of other requests.
 // Requests that arrive while others iterate join at the next iteration
 // boundary; their work shares the same kernel launches (and, on the same
 // gauge field, the same link loads).  Admission is FIFO: a request that does
@@ -84,9 +87,12 @@ void Server::loop() {
       std::unique_lock<std::mutex> lk(mu);
       const bool idle = engine->running() == 0;
       if (idle && queue.empty()) {
-        if (stop) return;
-        cv.wait_for(lk, std::chrono::milliseconds(2));
-        continue;
+        if (engine->draining() == 0) {
+          if (stop) return;
+          cv.wait_for(lk, std::chrono::milliseconds(2));
+          continue;
+        }
+        cv.wait_for(lk, std::chrono::microseconds(200));  // results still on their way to the host
       }
       if (stop && wall() > stop_deadline) {  // drain took too long: give up
         for (auto &kv : tickets)
@@ -154,25 +160,36 @@ void Server::loop() {
     if (!e && engine->running() > 0) e = engine->run(kItersPerStep);
     finished.clear();
     if (!e) e = engine->poll(&finished);
+    // finished solves: reconstruction queued, x copied to the caller's buffer
+    // on the copy stream while the other requests keep iterating
     for (int slot : finished) {
       if (e) break;
-      uint64_t id;
       ServeTicket *T;
       {
         std::lock_guard<std::mutex> lk(mu);
-        id = slot_ticket[slot];
-        T = tickets[id].get();
+        T = tickets[slot_ticket[slot]].get();
       }
-      jqcd_solve_info inf;
-      e = engine->collect(slot, T->req.x, &inf);
-      if (e) break;
+      e = engine->collect_async(slot, T->req.x);
+    }
+    // requests whose result has reached the host are done
+    std::vector<std::pair<int, uint64_t>> drained;
+    if (!e) {
       std::lock_guard<std::mutex> lk(mu);
+      for (auto &kv : slot_ticket)
+        if (engine->drained(kv.first)) drained.push_back(kv);
+    }
+    for (auto &d : drained) {
+      if (e) break;
+      jqcd_solve_info inf;
+      engine->finish(d.first, &inf);
+      std::lock_guard<std::mutex> lk(mu);
+      ServeTicket *T = tickets[d.second].get();
       T->t_done = wall();
       inf.seconds = T->t_done - T->t_submit;
       T->info = inf;
       T->status = inf.status;
       T->state = 2;
-      slot_ticket.erase(slot);
+      slot_ticket.erase(d.first);
       latencies.push_back(T->t_done - T->t_submit);
       t_last = T->t_done;
     }
