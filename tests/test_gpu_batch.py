@@ -22,8 +22,20 @@ def jq():
     ctx.close()
 
 
-@pytest.mark.parametrize("mode", ["mixed_f16", "mixed_f32"])
-def test_batch_mixed_lattices(jq, mode):
+def host_buffer(a, pinned):
+    """a itself (pageable) or a copy in page-locked memory, which the engine
+    moves on its copy stream."""
+    if not pinned:
+        return a
+    import torch
+    t = torch.empty(a.shape, dtype=torch.complex128, pin_memory=True)
+    t.numpy()[...] = a
+    return t.numpy()
+
+
+@pytest.mark.parametrize("mode,host", [("mixed_f16", "pageable"), ("mixed_f32", "pageable"),
+                                       ("mixed_f16", "pinned"), ("mixed_f16", "mixed")])
+def test_batch_mixed_lattices(jq, mode, host):
     jqcd, ctx = jq
     d1, d2, d3 = (8, 8, 8, 8), (6, 6, 6, 10), (4, 4, 4, 4)
     U1 = synth.gauge(d1, "expi", eps=0.3, seed=1)
@@ -38,9 +50,13 @@ def test_batch_mixed_lattices(jq, mode):
                        [1e-8, 1e-10, 1e-12][s]))
     solves.append((g3, U3, d3, synth.gaussian_spinor(d3, seed=30), 0.10, 1e-12))
     solves.append((g3, U3, d3, np.zeros(synth.spinor_shape(d3), complex), 0.10, 1e-10))
-    xs, infos, st = ctx.cg_solve_batch([s[0] for s in solves], [s[3] for s in solves],
+    # pinned: sources and solutions through the copy stream; mixed: alternate
+    pin = [host == "pinned" or (host == "mixed" and i % 2 == 0) for i in range(len(solves))]
+    bs = [host_buffer(s[3], p) for s, p in zip(solves, pin)]
+    outs = [host_buffer(np.full_like(s[3], np.nan), p) for s, p in zip(solves, pin)]
+    xs, infos, st = ctx.cg_solve_batch([s[0] for s in solves], bs,
                                        [s[4] for s in solves], [s[5] for s in solves],
-                                       mode=jqcd.MODES[mode])
+                                       mode=jqcd.MODES[mode], out=outs)
     assert st == 0
     for (g, U, dims, b, k, tol), x, info in zip(solves, xs, infos):
         assert info["status"] == 0

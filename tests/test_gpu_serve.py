@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2409_03030_gb300 import synth
+from test_gpu_batch import host_buffer
 from test_gpu_parity import rel, system_residual
 
 pytestmark = pytest.mark.gpu
@@ -39,7 +40,10 @@ def wait_all(ctx, jqcd, tickets, timeout=120.0):
     return out
 
 
-def test_serve_mix_equals_alone(jq):
+@pytest.mark.parametrize("host", ["pageable", "mixed"])
+def test_serve_mix_equals_alone(jq, host):
+    """host "mixed": every other request's source and solution in page-locked
+    memory (copy stream), the rest pageable (compute stream)."""
     jqcd, ctx = jq
     lat = {"a": (8, 8, 8, 8), "b": (6, 6, 6, 10), "c": (16, 16, 16, 16)}
     U = {k: synth.gauge(d, "expi", eps=0.3, seed=40 + i) for i, (k, d) in enumerate(lat.items())}
@@ -53,7 +57,9 @@ def test_serve_mix_equals_alone(jq):
     ctx.serve_start(8 << 30, max_slots=6, mode=jqcd.CG_MIXED_F16)
     xs, tickets = [], []
     for i, (k, b, kap, tol) in enumerate(reqs):
-        x = np.zeros_like(b)
+        pin = host == "mixed" and i % 2 == 1
+        b = host_buffer(b, pin)
+        x = host_buffer(np.full_like(b, np.nan), pin)
         st, t = ctx.serve_submit(G[k], b, x, kap, tol, mode=jqcd.CG_MIXED_F16)
         assert st == 0
         xs.append(x)
