@@ -179,128 +179,11 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
   }
 }
 
-constexpr int kDwStageChunks = 21;  // 12 spinor + 9 link chunks of 16 bytes
-[[maybe_unused]] constexpr size_t kDwStagedSmem = 2ull * kDwStageChunks * kHopThreads * 16;
-
-// Issue the copies of hop d's neighbour spinor and link (in [a][b] order of
-// the matrix W the hop multiplies) into one stage, chunk-major [k][thread].
-__device__ __forceinline__ void stage_hop(float4 *st, const float4 *in, const float4 *gauge,
-                                          int64_t vh, int p, int64_t idx, int d, int64_t nb) {
-  const int mu = d >> 1;
-  const bool bwd = (d & 1) != 0;
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) cp_async16(st + k * kHopThreads + tid, in + k * vh + nb, true);
-  const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-  const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b)
-      cp_async16(st + (12 + 3 * a + b) * kHopThreads + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
-}
-
-template <bool DAG, bool AXPY, bool NORM>
-__global__ void __launch_bounds__(kHopThreads) hop_dw_staged_kernel(const HopParams P) {
-  typedef PT<PREC_DW> T;
-  extern __shared__ float4 dsm[];
-  if (P.guard && *P.guard) return;  // uniform across the grid
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const Geom &g = P.g;
-  const int64_t vh = g.vh;
-  dwacc nrm{0.f, 0.f};
-  if (idx < vh) {
-    int x, y, z, t;
-    cb_coords(g, idx, P.out_parity, x, y, z, t);
-    cw acc[4][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[a][c] = T::zero();
-    const float4 *in = reinterpret_cast<const float4 *>(P.in);
-    const float4 *gauge = reinterpret_cast<const float4 *>(P.gauge);
-    const int p = P.out_parity;
-    const int tid = threadIdx.x;
-    bool neg_next;
-    int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
-    stage_hop(dsm, in, gauge, vh, p, idx, 0, nb);
-    cp_async_commit();
-#pragma unroll 1
-    for (int d = 0; d < 8; ++d) {
-      const bool neg = neg_next;
-      if (d < 7) {
-        nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-        stage_hop(dsm + ((d + 1) & 1) * kDwStageChunks * kHopThreads, in, gauge, vh, p, idx, d + 1, nb);
-      }
-      cp_async_commit();
-      cp_async_wait1();  // this thread's copies of hop d have landed
-      const float4 *st = dsm + (d & 1) * kDwStageChunks * kHopThreads + tid;
-      const int mu = d >> 1;
-      const bool bwd = (d & 1) != 0;
-      cw psi[4][3];
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        dwc_unpack(st[k * kHopThreads], psi[k / 3][k % 3].re, psi[k / 3][k % 3].im);
-      }
-      const float S = (bwd != DAG) ? 1.f : -1.f;
-      cw h[2][3];
-      switch (mu) {
-        case 0: project_dw<0>(psi, h, S); break;
-        case 1: project_dw<1>(psi, h, S); break;
-        case 2: project_dw<2>(psi, h, S); break;
-        default: project_dw<3>(psi, h, S);
-      }
-      if (neg) T::negate_if(h, true);
-      const float cs = bwd ? -1.f : 1.f;
-      cw u[3][3];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        dw ur, ui;
-        dwc_unpack(st[(12 + k) * kHopThreads], ur, ui);
-        u[k / 3][k % 3] = cw{ur, dw_make(cs * ui.h, cs * ui.l)};
-      }
-      cw r[2][3];
-      matvec2<false>(u, h, r);
-      switch (mu) {
-        case 0: reconstruct_dw<0>(r, acc, S); break;
-        case 1: reconstruct_dw<1>(r, acc, S); break;
-        case 2: reconstruct_dw<2>(r, acc, S); break;
-        default: reconstruct_dw<3>(r, acc, S);
-      }
-    }
-    const dw b = T::scalar(P.b, P.b_split);
-    cw o[4][3];
-    if (AXPY) {
-      const dw a = T::scalar(P.a, P.a_split);
-      cw xs[4][3];
-      T::load_spinor(P.x, vh, idx, xs);
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[s][c] = T::axpby(a, xs[s][c], b, acc[s][c]);
-    } else {
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[s][c] = T::scale(b, acc[s][c]);
-    }
-    T::store_spinor(P.out, vh, idx, o);
-    if (NORM) nrm = site_norm2<PREC_DW>(o);
-  }
-  if (NORM) {
-    const double s = block_sum_dw(nrm);
-    if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
-  }
-}
-
-
 // ---------------------------------------------------------------------------
-// Double-word hop in packed two-lane arithmetic (hop_dwp.cuh): half the
-// instruction issue of the scalar kernel above, which is bound by issue and
-// not by the FP32 datapath.
-#ifndef JQCD_DW_PACKED
-#define JQCD_DW_PACKED 1
-#endif
+// Double-word hop in packed two-lane arithmetic (hop_dwp.cuh): one fma/add/
+// mul.rn.f32x2 per complex operation halves the instruction issue of a
+// scalar double-word hop, which was bound by issue rather than by the FP32
+// datapath.
 #ifndef JQCD_DWP_MIN_BLOCKS  // resident blocks per SM the register budget is cut for
 #define JQCD_DWP_MIN_BLOCKS 3
 #endif
@@ -328,19 +211,13 @@ template <bool DAG, bool AXPY, bool NORM>
 static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
   note_launch();
   static bool configured = false;  // one attribute call per instantiation
-#if JQCD_DW_PACKED
   auto kern = hop_dwp_kernel<DAG, AXPY, NORM>;
-  const size_t smem = kDwpSmem;
-#else
-  auto kern = hop_dw_staged_kernel<DAG, AXPY, NORM>;
-  const size_t smem = kDwStagedSmem;
-#endif
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<hop_blocks(P.g.vh), kHopThreads, smem, s>>>(P);
+  kern<<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P);
   return cudaGetLastError();
 }
 

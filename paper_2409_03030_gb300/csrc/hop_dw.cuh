@@ -1,6 +1,6 @@
-// Double-word hop building blocks shared by the single-field and batched
-// kernels: projection and reconstruction with runtime signs, neighbour
-// lookup, cp.async helpers, per-site norms, and a direct-load hop body.
+// Building blocks shared by the hop kernels of every precision: per-site
+// norms of a hop's output, the cp.async helpers of the staged hops, and the
+// neighbour lookup with its boundary sign.
 #pragma once
 #include "fields.cuh"
 #include "hop.cuh"
@@ -36,52 +36,9 @@ template <> __device__ __forceinline__ dwacc site_norm2<PREC_F32>(const cf (&o)[
 template <> __device__ __forceinline__ dwacc site_norm2<PREC_F16N>(const cf (&o)[4][3]) { return site_norm2_f<PREC_F16N>(o); }
 
 // ---------------------------------------------------------------------------
-// Double-word hop: one runtime loop over the eight hops.  The body
-// (projection, compensated mat-vec, reconstruction) exists once in the
-// instruction stream; the direction only selects a small
-// projection/reconstruction case and the neighbour.  A fully unrolled
-// double-word body is ~10k instructions per site and does not fit the
-// instruction caches.  Forward/backward and dagger signs ride on the FMAs of
-// the error-free additions (dw_add_sgn), so they cost nothing.
-
-// h = a + sg * phi * b with phi = 1 (I = false) or i (I = true).
-template <bool I> __device__ __forceinline__ cw cadd_ph(const cw &a, const cw &b, float sg) {
-  if (I) return cw{dw_add_sgn(a.re, b.im, -sg), dw_add_sgn(a.im, b.re, sg)};
-  return cw{dw_add_sgn(a.re, b.re, sg), dw_add_sgn(a.im, b.im, sg)};
-}
-// acc += sg * phi * r
-template <bool I> __device__ __forceinline__ void cacc_ph(cw &acc, const cw &r, float sg) {
-  if (I) { acc.re = dw_add_sgn(acc.re, r.im, -sg); acc.im = dw_add_sgn(acc.im, r.re, sg); }
-  else { acc.re = dw_add_sgn(acc.re, r.re, sg); acc.im = dw_add_sgn(acc.im, r.im, sg); }
-}
-
-// (1 + S gamma_mu) psi, rows 0 and 1, DeGrand-Rossi basis (see hop.cuh).
-template <int MU> __device__ __forceinline__ void project_dw(const cw (&psi)[4][3], cw (&h)[2][3], float S) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (MU == 0) { h[0][c] = cadd_ph<true>(psi[0][c], psi[3][c], S);   h[1][c] = cadd_ph<true>(psi[1][c], psi[2][c], S); }
-    if (MU == 1) { h[0][c] = cadd_ph<false>(psi[0][c], psi[3][c], -S); h[1][c] = cadd_ph<false>(psi[1][c], psi[2][c], S); }
-    if (MU == 2) { h[0][c] = cadd_ph<true>(psi[0][c], psi[2][c], S);   h[1][c] = cadd_ph<true>(psi[1][c], psi[3][c], -S); }
-    if (MU == 3) { h[0][c] = cadd_ph<false>(psi[0][c], psi[2][c], S);  h[1][c] = cadd_ph<false>(psi[1][c], psi[3][c], S); }
-  }
-}
-
-template <int MU> __device__ __forceinline__ void reconstruct_dw(const cw (&r)[2][3], cw (&acc)[4][3], float S) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    cacc(acc[0][c], r[0][c]);
-    cacc(acc[1][c], r[1][c]);
-    if (MU == 0) { cacc_ph<true>(acc[2][c], r[1][c], -S);  cacc_ph<true>(acc[3][c], r[0][c], -S); }
-    if (MU == 1) { cacc_ph<false>(acc[2][c], r[1][c], S);  cacc_ph<false>(acc[3][c], r[0][c], -S); }
-    if (MU == 2) { cacc_ph<true>(acc[2][c], r[0][c], -S);  cacc_ph<true>(acc[3][c], r[1][c], S); }
-    if (MU == 3) { cacc_ph<false>(acc[2][c], r[0][c], S);  cacc_ph<false>(acc[3][c], r[1][c], S); }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Double-word hop with the operands of the next hop prefetched into shared
-// memory (cp.async, two stages), so each warp's memory latency overlaps its
-// own arithmetic instead of depending on other resident warps.
+// Staged hops copy the operands of the next hop into shared memory (cp.async,
+// two stages), so each warp's memory latency overlaps its own arithmetic
+// instead of depending on other resident warps.
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool keep_l1) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   if (keep_l1)
@@ -116,59 +73,5 @@ __device__ __forceinline__ int64_t hop_neighbour(const Geom &g, int x, int y, in
   return cb_index(g, x, y, z, t);
 }
 
-
-// (H in)(x) for one output site in double-word arithmetic, one runtime loop
-// over the eight hops, operands loaded directly (read-only path for the
-// spinor, streaming for the links).  DAG selects the adjoint hop.
-template <bool DAG>
-__device__ __forceinline__ void dw_hop_site(const float4 *in, const float4 *gauge, const Geom &g,
-                                            int p, int64_t idx, cw (&acc)[4][3]) {
-  typedef PT<PREC_DW> T;
-  int x, y, z, t;
-  cb_coords(g, idx, p, x, y, z, t);
-  const int64_t vh = g.vh;
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) acc[a][c] = T::zero();
-#pragma unroll 1
-  for (int d = 0; d < 8; ++d) {
-    const int mu = d >> 1;
-    const bool bwd = (d & 1) != 0;
-    bool neg;
-    const int64_t nb = hop_neighbour(g, x, y, z, t, d, neg);
-    cw psi[4][3];
-    T::load_spinor(in, vh, nb, psi);
-    const float S = (bwd != DAG) ? 1.f : -1.f;
-    cw h[2][3];
-    switch (mu) {
-      case 0: project_dw<0>(psi, h, S); break;
-      case 1: project_dw<1>(psi, h, S); break;
-      case 2: project_dw<2>(psi, h, S); break;
-      default: project_dw<3>(psi, h, S);
-    }
-    if (neg) T::negate_if(h, true);
-    const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-    const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-    const float cs = bwd ? -1.f : 1.f;
-    cw u[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        dw ur, ui;
-        dwc_unpack(__ldcs(L + (int64_t)(a * sa + b * sb) * vh), ur, ui);
-        u[a][b] = cw{ur, dw_make(cs * ui.h, cs * ui.l)};
-      }
-    cw r[2][3];
-    matvec2<false>(u, h, r);
-    switch (mu) {
-      case 0: reconstruct_dw<0>(r, acc, S); break;
-      case 1: reconstruct_dw<1>(r, acc, S); break;
-      case 2: reconstruct_dw<2>(r, acc, S); break;
-      default: reconstruct_dw<3>(r, acc, S);
-    }
-  }
-}
 
 }  // namespace jqcd
