@@ -30,6 +30,8 @@ namespace jqcd {
 namespace {
 
 constexpr int kForceThreads = 128;
+constexpr int kForceOwnChunks = 24;  // X and Y of the thread's own site
+constexpr size_t kForceSmem = (size_t)kForceOwnChunks * kForceThreads * 16;  // 48 KB
 
 // a + phase<PH> b for complex double-word pairs (PH: 0 -> 1, 1 -> i, 2 -> -1,
 // 3 -> -i); i b = (-b.im, b.re).
@@ -114,13 +116,14 @@ struct FieldPair {
 // direction and the part are runtime values, so the heavy arithmetic exists
 // once in the instruction stream (the per-direction copies overflowed the
 // instruction cache).
+// own: this thread's column of the block's shared memory, X(x) in chunks
+// 0..11 and Y(x) in chunks 12..23 (stride kForceThreads).
 __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int x, int y, int z, int t, int mu,
-                                           const FieldPair &F, const float4 *gauge, float2 two_kappa,
-                                           float4 *out) {
+                                           const FieldPair &F, const float4 *own, const float4 *gauge,
+                                           float2 two_kappa, float4 *out) {
   const int64_t vh = g.vh;
   bool neg;
   const int64_t nb = hop_neighbour(g, x, y, z, t, 2 * mu, neg);  // x + mu, parity 1-p
-  const float4 *Xh = p ? F.xo : F.xe, *Yh = p ? F.yo : F.ye;
   const float4 *Xn = p ? F.xe : F.xo, *Yn = p ? F.ye : F.yo;
   constexpr f2 kLane0 = 0x0000000080000000ull;
   p2 M[3][3];
@@ -132,7 +135,11 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
       load_dw_spinor_p(part ? Yn : Xn, vh, nb, s4);
       if (part) adjoint_rt(mu, 1, s4, v);
       else project_rt(mu, s4, v, -1.f);
-      load_dw_spinor_p(part ? Xh : Yh, vh, cb, s4);
+      {
+        const float4 *o = own + (part ? 0 : 12) * kForceThreads;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) s4[k / 3][k % 3] = ld_p2(o + k * kForceThreads);
+      }
       if (part) project_rt(mu, s4, c, 1.f);
       else adjoint_rt(mu, -1, s4, c);
     }
@@ -176,17 +183,31 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
   }
 }
 
+// The site's own X and Y are read by all four directions: they are copied
+// once into this thread's column of shared memory (an L1-cached reload would
+// not survive the ~350 KB per SM that the neighbours and links of one
+// direction stream through).
 __global__ void __launch_bounds__(kForceThreads, 3) force_kernel(Geom g, FieldPair F,
                                                                  const float4 *__restrict__ gauge,
                                                                  float2 two_kappa, float4 *__restrict__ out) {
+  extern __shared__ float4 fsm[];  // kForceOwnChunks x kForceThreads
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 2 * g.vh) return;
   const int p = (int)(q / g.vh);
   const int64_t cb = q - (int64_t)p * g.vh;
+  const float4 *Xh = p ? F.xo : F.xe, *Yh = p ? F.yo : F.ye;
+  float4 *own = fsm + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    cp_async16(own + k * kForceThreads, Xh + k * g.vh + cb, false);
+    cp_async16(own + (12 + k) * kForceThreads, Yh + k * g.vh + cb, false);
+  }
+  cp_async_commit();
   int x, y, z, t;
   cb_coords(g, cb, p, x, y, z, t);
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // only this thread's column is read
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) force_link(g, p, cb, x, y, z, t, mu, F, gauge, two_kappa, out);
+  for (int mu = 0; mu < 4; ++mu) force_link(g, p, cb, x, y, z, t, mu, F, own, gauge, two_kappa, out);
 }
 
 // out = gamma5 in on a whole-lattice double-word spinor (chunks k = 3*spin + c;
@@ -252,7 +273,7 @@ cudaError_t launch_fermi_force(const Geom &g, const float4 *xe, const float4 *xo
                                cudaStream_t s) {
   note_launch();
   const float2 tk = dw_split_host(2.0 * kappa);
-  force_kernel<<<(unsigned)((2 * g.vh + kForceThreads - 1) / kForceThreads), kForceThreads, 0, s>>>(
+  force_kernel<<<(unsigned)((2 * g.vh + kForceThreads - 1) / kForceThreads), kForceThreads, kForceSmem, s>>>(
       g, FieldPair{xe, xo, ye, yo}, gauge_dw, tk, out);
   return cudaGetLastError();
 }
