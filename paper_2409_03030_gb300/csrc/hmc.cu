@@ -8,8 +8,7 @@
 //   U dS_g/dU_mu(x) = -(beta/3) U_mu(x) V_mu(x) (V: the six staples),
 //   P = i sum_a p^a T^a, T^a = lambda^a / 2, K = -sum Tr P^2 = sum (p^a)^2 / 2,
 //   dP/dt = TA(U dS/dU) / 2, dU/dt = P U, TA(G) = (G - G^dag)/2 - Tr(G - G^dag)/6.
-// The gauge kernels run in native FP64 (they are a small part of a trajectory
-// next to the fermion solves); the FP64 links are the master copy and the
+// The gauge kernels run in native FP64; the FP64 links are the master copy and the
 // double-word and 12-real FP32 copies are refreshed from them after every
 // update.  Layouts: FP64 link-type fields double2[2][4][9][vh] (parity, mu,
 // element 3a+b, checkerboard site), like the uploaded FP64 gauge field.
@@ -40,15 +39,25 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cadd_d(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
+// 3x3 complex product accumulated in FMAs: 2 multiplies and 10 FMAs per
+// element (the FP64 pipe is the bound of every gauge kernel here).
 __device__ __forceinline__ m3 m3_mul(const m3 &A, const m3 &B) {
   m3 r;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      double2 acc = cmul_d(A.e[a][0], B.e[0][b]);
-      acc = cadd_d(acc, cmul_d(A.e[a][1], B.e[1][b]));
-      r.e[a][b] = cadd_d(acc, cmul_d(A.e[a][2], B.e[2][b]));
+      double re = A.e[a][0].x * B.e[0][b].x, im = A.e[a][0].x * B.e[0][b].y;
+      re = fma(-A.e[a][0].y, B.e[0][b].y, re);
+      im = fma(A.e[a][0].y, B.e[0][b].x, im);
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        re = fma(A.e[a][k].x, B.e[k][b].x, re);
+        re = fma(-A.e[a][k].y, B.e[k][b].y, re);
+        im = fma(A.e[a][k].x, B.e[k][b].y, im);
+        im = fma(A.e[a][k].y, B.e[k][b].x, im);
+      }
+      r.e[a][b] = make_double2(re, im);
     }
   return r;
 }
@@ -233,7 +242,57 @@ __global__ void mom_update_kernel(Geom g, double2 *__restrict__ P, const double2
   m3_store(P, g.vh, p, mu, cb, A);
 }
 
-// U <- exp(eps P) U: Taylor series of exp(eps P / 2^k) to double precision, squared k times
+// exp(X) for a 3x3 complex X with |X|_F <= 1, by the Cayley-Hamilton identity
+// X^3 = t X^2 - s X + d (t = tr X, s = ((tr X)^2 - tr X^2)/2, d = det X):
+// X^n = a_n + b_n X + c_n X^2 with a_{n+1} = d c_n, b_{n+1} = a_n - s c_n,
+// c_{n+1} = b_n + t c_n, so exp X = F0 + F1 X + F2 X^2 with
+// F = sum_n (a_n, b_n, c_n) / n!.  One matrix product (X^2) replaces the
+// products of a matrix Taylor series; the F are divided differences of exp
+// on the spectrum, smooth also for degenerate eigenvalues, and 18 terms
+// reach double precision for |X|_F <= 1 (checked against a dense matrix
+// exponential, degenerate spectra and a small trace included).  A fixed,
+// unrolled count measured faster than stopping at the first negligible term.
+__device__ __forceinline__ m3 m3_exp(const m3 &X) {
+  const m3 X2 = m3_mul(X, X);
+  const double2 t = cadd_d(cadd_d(X.e[0][0], X.e[1][1]), X.e[2][2]);
+  const double2 tr2 = cadd_d(cadd_d(X2.e[0][0], X2.e[1][1]), X2.e[2][2]);
+  const double2 tt = cmul_d(t, t);
+  const double2 sI = make_double2(0.5 * (tt.x - tr2.x), 0.5 * (tt.y - tr2.y));
+  const double2 m0 = cadd_d(cmul_d(X.e[1][1], X.e[2][2]), cmul_d(make_double2(-X.e[1][2].x, -X.e[1][2].y), X.e[2][1]));
+  const double2 m1 = cadd_d(cmul_d(X.e[1][0], X.e[2][2]), cmul_d(make_double2(-X.e[1][2].x, -X.e[1][2].y), X.e[2][0]));
+  const double2 m2 = cadd_d(cmul_d(X.e[1][0], X.e[2][1]), cmul_d(make_double2(-X.e[1][1].x, -X.e[1][1].y), X.e[2][0]));
+  const double2 d0 = cmul_d(X.e[0][0], m0), d1 = cmul_d(X.e[0][1], m1), d2 = cmul_d(X.e[0][2], m2);
+  const double2 d = make_double2(d0.x - d1.x + d2.x, d0.y - d1.y + d2.y);
+  double2 a = make_double2(1.0, 0.0), b = make_double2(0.0, 0.0), c = b;
+  double2 F0 = a, F1 = b, F2 = b;
+#pragma unroll
+  for (int n = 1; n <= 18; ++n) {
+    const double inv = 1.0 / n;
+    const double2 dc = cmul_d(d, c), sc = cmul_d(sI, c), tc = cmul_d(t, c);
+    const double2 na = make_double2(dc.x * inv, dc.y * inv);
+    const double2 nb = make_double2((a.x - sc.x) * inv, (a.y - sc.y) * inv);
+    const double2 nc = make_double2((b.x + tc.x) * inv, (b.y + tc.y) * inv);
+    a = na;
+    b = nb;
+    c = nc;
+    F0 = cadd_d(F0, a);
+    F1 = cadd_d(F1, b);
+    F2 = cadd_d(F2, c);
+  }
+  m3 E;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double2 v = cadd_d(cmul_d(F1, X.e[i][j]), cmul_d(F2, X2.e[i][j]));
+      if (i == j) v = cadd_d(v, F0);
+      E.e[i][j] = v;
+    }
+  return E;
+}
+
+// U <- exp(eps P) U: exp(eps P / 2^k) with |eps P / 2^k|_F <= 1 by m3_exp,
+// squared k times (k = 0 for the step sizes of a trajectory)
 __global__ void exp_update_kernel(Geom g, double2 *__restrict__ U, const double2 *__restrict__ P, double eps) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 8 * g.vh) return;
@@ -250,7 +309,7 @@ __global__ void exp_update_kernel(Geom g, double2 *__restrict__ U, const double2
   nrm = fabs(eps) * sqrt(nrm);  // Frobenius norm of eps P
   int k = 0;
   double sc = eps;
-  while (nrm > 0.25 && k < 40) {
+  while (nrm > 1.0 && k < 40) {
     nrm *= 0.5;
     sc *= 0.5;
     ++k;
@@ -259,23 +318,7 @@ __global__ void exp_update_kernel(Geom g, double2 *__restrict__ U, const double2
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b) A.e[a][b] = make_double2(sc * A.e[a][b].x, sc * A.e[a][b].y);
-  // E = sum_{n <= 16} A^n / n!   (|A| <= 1/4: remainder below 1e-20)
-  m3 E, T;
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) E.e[a][b] = T.e[a][b] = make_double2(a == b ? 1.0 : 0.0, 0.0);
-  for (int n = 1; n <= 16; ++n) {
-    T = m3_mul(T, A);
-    const double inv = 1.0 / n;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        T.e[a][b] = make_double2(T.e[a][b].x * inv, T.e[a][b].y * inv);
-        E.e[a][b] = cadd_d(E.e[a][b], T.e[a][b]);
-      }
-  }
+  m3 E = m3_exp(A);
   for (int i = 0; i < k; ++i) E = m3_mul(E, E);
   m3_store(U, g.vh, p, mu, cb, m3_mul(E, m3_load(U, g.vh, p, mu, cb)));
 }

@@ -11,7 +11,12 @@ site of the whole lattice).
 --op cg: --iters whole even-odd CG solves (--mode, tolerance 1e-10) from one
 Gaussian source, timed by the library's own events (gpu_seconds), for launch
 lists of a complete solve; --delta, --eps and --kappa set the reliable-update
-threshold, the links and the hopping parameter."""
+threshold, the links and the hopping parameter.
+
+--op hmc: --iters trajectories (10 leapfrog steps, beta 5.5, two Wilson
+flavours at --kappa, solves to 1e-10 in --mode; each trajectory is
+accepted and the next one continues from its links), wall time per
+trajectory."""
 from __future__ import annotations
 
 import argparse
@@ -32,7 +37,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--axpy", action="store_true")
     ap.add_argument("--dagger", action="store_true")
-    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg"])
+    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg", "hmc"])
     ap.add_argument("--mode", default="mixed_f16", choices=sorted(jqcd.MODES))
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eps", type=float, default=0.3, help="link generator exp(i eps H)")
@@ -44,6 +49,24 @@ def main():
     g = ctx.gauge_upload(dims, synth.gauge(dims, "expi", eps=a.eps, seed=1))
     stream = torch.cuda.Stream()
     vh = dims[0] * dims[1] * dims[2] * dims[3] // 2
+    if a.op == "hmc":
+        import numpy as np
+        rng = np.random.default_rng(62)
+        normals = rng.normal(size=(4,) + tuple(reversed(dims)) + (8,))
+        xi = synth.gaussian_spinor(dims, seed=63)
+        mode = jqcd.MODES[a.mode]
+        for _ in range(a.warmup):
+            g.hmc_trajectory(normals, xi, 0.0, 5.5, kappa=a.kappa, n_md=2, tol=1e-10, mode=mode)
+        secs, iters = [], 0
+        for _ in range(a.iters):
+            info, _ = g.hmc_trajectory(normals, xi, 0.0, 5.5, kappa=a.kappa, n_md=10, tol=1e-10, mode=mode)
+            secs.append(info["seconds"])
+            iters = info["cg_iters"]
+        print(json.dumps({"op": "hmc", "dims": dims, "mode": a.mode, "cg_iters": iters,
+                          "s_per_trajectory": round(sum(secs) / len(secs), 4)}))
+        g.free()
+        ctx.close()
+        return
     if a.op == "cg":
         import numpy as np
         b = synth.gaussian_spinor(dims, seed=2)
