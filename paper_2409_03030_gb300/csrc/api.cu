@@ -576,15 +576,20 @@ void add_info(jqcd_solve_info *acc, const jqcd_solve_info &s) {
 // X = (D^dag D)^{-1} eta into G->fX and Y = (D^dag)^{-1} eta into G->fY for the
 // double-word eta in G->feta, by two solves of D z = c:
 // Y = gamma5 D^{-1} gamma5 eta, X = D^{-1} Y.  Then S = Re <eta, X>.
+// Start vectors (bit mask `warm`): 1 -- D x = gamma5 eta starts from
+// gamma5 fY (the previous Y, or xi itself when fY still holds the heat-bath
+// xi with eta = D^dag xi: then gamma5 xi is the exact solution on the
+// unmoved links); 2 -- D x = Y starts from fX, the previous X.
 jqcd_status fermi_solves(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params &params,
-                         jqcd_solve_info *inf, double *action) {
+                         jqcd_solve_info *inf, double *action, int warm = 0) {
   cudaStream_t s = ctx->stream;
   const int64_t vh = G->g.vh;
   jqcd_solve_params P = params;
-  P.use_x0 = 0;
+  P.use_x0 = (warm & 1) ? 1 : 0;
   std::string msg;
   jqcd_solve_info one;
   CK(launch_gamma5_dw(G->vb, G->feta, vh, s), "gamma5");
+  if (warm & 1) CK(launch_gamma5_dw(G->vsol, G->fY, vh, s), "start vector");
   memset(&one, 0, sizeof one);
   jqcd_status st = solve_resident(*G, P, s, &one, &msg);
   add_info(inf, one);
@@ -594,6 +599,8 @@ jqcd_status fermi_solves(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params &
   }
   CK(launch_gamma5_dw(G->fY, G->vsol, vh, s), "gamma5");
   CK(launch_dw_copy(G->vb, G->fY, 24 * vh, s), "copy");
+  P.use_x0 = (warm & 2) ? 1 : 0;
+  if (warm & 2) CK(launch_dw_copy(G->vsol, G->fX, 24 * vh, s), "start vector");
   memset(&one, 0, sizeof one);
   st = solve_resident(*G, P, s, &one, &msg);
   add_info(inf, one);
@@ -1027,7 +1034,9 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
     if (hp->fermions) {
       jqcd_solve_info fi;
       memset(&fi, 0, sizeof fi);
-      st = fermi_solves(ctx, G, sp, &fi, nullptr);
+      // links moved by O(dt) since the previous solves: warm starts (the
+      // first step's second solve has no previous X and starts from 0)
+      st = fermi_solves(ctx, G, sp, &fi, nullptr, step == 0 ? 1 : 3);
       add_info(&inf, fi);
       if (st != JQCD_OK) break;
       CK(launch_fermi_force(G->g, G->fX, G->fX + nh, G->fY, G->fY + nh, (const float4 *)G->gauge_dw, hp->kappa,
@@ -1041,7 +1050,7 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
     if (hp->fermions) {
       jqcd_solve_info fi;
       memset(&fi, 0, sizeof fi);
-      st = fermi_solves(ctx, G, sp, &fi, &S_f);
+      st = fermi_solves(ctx, G, sp, &fi, &S_f, hp->n_md > 0 ? 3 : 1);
       add_info(&inf, fi);
     }
   }
