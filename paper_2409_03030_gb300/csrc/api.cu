@@ -576,20 +576,20 @@ void add_info(jqcd_solve_info *acc, const jqcd_solve_info &s) {
 // X = (D^dag D)^{-1} eta into G->fX and Y = (D^dag)^{-1} eta into G->fY for the
 // double-word eta in G->feta, by two solves of D z = c:
 // Y = gamma5 D^{-1} gamma5 eta, X = D^{-1} Y.  Then S = Re <eta, X>.
-// Start vectors (bit mask `warm`): 1 -- D x = gamma5 eta starts from
-// gamma5 fY (the previous Y, or xi itself when fY still holds the heat-bath
-// xi with eta = D^dag xi: then gamma5 xi is the exact solution on the
-// unmoved links); 2 -- D x = Y starts from fX, the previous X.
+// start1, start2: null (start from 0) or whole-lattice double-word start
+// vectors of D x = gamma5 eta and of D x = Y (read before either is
+// overwritten; they may be fX or fY).
 jqcd_status fermi_solves(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params &params,
-                         jqcd_solve_info *inf, double *action, int warm = 0) {
+                         jqcd_solve_info *inf, double *action, const float4 *start1 = nullptr,
+                         const float4 *start2 = nullptr) {
   cudaStream_t s = ctx->stream;
   const int64_t vh = G->g.vh;
   jqcd_solve_params P = params;
-  P.use_x0 = (warm & 1) ? 1 : 0;
+  P.use_x0 = start1 ? 1 : 0;
   std::string msg;
   jqcd_solve_info one;
   CK(launch_gamma5_dw(G->vb, G->feta, vh, s), "gamma5");
-  if (warm & 1) CK(launch_gamma5_dw(G->vsol, G->fY, vh, s), "start vector");
+  if (start1) CK(launch_dw_copy(G->vsol, start1, 24 * vh, s), "start vector");
   memset(&one, 0, sizeof one);
   jqcd_status st = solve_resident(*G, P, s, &one, &msg);
   add_info(inf, one);
@@ -599,8 +599,8 @@ jqcd_status fermi_solves(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params &
   }
   CK(launch_gamma5_dw(G->fY, G->vsol, vh, s), "gamma5");
   CK(launch_dw_copy(G->vb, G->fY, 24 * vh, s), "copy");
-  P.use_x0 = (warm & 2) ? 1 : 0;
-  if (warm & 2) CK(launch_dw_copy(G->vsol, G->fX, 24 * vh, s), "start vector");
+  P.use_x0 = start2 ? 1 : 0;
+  if (start2) CK(launch_dw_copy(G->vsol, start2, 24 * vh, s), "start vector");
   memset(&one, 0, sizeof one);
   st = solve_resident(*G, P, s, &one, &msg);
   add_info(inf, one);
@@ -989,6 +989,7 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
   const int64_t V = 2 * G->g.vh, nh = 12 * G->g.vh;
   CK(G->ensure_hmc(), "hmc workspace alloc");
   if (hp->fermions) CK(G->ensure_force(), "force workspace alloc");
+  if (hp->fermions) CK(G->ensure_hmc_history(), "solve history alloc");
   const size_t lf = (size_t)72 * 16 * G->g.vh;
   jqcd_solve_params sp;
   memset(&sp, 0, sizeof sp);
@@ -1026,6 +1027,32 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
   CK(hmc_kinetic(*G, &K, s), "kinetic");
   CK(hmc_plaquette_sum(*G, &plaq, s), "plaquette");
   out.H_old = K - hp->beta / 3.0 * plaq + S_f;
+  // Start vectors of the fermion solves (chronological): the solutions X(t),
+  // Y(t) at the force times t_k = (k + 1/2) dt are smooth in t, so step k
+  // starts from the linear extrapolation 2 x_{k-1} - x_{k-2} (error O(dt^2)),
+  // step 1 from x_0, step 0's first solve from gamma5 xi (exact at t = 0:
+  // eta = D^dag xi) and its second from 0.  hS1 holds gamma5 of Y's start.
+  const int64_t nfull = 24 * G->g.vh;
+  int nhist = 0;  // force-time solutions available (fX, fY newest; hXp, hYp before)
+  auto starts = [&](double ahead, const float4 **s1, const float4 **s2) -> cudaError_t {
+    // ahead: distance to the next solve time in units of dt
+    cudaError_t e = cudaSuccess;
+    if (nhist >= 2) {
+      e = launch_dw_lincomb(G->hS1, G->fY, G->hYp, 1.0 + ahead, -ahead, nfull, s);
+      if (!e) e = launch_dw_lincomb(G->hS2, G->fX, G->hXp, 1.0 + ahead, -ahead, nfull, s);
+      *s2 = G->hS2;
+    } else {
+      e = launch_dw_copy(G->hS1, G->fY, nfull, s);  // Y_0, or xi before the first solves
+      *s2 = nhist == 1 ? G->hS2 : nullptr;
+      if (!e && nhist == 1) e = launch_dw_copy(G->hS2, G->fX, nfull, s);
+    }
+    if (!e) e = launch_gamma5_dw(G->hS1, G->hS1, G->g.vh, s);
+    *s1 = G->hS1;
+    // the newest solutions become the history before the solves replace them
+    if (!e && nhist >= 1) e = launch_dw_copy(G->hYp, G->fY, nfull, s);
+    if (!e && nhist >= 1) e = launch_dw_copy(G->hXp, G->fX, nfull, s);
+    return e;
+  };
   // leapfrog
   const double dt = hp->tau / hp->n_md;
   for (int step = 0; step < hp->n_md; ++step) {
@@ -1034,9 +1061,10 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
     if (hp->fermions) {
       jqcd_solve_info fi;
       memset(&fi, 0, sizeof fi);
-      // links moved by O(dt) since the previous solves: warm starts (the
-      // first step's second solve has no previous X and starts from 0)
-      st = fermi_solves(ctx, G, sp, &fi, nullptr, step == 0 ? 1 : 3);
+      const float4 *s1 = nullptr, *s2 = nullptr;
+      CK(starts(1.0, &s1, &s2), "start vectors");
+      st = fermi_solves(ctx, G, sp, &fi, nullptr, s1, s2);
+      ++nhist;
       add_info(&inf, fi);
       if (st != JQCD_OK) break;
       CK(launch_fermi_force(G->g, G->fX, G->fX + nh, G->fY, G->fY + nh, (const float4 *)G->gauge_dw, hp->kappa,
@@ -1050,7 +1078,9 @@ jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc
     if (hp->fermions) {
       jqcd_solve_info fi;
       memset(&fi, 0, sizeof fi);
-      st = fermi_solves(ctx, G, sp, &fi, &S_f, hp->n_md > 0 ? 3 : 1);
+      const float4 *s1 = nullptr, *s2 = nullptr;
+      CK(starts(0.5, &s1, &s2), "start vectors");  // t = tau, half a step after the last force
+      st = fermi_solves(ctx, G, sp, &fi, &S_f, s1, s2);
       add_info(&inf, fi);
     }
   }

@@ -371,6 +371,27 @@ unsigned site_blocks2(int64_t vh) { return (unsigned)((2 * vh + kHmcThreads - 1)
 
 }  // namespace
 
+// out = a x + b y over n double-word complex numbers (a, b real, given as
+// (hi, lo) float pairs); out may alias x or y.
+__global__ void dw_lincomb_kernel(float4 *out, const float4 *x, const float4 *y, float2 a, float2 b, int64_t n) {
+  const dw A = dw_make(a.x, a.y), B = dw_make(b.x, b.y);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    dw xr, xi, yr, yi;
+    dwc_unpack(x[i], xr, xi);
+    dwc_unpack(y[i], yr, yi);
+    out[i] = dwc_pack(dw_add(dw_mul(A, xr), dw_mul(B, yr)), dw_add(dw_mul(A, xi), dw_mul(B, yi)));
+  }
+}
+
+cudaError_t launch_dw_lincomb(float4 *out, const float4 *x, const float4 *y, double a, double b, int64_t n,
+                              cudaStream_t s) {
+  const float ah = (float)a, bh = (float)b;
+  note_launch();
+  dw_lincomb_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(
+      out, x, y, make_float2(ah, (float)(a - (double)ah)), make_float2(bh, (float)(b - (double)bh)), n);
+  return cudaGetLastError();
+}
+
 cudaError_t GaugeEntry::ensure_hmc() {
   cudaError_t e = ensure_reduce();
   const size_t lf = (size_t)72 * 16 * g.vh;  // FP64 link field, double2[2][4][9][vh]
@@ -379,6 +400,15 @@ cudaError_t GaugeEntry::ensure_hmc() {
     if (e == cudaSuccess && !*v) e = alloc_t(v, lf);
   if (e == cudaSuccess && !hNormals) e = alloc_t(&hNormals, sizeof(double) * 8 * 4 * (size_t)(2 * g.vh));
   if (e == cudaSuccess && !hPart) e = alloc_t(&hPart, sizeof(double) * (link_blocks(g.vh) + 2));
+  return e;
+}
+
+cudaError_t GaugeEntry::ensure_hmc_history() {
+  cudaError_t e = cudaSuccess;
+  const size_t full = 2 * spinor_parity_bytes(PREC_DW, g.vh);
+  float4 **vs[] = {&hXp, &hYp, &hS1, &hS2};
+  for (float4 **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc_t(v, full);
   return e;
 }
 

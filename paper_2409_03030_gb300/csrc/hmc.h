@@ -22,5 +22,8 @@ cudaError_t hmc_gauge_force(GaugeEntry &G, double beta, cudaStream_t s);
 cudaError_t hmc_momenta_update(GaugeEntry &G, const float4 *Gf, double coef, cudaStream_t s);
 // U <- exp(eps P) U and refresh of the link copies
 cudaError_t hmc_links_update(GaugeEntry &G, double eps, cudaStream_t s);
+// out = a x + b y over n double-word complex numbers (out may alias x or y)
+cudaError_t launch_dw_lincomb(float4 *out, const float4 *x, const float4 *y, double a, double b, int64_t n,
+                              cudaStream_t s);
 
 }  // namespace jqcd

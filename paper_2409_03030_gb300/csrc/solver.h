@@ -70,6 +70,9 @@ struct GaugeEntry {
   cudaError_t ensure_multishift(int nshift);
   cudaError_t ensure_staggered();
   cudaError_t ensure_hmc();
+  // fermion-solve history of a trajectory: previous X, Y and two start vectors
+  float4 *hXp = nullptr, *hYp = nullptr, *hS1 = nullptr, *hS2 = nullptr;
+  cudaError_t ensure_hmc_history();
   size_t linkfield_bytes() const { return (size_t)72 * 16 * g.vh; }  // [2][4][9][vh] float4
   size_t link_canon_bytes() const { return sizeof(double) * 2 * 9 * 4 * (size_t)(2 * g.vh); }
   int n_partials() const;
