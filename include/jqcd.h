@@ -431,9 +431,10 @@ typedef struct {
   int32_t n_md;      /* leapfrog steps (paper: MDsteps = 10) */
   int32_t fermions;  /* 1: two-flavour Wilson fermions; 0: pure gauge */
   int32_t mode;      /* CG mode of the fermion solves (JQCD_CG_DW, _MIXED_F32, _MIXED_F16) */
-  int32_t maxiter;   /* per fermion solve; the solves start from the previous solution on
-                        the same pseudofermion (the first from gamma5 xi), since the links
-                        move by O(tau / n_md) in between, and stop at tol like a cold start */
+  int32_t maxiter;   /* per fermion solve; the solves start from the linear extrapolation
+                        of the previous two solutions on the same pseudofermion (the first
+                        from gamma5 xi), since the links move by O(tau / n_md) in between,
+                        and stop at tol like a cold start */
 } jqcd_hmc_params;
 typedef struct {
   double H_old, H_new, dH;
