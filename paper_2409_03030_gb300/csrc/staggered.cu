@@ -35,6 +35,56 @@ __device__ __forceinline__ float stag_eta(int mu, int x, int y, int z) {
   return (s & 1) ? -1.f : 1.f;
 }
 
+// acc = sum over the 8 hops of eta_mu(x) * (+U_mu(x) in(x+mu) or -U_mu(x-mu)^dag in(x-mu)),
+// with the boundary sign (DAG: negated), at output site cb of parity p.
+template <bool DAG>
+__device__ __forceinline__ void stag_hop_sum(const Geom &g, int p, int64_t cb, const float4 *__restrict__ in,
+                                             const float4 *__restrict__ gauge, p2 (&acc)[3]) {
+  const int64_t vh = g.vh;
+  int x, y, z, t;
+  cb_coords(g, cb, p, x, y, z, t);
+  acc[0] = acc[1] = acc[2] = p2{0ull, 0ull};
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool bwd = (d & 1) != 0;
+    bool neg;
+    const int64_t nb = hop_neighbour(g, x, y, z, t, d, neg);
+    // link: forward U_mu(x); backward U_mu(x-mu)^dag (transposed here, conjugated below)
+    const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(gauge) +
+                          (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : cb);
+    const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
+    p2 W[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const ulonglong2 v = __ldcs(L + (int64_t)(a * sa + b * sb) * vh);
+        W[a][b] = p2{v.x, v.y};
+      }
+    p2 h[3];
+    const ulonglong2 *P = reinterpret_cast<const ulonglong2 *>(in) + nb;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const ulonglong2 v = __ldg(P + c * vh);
+      h[c] = p2{v.x, v.y};
+    }
+    if (bwd) {
+      const f2 cc = f2_make(1.f, -1.f);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
+    }
+    p2 r[3];
+    matvec_half_p(W, h, r);
+    // sign: eta, boundary, +forward / -backward, and -1 for the adjoint
+    float sg = stag_eta(mu, x, y, z) * (neg ? -1.f : 1.f) * (bwd ? -1.f : 1.f);
+    if (DAG) sg = -sg;
+    const f2 sv = f2_make(sg, sg);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) acc[c] = p2_add_sgn(acc[c], r[c], sv);
+  }
+}
+
 // out_p = a x_p + b D_hop(p <- 1-p) in   (DAG: D_hop^dag = -D_hop)
 template <bool DAG, bool AXPY, bool NORM>
 __global__ void __launch_bounds__(kStagThreads) stag_hop_kernel(Geom g, int p, const float4 *__restrict__ in,
@@ -48,48 +98,8 @@ __global__ void __launch_bounds__(kStagThreads) stag_hop_kernel(Geom g, int p, c
   const int64_t vh = g.vh;
   dwacc nrm{0.f, 0.f};
   if (cb < vh) {
-    int x, y, z, t;
-    cb_coords(g, cb, p, x, y, z, t);
-    p2 acc[3] = {p2{0ull, 0ull}, p2{0ull, 0ull}, p2{0ull, 0ull}};
-#pragma unroll 1
-    for (int d = 0; d < 8; ++d) {
-      const int mu = d >> 1;
-      const bool bwd = (d & 1) != 0;
-      bool neg;
-      const int64_t nb = hop_neighbour(g, x, y, z, t, d, neg);
-      // link: forward U_mu(x); backward U_mu(x-mu)^dag (transposed here, conjugated below)
-      const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(gauge) +
-                            (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : cb);
-      const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-      p2 W[3][3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const ulonglong2 v = __ldcs(L + (int64_t)(a * sa + b * sb) * vh);
-          W[a][b] = p2{v.x, v.y};
-        }
-      p2 h[3];
-      const ulonglong2 *P = reinterpret_cast<const ulonglong2 *>(in) + nb;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const ulonglong2 v = __ldg(P + c * vh);
-        h[c] = p2{v.x, v.y};
-      }
-      if (bwd) {
-        const f2 cc = f2_make(1.f, -1.f);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
-      }
-      p2 r[3];
-      matvec_half_p(W, h, r);
-      // sign: eta, boundary, +forward / -backward, and -1 for the adjoint
-      float sg = stag_eta(mu, x, y, z) * (neg ? -1.f : 1.f) * (bwd ? -1.f : 1.f);
-      if (DAG) sg = -sg;
-      const f2 sv = f2_make(sg, sg);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[c] = p2_add_sgn(acc[c], r[c], sv);
-    }
+    p2 acc[3];
+    stag_hop_sum<DAG>(g, p, cb, in, gauge, acc);
     // out = a x + (b / 2) acc  (the 1/2 is exact)
     const f2 bh = f2_make(0.5f * b_split.x, 0.5f * b_split.x);
     const mul2 Bm{bh, f2_make(0.5f * b_split.y, 0.5f * b_split.y)};
@@ -174,6 +184,103 @@ __global__ void stag_unpack_kernel(Geom g, const float4 *even, const float4 *odd
   for (int c = 0; c < 3; ++c) {
     const float4 v = base[c * g.vh + cb];
     dst[c] = make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
+}
+
+// Second hop of the even-odd CG on m^2 - D_eo D_oe fused with the update:
+// Ap = a p + (b/2) H t at the site in registers (a = m^2, b = -1), then
+// x += alpha p, r -= alpha Ap and the block partial of ||r||^2; Ap is never
+// stored.
+__global__ void __launch_bounds__(kStagThreads)
+    stag_hop_cg_kernel(Geom g, const float4 *__restrict__ t, const float4 *__restrict__ pv,
+                       float4 *__restrict__ xs, float4 *__restrict__ r, const float4 *__restrict__ gauge,
+                       float2 a_split, float2 b_split, const SolverScalars *__restrict__ S, double *partials) {
+  if (S->halt) return;  // uniform across the grid
+  const int64_t cb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t vh = g.vh;
+  dwacc nrm{0.f, 0.f};
+  if (cb < vh) {
+    p2 acc[3];
+    stag_hop_sum<false>(g, 0, cb, t, gauge, acc);
+    const mul2 Bm{f2_make(0.5f * b_split.x, 0.5f * b_split.x), f2_make(0.5f * b_split.y, 0.5f * b_split.y)};
+    const mul2 Am{f2_make(a_split.x, a_split.x), f2_make(a_split.y, a_split.y)};
+    const float2 al = S->alpha_dw;
+    const mul2 Al{f2_make(al.x, al.x), f2_make(al.y, al.y)};
+    const mul2 Ml{f2_neg(Al.h), f2_neg(Al.l)};
+    const ulonglong2 *P = reinterpret_cast<const ulonglong2 *>(pv) + cb;
+    ulonglong2 *X = reinterpret_cast<ulonglong2 *>(xs) + cb;
+    ulonglong2 *R = reinterpret_cast<ulonglong2 *>(r) + cb;
+    acc2 nq{0ull, 0ull};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const ulonglong2 pw = __ldg(P + c * vh), xw = X[c * vh], rw = R[c * vh];
+      const p2 pc{pw.x, pw.y};
+      acc2 Q = acc2_first(Bm, p2_norm(acc[c]));
+      acc2_mad(Q, Am, pc);
+      const p2 q = p2_norm(acc2_get(Q));
+      const p2 xn = p2_norm(p2_add(p2{xw.x, xw.y}, acc2_get(acc2_first(Al, pc))));
+      const p2 rn = p2_norm(p2_add(p2{rw.x, rw.y}, acc2_get(acc2_first(Ml, q))));
+      X[c * vh] = make_ulonglong2(xn.h, xn.l);
+      R[c * vh] = make_ulonglong2(rn.h, rn.l);
+      const mul2 Rm{rn.h, rn.l};
+      if (c == 0) nq = acc2_first(Rm, rn);
+      else acc2_mad(nq, Rm, rn);
+    }
+    float s0, s1, c0, c1;
+    f2_split(nq.s, s0, s1);
+    f2_split(nq.c, c0, c1);
+    float sum, e;
+    two_sum(s0, s1, sum, e);
+    nrm = dwacc{sum, __fadd_rn(__fadd_rn(c0, c1), e)};
+  }
+  const double bs = block_sum_dw(nrm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+// p = r + beta p (beta = S->beta_dw) with the block partial of ||p||^2.
+__global__ void stag_xpay_norm_kernel(float4 *__restrict__ p, const float4 *__restrict__ r, int64_t n,
+                                      const SolverScalars *S, double *partials) {
+  if (S->halt) return;  // uniform across the grid
+  const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
+  dwacc A{0.f, 0.f};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    dw p_r, p_i, r_r, r_i;
+    dwc_unpack(p[i], p_r, p_i);
+    dwc_unpack(r[i], r_r, r_i);
+    const dw nr = dw_add(r_r, dw_mul(be, p_r)), ni = dw_add(r_i, dw_mul(be, p_i));
+    p[i] = dwc_pack(nr, ni);
+    acc_sq(A, nr);
+    acc_sq(A, ni);
+  }
+  const double bs = block_sum_dw(A);
+  if (threadIdx.x == 0) partials[blockIdx.x] = bs;
+}
+
+// alpha = ||r||^2 / <p, (m^2 - D_eo D_oe) p> with <p, A p> = m^2 ||p||^2 + ||D_oe p||^2
+// (D_eo^dag = -D_oe): the two norms come as per-block partials of the first
+// hop (pt) and of the p update (pp); breakdown when the sum is not positive.
+__global__ void stag_alpha_kernel(const double *pt, int nt, const double *pp, int np, double m2,
+                                  SolverScalars *S) {
+  if (S->halt) return;
+  double vt = 0.0, vp = 0.0;
+  for (int i = threadIdx.x; i < nt; i += blockDim.x) vt += pt[i];
+  for (int i = threadIdx.x; i < np; i += blockDim.x) vp += pp[i];
+  vt = block_sum_d(vt);
+  vp = block_sum_d(vp);
+  if (threadIdx.x == 0) {
+    const double pAp = m2 * vp + vt;
+    S->pAp = pAp;
+    if (!(pAp > 0.0) || !isfinite(pAp)) {
+      S->done = 2;
+      S->halt = 1;
+      return;
+    }
+    const double a = S->rr / pAp;
+    S->alpha = a;
+    S->alpha_dw = split_dev2(a);
+    S->malpha_dw = split_dev2(-a);
+    S->alpha_f = (float)a;
+    S->malpha_f = (float)-a;
   }
 }
 
@@ -267,6 +374,11 @@ jqcd_status solve_staggered(GaugeEntry &G, double mass, const jqcd_solve_params 
   CKT(launch_dw_norm2(r, n, G.partials, s));
   CKT(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, 0.0, s));
   CKT(launch_dw_copy(p, r, n, s));
+  // partials: ||t||^2 and ||r||^2 per hop block from the start, ||p||^2 per
+  // vector block after them
+  const int nstag = (int)stag_blocks(vh);
+  double *part_t = G.partials, *part_p = G.partials + nstag;
+  CKT(launch_dw_norm2(p, n, part_p, s));
   long long hops = 1;
   int restarts = 0;
   jqcd_status st = JQCD_OK;
@@ -279,12 +391,19 @@ jqcd_status solve_staggered(GaugeEntry &G, double mass, const jqcd_solve_params 
   for (;;) {
     for (;;) {
       for (int k = 0; k < 8; ++k) {
-        CKT(apply(p, Ap, &S->halt));
-        CKT(launch_dw_dot_re(p, Ap, n, G.partials, nblas, s, &S->halt));
-        CKT(launch_cg_alpha(G.partials, nblas, S, s));
-        CKT(launch_dw_cg_update(xe, r, p, Ap, n, S, G.partials, s));
-        CKT(launch_cg_beta(G.partials, nblas, S, s));
-        CKT(launch_dw_xpay(p, r, n, S, s));
+        // t = D_oe p with ||t||^2; alpha from m^2 ||p||^2 + ||t||^2; the second
+        // hop applies the update and forms ||r||^2; beta; p = r + beta p, ||p||^2
+        CKT(launch_stag_hop(G.g, 1, false, p, nullptr, t, U, 0.0, 1.0, part_t, s, &S->halt));
+        note_launch();
+        stag_alpha_kernel<<<1, kReduceThreads, 0, s>>>(part_t, nstag, part_p, nblas, m2, S);
+        note_launch();
+        stag_hop_cg_kernel<<<nstag, kStagThreads, 0, s>>>(G.g, t, p, xe, r, U, dw_split_host(m2),
+                                                          dw_split_host(-1.0), S, part_t);
+        CKT(cudaGetLastError());
+        CKT(launch_cg_beta(part_t, nstag, S, s));
+        note_launch();
+        stag_xpay_norm_kernel<<<nblas, kBlasThreads, 0, s>>>(p, r, n, S, part_p);
+        CKT(cudaGetLastError());
       }
       CKT(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
       CKT(cudaStreamSynchronize(s));
@@ -311,6 +430,7 @@ jqcd_status solve_staggered(GaugeEntry &G, double mass, const jqcd_solve_params 
     ++restarts;
     CKT(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, 0.0, s));
     CKT(launch_dw_copy(p, r, n, s));
+    CKT(launch_dw_norm2(p, n, part_p, s));
   }
   // x_o = (b_o - D_oe x_e) / m
   CKT(launch_stag_hop(G.g, 1, false, xe, bo, xo, U, 1.0 / mass, -1.0 / mass, nullptr, s));
