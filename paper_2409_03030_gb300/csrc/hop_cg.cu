@@ -22,8 +22,9 @@ namespace jqcd {
 
 namespace {
 
-// q = a*w + b*acc is (Ap)(idx); x += alpha p, r -= alpha q in place; returns
-// this thread's ||r||^2.  Every operand is a 16-byte double-word chunk.
+// q = a*w + b*acc is (Ap)(idx); x += alpha p (XUPD) and r -= alpha q in place;
+// returns this thread's ||r||^2.  Every operand is a 16-byte double-word chunk.
+template <bool XUPD>
 __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float4 *__restrict__ w_base,
                                               const float4 *__restrict__ p_base,
                                               float4 *__restrict__ x_base, float4 *__restrict__ r_base,
@@ -40,14 +41,16 @@ __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float
   acc2 nq{0ull, 0ull};
 #pragma unroll
   for (int k = 0; k < 12; ++k) {
-    const ulonglong2 wv = __ldg(wp + k * vh), pv = __ldg(pp + k * vh);
-    const ulonglong2 xv = xp[k * vh], rv = rp[k * vh];
+    const ulonglong2 wv = __ldg(wp + k * vh), rv = rp[k * vh];
     acc2 R = acc2_first(Bm, p2_norm(acc[k / 3][k % 3]));
     acc2_mad(R, Am, p2{wv.x, wv.y});
     const p2 q = p2_norm(acc2_get(R));
-    const p2 xn = p2_norm(p2_add(p2{xv.x, xv.y}, acc2_get(acc2_first(Al, p2{pv.x, pv.y}))));
+    if (XUPD) {
+      const ulonglong2 pv = __ldg(pp + k * vh), xv = xp[k * vh];
+      const p2 xn = p2_norm(p2_add(p2{xv.x, xv.y}, acc2_get(acc2_first(Al, p2{pv.x, pv.y}))));
+      xp[k * vh] = make_ulonglong2(xn.h, xn.l);
+    }
     const p2 rn = p2_norm(p2_add(p2{rv.x, rv.y}, acc2_get(acc2_first(Ml, q))));
-    xp[k * vh] = make_ulonglong2(xn.h, xn.l);
     rp[k * vh] = make_ulonglong2(rn.h, rn.l);
     const mul2 Q{rn.h, rn.l};
     if (k == 0) nq = acc2_first(Q, rn);
@@ -61,9 +64,10 @@ __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float
   return dwacc{s, __fadd_rn(__fadd_rn(c0, c1), e)};
 }
 
+template <bool XUPD>
 __global__ void __launch_bounds__(kHopThreads, 3)
     hop_dwp_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
-                      float4 *__restrict__ r, const SolverScalars *__restrict__ S) {
+                      float4 *__restrict__ r, const float2 *__restrict__ alpha) {
   extern __shared__ float4 dsm[];
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -72,8 +76,8 @@ __global__ void __launch_bounds__(kHopThreads, 3)
     p2 acc[4][3];
     dwp_hop_site<true>(dsm, reinterpret_cast<const float4 *>(P.in),
                        reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
-    nrm = dwp_store_cg(acc, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx, P.a_split,
-                       P.b_split, S->alpha_dw);
+    nrm = dwp_store_cg<XUPD>(acc, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx, P.a_split,
+                             P.b_split, *alpha);
   }
   const double s = block_sum_dw(nrm);
   if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
@@ -139,18 +143,28 @@ cudaError_t launch_hop_lp_cg(int prec, const HopParams &P, const void *p, float4
   }
 }
 
-cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
-                             const SolverScalars *S, cudaStream_t s) {
+template <bool XUPD>
+static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x, float4 *r, const float2 *alpha,
+                                  cudaStream_t s) {
   note_launch();
-  static bool configured = false;
+  static bool configured = false;  // one attribute call per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDwpSmem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  hop_dwp_cg_kernel<<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P, p, x, r, S);
+  hop_dwp_cg_kernel<XUPD><<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P, p, x, r, alpha);
   return cudaGetLastError();
+}
+
+cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
+                             const SolverScalars *S, cudaStream_t s) {
+  return launch_dw_cg_t<true>(P, p, x, r, &S->alpha_dw, s);
+}
+
+cudaError_t launch_hop_dw_r(const HopParams &P, float4 *r, const float2 *alpha_dw, cudaStream_t s) {
+  return launch_dw_cg_t<false>(P, nullptr, nullptr, r, alpha_dw, s);
 }
 
 }  // namespace jqcd

@@ -58,6 +58,7 @@ __global__ void ms_start_kernel(const double *partials, int n, MsScalars *S, dou
     S->max_iters = max_iters;
     S->done = 0;
     S->halt = 0;
+    S->final_x = 0;
     for (int i = 0; i < S->nshift; ++i) {
       S->zeta_prev[i] = S->zeta[i] = S->zeta_next[i] = 1.0;
       S->alpha_s[i] = S->beta_s[i] = 0.0;
@@ -72,12 +73,17 @@ __global__ void ms_start_kernel(const double *partials, int n, MsScalars *S, dou
 }
 
 __global__ void ms_alpha_kernel(const double *partials, int n, MsScalars *S) {
-  if (S->halt) return;
+  if (S->halt) {  // a queued iteration after the halt: the last x_i update is done
+    if (threadIdx.x == 0) S->final_x = 0;
+    return;
+  }
   const double pAp = sum_partials(partials, n);
   if (threadIdx.x == 0) {
     if (!(pAp > 0.0) || !isfinite(pAp)) { S->done = 2; S->halt = 1; return; }
     const double a = S->rr / pAp, ap = S->alpha_prev, b = S->beta;
     S->alpha = a;
+    const float ah = __double2float_rn(a);
+    S->alpha_dw = make_float2(ah, __double2float_rn(a - (double)ah));
     for (int i = 0; i < S->nshift; ++i) {
       if (!S->active[i]) continue;
       const double z = S->zeta[i], zp = S->zeta_prev[i];
@@ -86,51 +92,6 @@ __global__ void ms_alpha_kernel(const double *partials, int n, MsScalars *S) {
       S->alpha_s[i] = a * zn / z;
     }
   }
-}
-
-// x_i += alpha_i p_i for every active shift.
-__global__ void ms_x_kernel(MsVectors V, int64_t n, const MsScalars *S) {
-  __shared__ float2 coef[kMsMaxShifts];
-  __shared__ int act[kMsMaxShifts];
-  if (S->halt) return;
-  const int ns = S->nshift;
-  for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-    const double a = S->alpha_s[i];
-    const float h = __double2float_rn(a);
-    coef[i] = make_float2(h, __double2float_rn(a - (double)h));
-    act[i] = S->active[i];
-  }
-  __syncthreads();
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    for (int i = 0; i < ns; ++i) {
-      if (!act[i]) continue;
-      const dw a = dw_make(coef[i].x, coef[i].y);
-      dw xr, xi, pr, pi;
-      dwc_unpack(V.x[i][q], xr, xi);
-      dwc_unpack(V.p[i][q], pr, pi);
-      V.x[i][q] = dwc_pack(dw_add(xr, dw_mul(a, pr)), dw_add(xi, dw_mul(a, pi)));
-    }
-  }
-}
-
-// r -= alpha Ap, per-block partials of ||r||^2.
-__global__ void ms_r_kernel(float4 *__restrict__ r, const float4 *__restrict__ Ap, int64_t n, const MsScalars *S,
-                            double *partials) {
-  if (S->halt) return;
-  const dw a = dw_from_double(-S->alpha);
-  dwacc A{0.f, 0.f};
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
-    dw rr, ri, yr, yi;
-    dwc_unpack(r[q], rr, ri);
-    dwc_unpack(Ap[q], yr, yi);
-    rr = dw_add(rr, dw_mul(a, yr));
-    ri = dw_add(ri, dw_mul(a, yi));
-    r[q] = dwc_pack(rr, ri);
-    acc_sq(A, rr);
-    acc_sq(A, ri);
-  }
-  const double s = block_sum_dw(A);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
 __global__ void ms_beta_kernel(const double *partials, int n, MsScalars *S) {
@@ -142,6 +103,7 @@ __global__ void ms_beta_kernel(const double *partials, int n, MsScalars *S) {
     const double b = rr_new / S->rr;
     int any = 0;
     for (int i = 0; i < S->nshift; ++i) {
+      S->xact[i] = S->active[i];
       if (!S->active[i]) continue;
       const double z = S->zeta[i], zn = S->zeta_next[i];
       S->beta_s[i] = b * (zn / z) * (zn / z);
@@ -157,23 +119,30 @@ __global__ void ms_beta_kernel(const double *partials, int n, MsScalars *S) {
     S->beta = b;
     S->alpha_prev = S->alpha;
     S->rr = rr_new;
-    if (!any) { S->done = 1; S->halt = 1; }
-    else if (S->iters >= S->max_iters) { S->done = 3; S->halt = 1; }
+    if (!any) { S->done = 1; S->halt = 1; S->final_x = 1; }
+    else if (S->iters >= S->max_iters) { S->done = 3; S->halt = 1; S->final_x = 1; }
   }
 }
 
-// p = r + beta p; p_i = zeta_i r + beta_i p_i for every active shift.
-__global__ void ms_p_kernel(float4 *__restrict__ pb, const float4 *__restrict__ r, MsVectors V, int64_t n,
-                            const MsScalars *S) {
-  __shared__ float4 coef[kMsMaxShifts];  // (zeta.h, zeta.l, beta.h, beta.l)
-  __shared__ int act[kMsMaxShifts];
-  if (S->halt) return;
+// After beta: x_i += alpha_i p_i for the shifts active in this iteration
+// (xact; alpha_i from this iteration's alpha step) and p_i = zeta_i r +
+// beta_i p_i for those still active, p = r + beta p: each p_i is read once.
+// Runs while the solve iterates, and once more after the beta step that
+// halted it (final_x).
+__global__ void ms_xp_kernel(float4 *__restrict__ pb, const float4 *__restrict__ r, MsVectors V, int64_t n,
+                             const MsScalars *S) {
+  __shared__ float4 cp[kMsMaxShifts];  // (zeta.h, zeta.l, beta.h, beta.l)
+  __shared__ float2 cx[kMsMaxShifts];  // alpha_i (h, l)
+  __shared__ int ax[kMsMaxShifts], ap[kMsMaxShifts];
+  if (S->halt && !S->final_x) return;  // uniform across the grid
   const int ns = S->nshift;
   for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-    const double z = S->zeta[i], b = S->beta_s[i];
-    const float zh = __double2float_rn(z), bh = __double2float_rn(b);
-    coef[i] = make_float4(zh, __double2float_rn(z - (double)zh), bh, __double2float_rn(b - (double)bh));
-    act[i] = S->active[i];
+    const double z = S->zeta[i], b = S->beta_s[i], a = S->alpha_s[i];
+    const float zh = __double2float_rn(z), bh = __double2float_rn(b), ah = __double2float_rn(a);
+    cp[i] = make_float4(zh, __double2float_rn(z - (double)zh), bh, __double2float_rn(b - (double)bh));
+    cx[i] = make_float2(ah, __double2float_rn(a - (double)ah));
+    ax[i] = S->xact[i];
+    ap[i] = S->active[i] && !S->halt;
   }
   __syncthreads();
   const dw beta = dw_from_double(S->beta);
@@ -183,9 +152,14 @@ __global__ void ms_p_kernel(float4 *__restrict__ pb, const float4 *__restrict__ 
     dwc_unpack(pb[q], pr, pi);
     pb[q] = dwc_pack(dw_add(rr, dw_mul(beta, pr)), dw_add(ri, dw_mul(beta, pi)));
     for (int i = 0; i < ns; ++i) {
-      if (!act[i]) continue;
-      const dw z = dw_make(coef[i].x, coef[i].y), b = dw_make(coef[i].z, coef[i].w);
+      if (!ax[i]) continue;
       dwc_unpack(V.p[i][q], pr, pi);
+      const dw a = dw_make(cx[i].x, cx[i].y);
+      dw xr, xi;
+      dwc_unpack(V.x[i][q], xr, xi);
+      V.x[i][q] = dwc_pack(dw_add(xr, dw_mul(a, pr)), dw_add(xi, dw_mul(a, pi)));
+      if (!ap[i]) continue;
+      const dw z = dw_make(cp[i].x, cp[i].y), b = dw_make(cp[i].z, cp[i].w);
       V.p[i][q] = dwc_pack(dw_add(dw_mul(z, rr), dw_mul(b, pr)), dw_add(dw_mul(z, ri), dw_mul(b, pi)));
     }
   }
@@ -276,11 +250,31 @@ jqcd_status solve_multishift(GaugeEntry &G, const jqcd_solve_params &P, int nshi
     CKM(launch_dw_copy(V.p[i], rhs, n, s));
     CKM(launch_dw_zero(V.x[i], n, s));
   }
+  // One iteration: t = H_oe p; w = p - k^2 H_eo t with ||w||^2 = <p, Mhat^dag Mhat p>;
+  // alpha; t = H^dag_oe w; the last hop forms Ap at its site and applies
+  // r -= alpha Ap with ||r||^2 (Ap is not stored); beta; then the x_i and p_i
+  // of every shift in one pass.
+  const double k2 = -P.kappa * P.kappa;
+  float4 *t = G.vec_odd(G.vt), *w = G.vec_even(G.vw);
+  auto iteration = [&]() -> cudaError_t {
+    HopParams H = G.hop_params(PREC_DW, 1, pb, nullptr, t, 0.0, 1.0, nullptr);
+    H.guard = &S->halt;
+    cudaError_t e = launch_hop(PREC_DW, H, false, false, false, s);
+    if (e) return e;
+    H = G.hop_params(PREC_DW, 0, t, pb, w, 1.0, k2, G.partials);
+    H.guard = &S->halt;
+    if ((e = launch_hop(PREC_DW, H, false, true, true, s))) return e;
+    if ((e = launch_ms_alpha(G.partials, nhop, S, s))) return e;
+    H = G.hop_params(PREC_DW, 1, w, nullptr, t, 0.0, 1.0, nullptr);
+    H.guard = &S->halt;
+    if ((e = launch_hop(PREC_DW, H, true, false, false, s))) return e;
+    H = G.hop_params(PREC_DW, 0, t, w, nullptr, 1.0, k2, G.partials);
+    H.guard = &S->halt;
+    if ((e = launch_hop_dw_r(H, r, &S->alpha_dw, s))) return e;
+    return launch_ms_beta_xp(G.partials, nhop, nblas, S, V, r, pb, n, s);
+  };
   for (;;) {
-    for (int k = 0; k < kMsCheckEvery; ++k) {
-      CKM(apply_mdagm(G, PREC_DW, P.kappa, pb, Ap, G.vec_odd(G.vt), G.vec_even(G.vw), G.partials, &S->halt, s));
-      CKM(launch_ms_iteration(G.partials, nhop, nblas, S, V, r, pb, Ap, n, s));
-    }
+    for (int k = 0; k < kMsCheckEvery; ++k) CKM(iteration());
     CKM(cudaMemcpyAsync(H, S, sizeof(MsScalars), cudaMemcpyDeviceToHost, s));
     CKM(cudaStreamSynchronize(s));
     if (P.verbose >= 3)
@@ -335,14 +329,17 @@ cudaError_t launch_ms_start(const double *partials, int n, MsScalars *S, double 
   return cudaGetLastError();
 }
 
-cudaError_t launch_ms_iteration(double *partials, int nhop, int nblas, MsScalars *S, const MsVectors &V,
-                                float4 *r, float4 *pb, const float4 *Ap, int64_t n, cudaStream_t s) {
-  note_launch(5);
+cudaError_t launch_ms_alpha(const double *partials, int nhop, MsScalars *S, cudaStream_t s) {
+  note_launch();
   ms_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partials, nhop, S);
-  ms_x_kernel<<<nblas, kBlasThreads, 0, s>>>(V, n, S);
-  ms_r_kernel<<<nblas, kBlasThreads, 0, s>>>(r, Ap, n, S, partials);
-  ms_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, nblas, S);
-  ms_p_kernel<<<nblas, kBlasThreads, 0, s>>>(pb, r, V, n, S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ms_beta_xp(const double *partials, int nhop, int nblas, MsScalars *S, const MsVectors &V,
+                              const float4 *r, float4 *pb, int64_t n, cudaStream_t s) {
+  note_launch(2);
+  ms_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, nhop, S);
+  ms_xp_kernel<<<nblas, kBlasThreads, 0, s>>>(pb, r, V, n, S);
   return cudaGetLastError();
 }
 

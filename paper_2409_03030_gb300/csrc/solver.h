@@ -96,6 +96,11 @@ cudaError_t apply_mdagm(const GaugeEntry &G, int prec, double kappa, const void 
 cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
                              const SolverScalars *S, cudaStream_t s);
 
+// The same without x: Ap stays in registers, r -= alpha Ap with alpha =
+// *alpha_dw (device, hi/lo pair), P.partials gets ||r||^2 per hop block
+// (multi-shift CG, whose x_i are updated per shift elsewhere).
+cudaError_t launch_hop_dw_r(const HopParams &P, float4 *r, const float2 *alpha_dw, cudaStream_t s);
+
 // The same for the inner CG of the mixed solver in hop precision prec (FP32 or
 // FP16 with norm): p, t and w in that precision, xs and rs FP32, alpha =
 // S->alpha_f.
