@@ -10,6 +10,9 @@ source are resident in HBM when the timed region starts.
 value = Dslash GB/s of the whole job: algorithmic bytes of every hop launch
 in the timed solves (1536 B per output site, +192 B when the hop also reads
 an axpy operand) divided by the wall time of the solves, summed over ranks.
+gflops = the same solves in the Wilson hop's conventional 1320 flops per
+output site (spin projection, SU(3) times half-spinor, reconstruction and
+accumulation over the 8 directions; axpy terms not counted) per second.
 e2e   = the same quantity through jqcd_cg_solve with host buffers in pinned
 memory (copy of b in, copy of x out, inside the timed region).
 roofline = the double-word hop kernel timed alone on the same lattice.  It is
@@ -42,6 +45,7 @@ TOL = 1e-10
 METRIC = "Dslash GB/s vs HBM peak; CG s to 1e-10 mixed vs FP64; serve p50/p99"
 HOP_BYTES = {"dw": 1536, "f64": 1536, "f32": 576, "f16n": 488}  # per output site
 AXPY_BYTES = {"dw": 192, "f64": 192, "f32": 96, "f16n": 52}
+HOP_FLOPS_PER_SITE = 1320  # conventional Wilson hop count per output site (axpy not counted)
 HOP_KERNEL_SOURCES = ["dslash.cu", "hop.cuh", "hop_dw.cuh", "hop_dwp.cuh", "hop_lp.cuh", "dw2.cuh",
                       "fields.cuh", "dw.cuh", "lattice.cuh", "reduce.cuh", "kernels.h"]
 
@@ -552,8 +556,10 @@ def run_gpu(args):
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
     hop_bytes = sum(i["hop_bytes"] for i in infos)
-    (ms_max,), (bytes_sum,) = reduce_over_ranks([ms], [hop_bytes], "cuda")
+    hop_flops = sum(i["hop_count"] for i in infos) * (vol(DIMS) // 2) * HOP_FLOPS_PER_SITE
+    (ms_max,), (bytes_sum, flops_sum) = reduce_over_ranks([ms], [hop_bytes, hop_flops], "cuda")
     value = bytes_sum / (ms_max * 1e-3) / 1e9
+    gflops = flops_sum / (ms_max * 1e-3) / 1e9
     dw_s = ms / args.steps * 1e-3
 
     # end to end through the host-buffer C ABI call, pinned host memory
@@ -690,7 +696,8 @@ def run_gpu(args):
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "gflops": round(gflops, 1),
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_max / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32x2 (double-word, FP64-class)", "data": "synthetic",
@@ -715,6 +722,8 @@ def run_gpu(args):
                    "modes_24x24x24x48": cg_work, "modes_32x32x32x64": cg_c2},
             "dslash_gbs": {k: round(vh * HOP_BYTES[k] / (v * 1e-3) / 1e9, 1)
                            for k, v in hop_ms.items()},
+            "dslash_gflops": {k: round(vh * HOP_FLOPS_PER_SITE / (v * 1e-3) / 1e9, 1)
+                              for k, v in hop_ms.items()},
             "dslash_sweep_gbs": sweep,
             "force": force,
             "multishift": multishift,
