@@ -196,7 +196,6 @@ cudaError_t BatchEngine::admit(int slot, GaugeEntry *G, const jqcd_solve_params 
   const Geom &g = G->g;
   const int64_t vh = g.vh;
   cudaError_t e = H.buf.ensure(vh, hp_);
-  if (!e) e = G->ensure_row2(s_);  // 18-real FP32 links for the batched operator
   if (e) return e;
   SlotBuffers &B = H.buf;
   SolverScalars *S = d_S_ + slot;
@@ -241,7 +240,6 @@ cudaError_t BatchEngine::admit(int slot, GaugeEntry *G, const jqcd_solve_params 
   memset(&D, 0, sizeof D);
   D.g = g;
   D.gauge_f32 = (const float4 *)G->gauge_f32;
-  D.gauge_row2 = (const float4 *)G->gauge_row2;
   D.gauge_dw = (const float4 *)G->gauge_dw;
   D.kappa = k;
   D.k2 = (float)(-k * k);
@@ -278,7 +276,6 @@ cudaError_t BatchEngine::rebuild() {
       memset(&Gd, 0, sizeof Gd);
       Gd.g = D.g;
       Gd.gauge_f32 = D.gauge_f32;
-      Gd.gauge_row2 = D.gauge_row2;
       Gd.gauge_dw = D.gauge_dw;
       groups.push_back(Gd);
       open[D.gauge_f32] = (int)groups.size() - 1;

@@ -22,8 +22,7 @@ constexpr int kBatchMaxRhs = 16;  // right-hand sides per group (one tile pass)
 
 struct SlotDev {
   Geom g;
-  const float4 *gauge_f32;  // [2][4][3][vh]  FP32 link rows 0 and 1
-  const float4 *gauge_row2; // [2][4][2][vh]  FP32 link row 2 (18-real links with gauge_f32)
+  const float4 *gauge_f32;  // [2][4][3][vh]  12-real FP32 links
   const float4 *gauge_dw;   // [2][4][9][vh]  double-word links
   double kappa;
   float k2;                 // -kappa^2
@@ -43,7 +42,6 @@ struct SlotDev {
 struct GroupDev {
   Geom g;
   const float4 *gauge_f32;
-  const float4 *gauge_row2;
   const float4 *gauge_dw;
   int nslots;
   int slot[kBatchMaxRhs];

@@ -26,17 +26,12 @@ __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
 // (slot, block of 128 sites); consecutive items are the right-hand sides of
 // one group on the same sites, so their link loads meet in L2.  The site
 // loop (hop_lp.cuh) prefetches the next hop's neighbour and link into shared
-// memory while the current hop computes.  Links are 18-real (the third row
-// from gauge_row2): the kernel is bound by instruction issue and the links
-// come from L2, so reading two more chunks beats rebuilding the row.
+// memory while the current hop computes.
 // STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t, ||w||^2;  2: t = H^dag_oe w;
 // STAGE 3: Ap = w - kappa^2 H^dag_eo t, then (UPDATE) x_s += alpha p,
 //          r_s -= alpha Ap, ||r_s||^2 without storing Ap.
-// 5 blocks/SM: 96 registers (8-24 bytes of spill in a few instantiations);
-// uncapped the 18-real form takes 109-128 registers and 4 blocks/SM, which
-// measured slower than rebuilding the row at 5.
 template <int PREC, int STAGE, bool UPDATE>
-__global__ void __launch_bounds__(kLpThreads, 5) batch_lp_hop_kernel(const BatchArgs A) {
+__global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
   extern __shared__ float4 lsm[];
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
@@ -58,7 +53,7 @@ __global__ void __launch_bounds__(kLpThreads, 5) batch_lp_hop_kernel(const Batch
       const void *xv = STAGE == 1 ? Sl.p : Sl.w;
       void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
       cf acc[4][3];
-      lp_hop_site<PREC, DAG, true, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc, G->gauge_row2);
+      lp_hop_site<PREC, DAG, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc);
       const int64_t vh = g.vh;
       cf o[4][3];
       if (AXPY) {
@@ -344,7 +339,7 @@ cudaError_t batch_configure() {
 template <int PREC, int STAGE, bool UPDATE>
 static void lp_stage(const BatchArgs &A, int lp_grid, cudaStream_t s) {
   note_launch();
-  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC, true>(), s>>>(A);
+  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
 }
 
 template <int PREC>

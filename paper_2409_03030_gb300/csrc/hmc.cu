@@ -325,7 +325,7 @@ __global__ void exp_update_kernel(Geom g, double2 *__restrict__ U, const double2
 
 // FP64 links -> double-word and 12-real FP32 copies (same per-link layout as gauge_pack)
 __global__ void links_refresh_kernel(Geom g, const double2 *__restrict__ U, float4 *__restrict__ dwo,
-                                     float4 *__restrict__ f32o, float4 *__restrict__ row2o) {
+                                     float4 *__restrict__ f32o) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 8 * g.vh) return;
   const int mu = (int)(q / (2 * g.vh));
@@ -346,27 +346,6 @@ __global__ void links_refresh_kernel(Geom g, const double2 *__restrict__ U, floa
   for (int j = 0; j < 3; ++j)
     f32o[(blk * 3 + j) * g.vh + cb] = make_float4((float)e[2 * j].x, (float)e[2 * j].y, (float)e[2 * j + 1].x,
                                                   (float)e[2 * j + 1].y);
-  if (row2o) {
-    row2o[(blk * 2) * g.vh + cb] = make_float4((float)A.e[2][0].x, (float)A.e[2][0].y, (float)A.e[2][1].x,
-                                               (float)A.e[2][1].y);
-    row2o[(blk * 2 + 1) * g.vh + cb] = make_float4((float)A.e[2][2].x, (float)A.e[2][2].y, 0.f, 0.f);
-  }
-}
-
-// Third row of every FP64 master link in FP32, [2][4][2][vh] chunks
-// (U20, U21), (U22, 0): completes the 12-real FP32 field to 18 reals.
-__global__ void links_row2_kernel(Geom g, const double2 *__restrict__ U, float4 *__restrict__ row2o) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= 8 * g.vh) return;
-  const int mu = (int)(q / (2 * g.vh));
-  const int64_t r = q % (2 * g.vh);
-  const int p = (int)(r / g.vh);
-  const int64_t cb = r - (int64_t)p * g.vh;
-  const double2 *u = U + (size_t)((p * 4 + mu) * 9) * g.vh + cb;
-  const double2 a = u[6 * g.vh], b = u[7 * g.vh], c = u[8 * g.vh];
-  const int64_t blk = (int64_t)(p * 4 + mu);
-  row2o[(blk * 2) * g.vh + cb] = make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-  row2o[(blk * 2 + 1) * g.vh + cb] = make_float4((float)c.x, (float)c.y, 0.f, 0.f);
 }
 
 // FP64 link field -> canonical host layout a + 3(b + 3(site + V mu))
@@ -424,15 +403,6 @@ cudaError_t GaugeEntry::ensure_hmc() {
   return e;
 }
 
-cudaError_t GaugeEntry::ensure_row2(cudaStream_t s) {
-  if (gauge_row2) return cudaSuccess;
-  cudaError_t e = alloc(&gauge_row2, (size_t)2 * 4 * 2 * 16 * g.vh);
-  if (e) return e;
-  note_launch();
-  links_row2_kernel<<<link_blocks(g.vh), kHmcThreads, 0, s>>>(g, (const double2 *)gauge_f64, (float4 *)gauge_row2);
-  return cudaGetLastError();
-}
-
 cudaError_t GaugeEntry::ensure_hmc_history() {
   cudaError_t e = cudaSuccess;
   const size_t full = 2 * spinor_parity_bytes(PREC_DW, g.vh);
@@ -445,8 +415,7 @@ cudaError_t GaugeEntry::ensure_hmc_history() {
 cudaError_t launch_hmc_links_refresh(GaugeEntry &G, cudaStream_t s) {
   note_launch();
   links_refresh_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (const double2 *)G.gauge_f64,
-                                                                      (float4 *)G.gauge_dw, (float4 *)G.gauge_f32,
-                                                                      (float4 *)G.gauge_row2);
+                                                                      (float4 *)G.gauge_dw, (float4 *)G.gauge_f32);
   return cudaGetLastError();
 }
 

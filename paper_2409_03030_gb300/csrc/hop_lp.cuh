@@ -25,14 +25,9 @@ template <> struct LpStage<PREC_F16N> {
   static constexpr int kSpin = 4;    // three half chunks + one slot for the site norm
   static constexpr int kChunks = 7;
 };
-// Chunks of one stage: the spinor and the link's rows 0 and 1, plus row 2
-// (two chunks) when ROW2 (18-real links, no reconstruction).
-template <int PREC, bool ROW2 = false> __host__ __device__ constexpr int lp_stage_chunks() {
-  return LpStage<PREC>::kChunks + (ROW2 ? 2 : 0);
-}
 // Dynamic shared memory of a kHopThreads block.
-template <int PREC, bool ROW2 = false> constexpr size_t lp_stage_smem() {
-  return 2ull * lp_stage_chunks<PREC, ROW2>() * kHopThreads * 16;
+template <int PREC> constexpr size_t lp_stage_smem() {
+  return 2ull * LpStage<PREC>::kChunks * kHopThreads * 16;
 }
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
@@ -41,12 +36,10 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
 }
 
 // Copies of hop d's neighbour spinor (site nb of the input parity) and link
-// (forward: U_mu(idx) of parity p; backward: U_mu(nb) of parity 1-p); with
-// ROW2 also the link's third row from row2 ([2][4][2][vh] chunks).
-template <int PREC, bool LINK_L1, bool ROW2 = false>
+// (forward: U_mu(idx) of parity p; backward: U_mu(nb) of parity 1-p).
+template <int PREC, bool LINK_L1>
 __device__ __forceinline__ void lp_stage_issue(float4 *st, const void *in, const float4 *gauge,
-                                               int64_t vh, int p, int64_t idx, int d, int64_t nb,
-                                               const float4 *row2 = nullptr) {
+                                               int64_t vh, int p, int64_t idx, int d, int64_t nb) {
   typedef LpStage<PREC> S;
   const int tid = threadIdx.x;
   if (PREC == PREC_F32) {
@@ -64,18 +57,13 @@ __device__ __forceinline__ void lp_stage_issue(float4 *st, const void *in, const
   const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 3) * vh + (bwd ? nb : idx);
 #pragma unroll
   for (int k = 0; k < 3; ++k) cp_async16(st + (S::kSpin + k) * kHopThreads + tid, L + k * vh, LINK_L1);
-  if (ROW2) {
-    const float4 *R = row2 + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 2) * vh + (bwd ? nb : idx);
-#pragma unroll
-    for (int k = 0; k < 2; ++k) cp_async16(st + (S::kChunks + k) * kHopThreads + tid, R + k * vh, LINK_L1);
-  }
 }
 
 // Spinor and link of one stage slot (st already offset by the thread).  For
 // FP16 the spinor comes back unscaled and *norm holds the site norm (the
 // caller scales the projected half-spinor: 12 multiplies instead of 24);
 // for FP32 *norm = 1.
-template <int PREC, bool ROW2 = false>
+template <int PREC>
 __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3], cf (&u)[3][3], float *norm) {
   typedef LpStage<PREC> S;
   if (PREC == PREC_F32) {
@@ -100,19 +88,8 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
       }
     }
   }
-  if (ROW2) {
-    const float4 c0 = st[S::kSpin * kHopThreads], c1 = st[(S::kSpin + 1) * kHopThreads],
-                 c2 = st[(S::kSpin + 2) * kHopThreads], c3 = st[S::kChunks * kHopThreads],
-                 c4 = st[(S::kChunks + 1) * kHopThreads];
-    u[0][0] = cf{c0.x, c0.y}; u[0][1] = cf{c0.z, c0.w};
-    u[0][2] = cf{c1.x, c1.y}; u[1][0] = cf{c1.z, c1.w};
-    u[1][1] = cf{c2.x, c2.y}; u[1][2] = cf{c2.z, c2.w};
-    u[2][0] = cf{c3.x, c3.y}; u[2][1] = cf{c3.z, c3.w};
-    u[2][2] = cf{c4.x, c4.y};
-  } else {
-    PT_F32Links::link_from_chunks(st[S::kSpin * kHopThreads], st[(S::kSpin + 1) * kHopThreads],
-                                  st[(S::kSpin + 2) * kHopThreads], u);
-  }
+  PT_F32Links::link_from_chunks(st[S::kSpin * kHopThreads], st[(S::kSpin + 1) * kHopThreads],
+                                st[(S::kSpin + 2) * kHopThreads], u);
 }
 
 // One hop: project, site norm (FP16) and boundary sign, link multiply,
@@ -137,13 +114,11 @@ __device__ __forceinline__ void lp_apply(const cf (&psi)[4][3], const cf (&u)[3]
 }
 
 // acc = (H_{p,1-p} in)(idx) (DAG: the adjoint hop); smem: this block's
-// lp_stage_smem<PREC, ROW2>() bytes; blockDim.x must be kHopThreads.  ROW2:
-// 18-real links, the third row read from row2 instead of rebuilt.
-template <int PREC, bool DAG, bool LINK_L1, bool ROW2 = false>
+// lp_stage_smem<PREC>() bytes; blockDim.x must be kHopThreads.
+template <int PREC, bool DAG, bool LINK_L1>
 __device__ __forceinline__ void lp_hop_site(float4 *smem, const void *in, const float4 *gauge,
-                                            const Geom &g, int p, int64_t idx, cf (&acc)[4][3],
-                                            const float4 *row2 = nullptr) {
-  constexpr int C = lp_stage_chunks<PREC, ROW2>();
+                                            const Geom &g, int p, int64_t idx, cf (&acc)[4][3]) {
+  constexpr int C = LpStage<PREC>::kChunks;
   const int64_t vh = g.vh;
   int x, y, z, t;
   cb_coords(g, idx, p, x, y, z, t);
@@ -154,21 +129,20 @@ __device__ __forceinline__ void lp_hop_site(float4 *smem, const void *in, const 
   const int tid = threadIdx.x;
   bool neg_next;
   int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
-  lp_stage_issue<PREC, LINK_L1, ROW2>(smem, in, gauge, vh, p, idx, 0, nb, row2);
+  lp_stage_issue<PREC, LINK_L1>(smem, in, gauge, vh, p, idx, 0, nb);
   cp_async_commit();
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
     const bool neg = neg_next;
     if (d < 7) {
       nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-      lp_stage_issue<PREC, LINK_L1, ROW2>(smem + ((d + 1) & 1) * C * kHopThreads, in, gauge, vh, p, idx, d + 1,
-                                          nb, row2);
+      lp_stage_issue<PREC, LINK_L1>(smem + ((d + 1) & 1) * C * kHopThreads, in, gauge, vh, p, idx, d + 1, nb);
     }
     cp_async_commit();
     cp_async_wait1();  // this thread's copies of hop d have landed
     cf psi[4][3], u[3][3];
     float nrm;
-    lp_stage_read<PREC, ROW2>(smem + (d & 1) * C * kHopThreads + tid, psi, u, &nrm);
+    lp_stage_read<PREC>(smem + (d & 1) * C * kHopThreads + tid, psi, u, &nrm);
     switch (d) {  // d is a constant after unrolling
       case 0: lp_apply<PREC, 0, false, DAG>(psi, u, nrm, neg, acc); break;
       case 1: lp_apply<PREC, 0, true, DAG>(psi, u, nrm, neg, acc); break;

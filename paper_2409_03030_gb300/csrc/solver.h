@@ -14,11 +14,6 @@ namespace jqcd {
 struct GaugeEntry {
   Geom g{};
   void *gauge_dw = nullptr, *gauge_f64 = nullptr, *gauge_f32 = nullptr;
-  // third link row in FP32, [2][4][2][vh] chunks (U20, U21), (U22, 0): with
-  // gauge_f32 an 18-real field for the batched operator (ensure_row2; kept
-  // current by the HMC link refresh)
-  void *gauge_row2 = nullptr;
-  cudaError_t ensure_row2(cudaStream_t s);
 
   // workspace, allocated on first use
   double *canon = nullptr;        // 12*V complex doubles: host <-> device staging
