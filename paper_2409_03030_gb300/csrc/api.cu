@@ -24,6 +24,7 @@
 #include "solver.h"
 #include "staggered.h"
 #include "hmc.h"
+#include <nvtx3/nvToolsExt.h>
 
 using namespace jqcd;
 
@@ -110,6 +111,16 @@ bool valid_prec(int32_t p) { return p >= 0 && p <= 3; }
 
 }  // namespace
 
+// NVTX range over one C ABI call, named after the call: visible to
+// profilers, a no-op when none is attached.
+struct AbiRange {
+  explicit AbiRange(const char *name) { nvtxRangePushA(name); }
+  ~AbiRange() { nvtxRangePop(); }
+  AbiRange(const AbiRange &) = delete;
+  AbiRange &operator=(const AbiRange &) = delete;
+};
+#define JQCD_RANGE() AbiRange jqcd_range_(__func__)
+
 extern "C" {
 
 int32_t jqcd_abi_version(void) { return JQCD_ABI_VERSION; }
@@ -117,6 +128,7 @@ int32_t jqcd_abi_version(void) { return JQCD_ABI_VERSION; }
 uint64_t jqcd_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 jqcd_status jqcd_init(int device, jqcd_ctx **out) {
+  JQCD_RANGE();
   if (!out) return JQCD_EINVAL;
   *out = nullptr;
   int n = 0;
@@ -136,6 +148,7 @@ jqcd_status jqcd_init(int device, jqcd_ctx **out) {
 }
 
 jqcd_status jqcd_finalize(jqcd_ctx *ctx) {
+  JQCD_RANGE();
   if (!ctx) return JQCD_EINVAL;
   cudaSetDevice(ctx->device);
   if (ctx->server) {
@@ -156,6 +169,7 @@ const char *jqcd_last_error(const jqcd_ctx *ctx) { return ctx ? ctx->err.c_str()
 
 jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const double *links,
                               uint32_t flags, uint64_t *gauge_id) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   if (!links || !gauge_id) return fail(ctx, JQCD_EINVAL, "links or gauge_id is NULL");
@@ -187,6 +201,7 @@ jqcd_status jqcd_gauge_upload(jqcd_ctx *ctx, const jqcd_lattice *lat, const doub
 }
 
 jqcd_status jqcd_gauge_free(jqcd_ctx *ctx, uint64_t gauge_id) {
+  JQCD_RANGE();
   if (!ctx) return JQCD_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->gauges_mu);
   auto it = ctx->gauges.find(gauge_id);
@@ -201,6 +216,7 @@ jqcd_status jqcd_gauge_free(jqcd_ctx *ctx, uint64_t gauge_id) {
 }
 
 jqcd_status jqcd_spinor_bytes(const jqcd_lattice *lat, int32_t prec, size_t *bytes) {
+  JQCD_RANGE();
   if (!bytes || !valid_prec(prec)) return JQCD_EINVAL;
   Geom g;
   if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
@@ -210,6 +226,7 @@ jqcd_status jqcd_spinor_bytes(const jqcd_lattice *lat, int32_t prec, size_t *byt
 
 jqcd_status jqcd_spinor_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, int32_t prec,
                              void *dev_even, void *dev_odd, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -226,6 +243,7 @@ jqcd_status jqcd_spinor_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *hos
 jqcd_status jqcd_spinor_unpack(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
                                const void *dev_even, const void *dev_odd, double *host,
                                void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -243,6 +261,7 @@ jqcd_status jqcd_spinor_unpack(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec,
 jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, int32_t out_parity,
                            int32_t dagger, const void *in, const void *x, void *out, double a,
                            double b, double *norm2_dev, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -259,6 +278,7 @@ jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, int32
 
 jqcd_status jqcd_mdagm(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa, const void *in,
                        void *out, double *norm2_dev, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -277,6 +297,7 @@ jqcd_status jqcd_mdagm(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double ka
 jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double kappa,
                              int32_t dagger, const void *in_even, const void *in_odd,
                              void *out_even, void *out_odd, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -294,6 +315,7 @@ jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, dou
 
 jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                           const double *b, double *x, jqcd_solve_info *info) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -331,6 +353,7 @@ jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_par
 jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                               const void *b_even, const void *b_odd, void *x_even, void *x_odd,
                               jqcd_solve_info *info, void *stream) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -368,6 +391,7 @@ jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve
 jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_ids,
                                 const jqcd_solve_params *params, const double *const *b,
                                 double *const *x, jqcd_solve_info *infos) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   if (n < 1 || !gauge_ids || !params || !b || !x) return fail(ctx, JQCD_EINVAL, "cg_solve_batch: bad argument");
@@ -446,6 +470,7 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
 
 jqcd_status jqcd_serve_start(jqcd_ctx *ctx, size_t hbm_budget_bytes, int32_t max_slots,
                              int32_t max_queue, int32_t mode) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   if (ctx->server) return fail(ctx, JQCD_EBUSY, "a server is already running on this context");
@@ -461,6 +486,7 @@ jqcd_status jqcd_serve_start(jqcd_ctx *ctx, size_t hbm_budget_bytes, int32_t max
 }
 
 jqcd_status jqcd_serve_submit(jqcd_ctx *ctx, const jqcd_request *req, uint64_t *ticket) {
+  JQCD_RANGE();
   if (!ctx || !req || !ticket || !req->b || !req->x) return JQCD_EINVAL;
   if (!ctx->server) return JQCD_EINVAL;
   const jqcd_solve_params &P = req->params;
@@ -478,11 +504,13 @@ jqcd_status jqcd_serve_submit(jqcd_ctx *ctx, const jqcd_request *req, uint64_t *
 }
 
 jqcd_status jqcd_serve_poll(jqcd_ctx *ctx, uint64_t ticket, jqcd_solve_info *info) {
+  JQCD_RANGE();
   if (!ctx || !ctx->server) return JQCD_EINVAL;
   return serve_poll(ctx->server, ticket, info, true);
 }
 
 jqcd_status jqcd_serve_stop(jqcd_ctx *ctx, jqcd_serve_stats *stats) {
+  JQCD_RANGE();
   if (!ctx) return JQCD_EINVAL;
   if (!ctx->server) return fail(ctx, JQCD_EINVAL, "no server running");
   std::string err;
@@ -656,18 +684,21 @@ extern "C" {
 
 jqcd_status jqcd_fermi_action(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                               const double *eta, double *action, jqcd_solve_info *info) {
+  JQCD_RANGE();
   if (!action) return fail(ctx, JQCD_EINVAL, "fermi_action: action is NULL");
   return fermi_common(ctx, gauge_id, params, eta, nullptr, action, info, "fermi_action");
 }
 
 jqcd_status jqcd_fermi_force(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                              const double *eta, double *udsdu, double *action, jqcd_solve_info *info) {
+  JQCD_RANGE();
   if (!udsdu) return fail(ctx, JQCD_EINVAL, "fermi_force: udsdu is NULL");
   return fermi_common(ctx, gauge_id, params, eta, udsdu, action, info, "fermi_force");
 }
 
 jqcd_status jqcd_fermi_force_xy(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const double *X,
                                 const double *Y, double *udsdu) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -691,6 +722,7 @@ jqcd_status jqcd_fermi_force_xy(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, 
 jqcd_status jqcd_fermi_force_dev(jqcd_ctx *ctx, uint64_t gauge_id, double kappa, const void *X_even,
                                  const void *X_odd, const void *Y_even, const void *Y_odd, void *out,
                                  void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -704,6 +736,7 @@ jqcd_status jqcd_fermi_force_dev(jqcd_ctx *ctx, uint64_t gauge_id, double kappa,
 }
 
 jqcd_status jqcd_linkfield_bytes(const jqcd_lattice *lat, size_t *bytes) {
+  JQCD_RANGE();
   if (!bytes) return JQCD_EINVAL;
   Geom g;
   if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
@@ -719,6 +752,7 @@ extern "C" {
 jqcd_status jqcd_cg_multishift(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                                int32_t nshift, const double *shifts, const double *rhs, double *const *x,
                                jqcd_solve_info *infos) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -768,6 +802,7 @@ jqcd_status jqcd_cg_multishift(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solv
 jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                                    int32_t nshift, const double *shifts, const void *rhs_even,
                                    void *const *x_even, jqcd_solve_info *infos, void *stream) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -803,6 +838,7 @@ jqcd_status jqcd_cg_multishift_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_
 extern "C" {
 
 jqcd_status jqcd_staggered_bytes(const jqcd_lattice *lat, size_t *bytes) {
+  JQCD_RANGE();
   if (!bytes) return JQCD_EINVAL;
   Geom g;
   if (lattice_geom(nullptr, lat, &g)) return JQCD_EINVAL;
@@ -812,6 +848,7 @@ jqcd_status jqcd_staggered_bytes(const jqcd_lattice *lat, size_t *bytes) {
 
 jqcd_status jqcd_staggered_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *host, void *dev_even,
                                 void *dev_odd, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -827,6 +864,7 @@ jqcd_status jqcd_staggered_pack(jqcd_ctx *ctx, uint64_t gauge_id, const double *
 
 jqcd_status jqcd_staggered_unpack(jqcd_ctx *ctx, uint64_t gauge_id, const void *dev_even, const void *dev_odd,
                                   double *host, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -844,6 +882,7 @@ jqcd_status jqcd_staggered_unpack(jqcd_ctx *ctx, uint64_t gauge_id, const void *
 jqcd_status jqcd_staggered_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t out_parity, int32_t dagger,
                                      const void *in, const void *x, void *out, double a, double b,
                                      double *norm2_dev, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -865,6 +904,7 @@ jqcd_status jqcd_staggered_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t o
 jqcd_status jqcd_staggered_apply(jqcd_ctx *ctx, uint64_t gauge_id, double mass, int32_t dagger,
                                  const void *in_even, const void *in_odd, void *out_even, void *out_odd,
                                  void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -882,6 +922,7 @@ jqcd_status jqcd_staggered_apply(jqcd_ctx *ctx, uint64_t gauge_id, double mass, 
 
 jqcd_status jqcd_staggered_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params, double mass,
                                  const double *b, double *x, jqcd_solve_info *info) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -914,6 +955,7 @@ jqcd_status jqcd_staggered_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_so
 jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                                      double mass, const void *b_even, const void *b_odd, void *x_even, void *x_odd,
                                      jqcd_solve_info *info, void *stream) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
@@ -949,6 +991,7 @@ jqcd_status jqcd_staggered_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqc
 extern "C" {
 
 jqcd_status jqcd_gauge_plaquette(jqcd_ctx *ctx, uint64_t gauge_id, double *plaquette) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -962,6 +1005,7 @@ jqcd_status jqcd_gauge_plaquette(jqcd_ctx *ctx, uint64_t gauge_id, double *plaqu
 }
 
 jqcd_status jqcd_gauge_download(jqcd_ctx *ctx, uint64_t gauge_id, double *links) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
@@ -977,6 +1021,7 @@ jqcd_status jqcd_gauge_download(jqcd_ctx *ctx, uint64_t gauge_id, double *links)
 
 jqcd_status jqcd_hmc_trajectory(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_hmc_params *hp, const double *normals,
                                 const double *xi, double u, jqcd_hmc_info *info) {
+  JQCD_RANGE();
   const auto t0 = std::chrono::steady_clock::now();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;

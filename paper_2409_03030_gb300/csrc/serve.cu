@@ -27,6 +27,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "batch_engine.h"
 #include "serve.h"
 
@@ -139,7 +141,9 @@ void Server::loop() {
     cudaError_t e = cudaSuccess;
     for (auto &a : admit) {
       ServeTicket *T = a.second;
+      nvtxRangePushA("serve admit");
       e = engine->admit(T->slot, T->G, T->req.params, T->req.b);
+      nvtxRangePop();
       if (e) break;
       std::lock_guard<std::mutex> lk(mu);
       T->state = 1;
@@ -157,9 +161,11 @@ void Server::loop() {
         if (slot >= 0 && (int64_t)engine->allocated_bytes() + extra <= (int64_t)budget) continue;
       }
     }
+    nvtxRangePushA("serve iterate");
     if (!e && engine->running() > 0) e = engine->run(kItersPerStep);
     finished.clear();
     if (!e) e = engine->poll(&finished);
+    nvtxRangePop();
     // finished solves: reconstruction queued, x copied to the caller's buffer
     // on the copy stream while the other requests keep iterating
     for (int slot : finished) {
