@@ -496,7 +496,8 @@ def bench_serve(ctx, jqcd, synth, np, n_req, rate=20.0, host="pinned"):
            "arrival_span_s": round(float(arrivals[-1]), 3), "wall_s": round(wall, 3),
            "stable": bool(wall < arrivals[-1] + 2.0),
            "server_p50_s": round(stats["p50_s"], 5), "server_p99_s": round(stats["p99_s"], 5),
-           "peak_active": stats["peak_active"], "peak_slot_bytes": stats["peak_hbm_bytes"],
+           "peak_active": stats["peak_active"], "peak_queue": stats["peak_queue"],
+           "peak_slot_bytes": stats["peak_hbm_bytes"],
            "max_true_resid_over_tol": worst_res,
            "by_volume": {"x".join(map(str, d)): {
                "n": len(lv), "p50_s": round(float(np.percentile(lv, 50)), 5) if lv else None,

@@ -283,7 +283,7 @@ typedef struct {
   double wall_s;
   double peak_hbm_bytes;  /* peak device bytes held by solve slots */
   int32_t peak_active;    /* largest number of solves iterating together */
-  int32_t reserved;
+  int32_t peak_queue;     /* largest number of requests waiting for admission */
 } jqcd_serve_stats;
 
 /* Start the scheduler thread.  max_slots: solves iterating together (>= 1);

@@ -73,6 +73,7 @@ struct Server {
   std::map<int, uint64_t> slot_ticket;              // engine slot -> ticket
   size_t peak_alloc = 0;                            // peak device bytes of slot buffers
   int peak_active = 0;
+  int peak_queue = 0;                               // most requests waiting at once
   double t_first = 0.0, t_last = 0.0;
   std::vector<double> latencies;
   int64_t rejected = 0;
@@ -245,6 +246,7 @@ jqcd_status serve_submit(Server *S, GaugeEntry *G, const jqcd_request &r, uint64
   if (S->t_first == 0.0) S->t_first = T->t_submit;
   S->tickets[id] = std::move(T);
   S->queue.push_back(id);
+  S->peak_queue = std::max(S->peak_queue, (int)S->queue.size());
   *ticket = id;
   S->cv.notify_one();
   return JQCD_OK;
@@ -299,6 +301,7 @@ jqcd_status serve_destroy(Server *S, jqcd_serve_stats *stats, std::string *err) 
     stats->solves_per_s = stats->wall_s > 0 ? l.size() / stats->wall_s : 0.0;
     stats->peak_hbm_bytes = (double)S->peak_alloc;
     stats->peak_active = S->peak_active;
+    stats->peak_queue = S->peak_queue;
   }
   S->engine.reset();
   if (S->stream) cudaStreamDestroy(S->stream);

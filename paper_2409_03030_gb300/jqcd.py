@@ -52,7 +52,7 @@ class jqcd_serve_stats(ctypes.Structure):
                 ("p50_s", ctypes.c_double), ("p99_s", ctypes.c_double), ("mean_s", ctypes.c_double),
                 ("solves_per_s", ctypes.c_double), ("wall_s", ctypes.c_double),
                 ("peak_hbm_bytes", ctypes.c_double), ("peak_active", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("peak_queue", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

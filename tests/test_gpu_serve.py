@@ -68,7 +68,7 @@ def test_serve_mix_equals_alone(jq, host):
             time.sleep(0.005)  # later requests join while earlier ones iterate
     res = wait_all(ctx, jqcd, tickets)
     stats = ctx.serve_stop()
-    assert stats["completed"] == len(reqs) and stats["peak_active"] >= 2
+    assert stats["completed"] == len(reqs) and stats["peak_active"] >= 2 and stats["peak_queue"] >= 1
     for (k, b, kap, tol), x, t in zip(reqs, xs, tickets):
         st, info = res[t]
         assert st == 0 and info["true_rel_resid"] <= tol
@@ -110,5 +110,6 @@ def test_serve_backpressure_and_budget(jq):
     assert st == jqcd.EINVAL
     res = wait_all(ctx, jqcd, tickets)
     assert all(v[0] == 0 for v in res.values())
-    ctx.serve_stop()
+    stats = ctx.serve_stop()
+    assert stats["peak_queue"] == 1  # the queue limit held and was reached
     g.free()
