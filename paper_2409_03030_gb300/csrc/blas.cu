@@ -39,15 +39,6 @@ __global__ void dw_zero_kernel(float4 *__restrict__ d, int64_t n) {
     d[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-__global__ void dw_add_kernel(float4 *__restrict__ y, const float4 *__restrict__ x, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    dw ar, ai, br, bi;
-    dwc_unpack(y[i], ar, ai);
-    dwc_unpack(x[i], br, bi);
-    y[i] = dwc_pack(dw_add(ar, br), dw_add(ai, bi));
-  }
-}
-
 __global__ void dw_norm2_kernel(const float4 *__restrict__ a, int64_t n, double *partials) {
   dwacc A{0.f, 0.f};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -200,12 +191,8 @@ cudaError_t launch_dw_zero(float4 *dst, int64_t n, cudaStream_t s) {
   dw_zero_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(dst, n);
   return cudaGetLastError();
 }
-cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s) {
-  note_launch();
-  dw_add_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(y, x, n);
-  return cudaGetLastError();
-}
 cudaError_t launch_dw_norm2(const float4 *a, int64_t n, double *partials, cudaStream_t s) {
+  note_launch();
   dw_norm2_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(a, n, partials);
   return cudaGetLastError();
 }

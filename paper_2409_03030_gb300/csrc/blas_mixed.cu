@@ -26,37 +26,6 @@ __device__ __forceinline__ void store_f32(float4 *base, int64_t vh, int64_t i, c
 }
 
 template <int PREC>
-__global__ void mixed_update_kernel(float4 *__restrict__ xs, float4 *__restrict__ rs,
-                                    const void *__restrict__ p, const void *__restrict__ Ap,
-                                    int64_t vh, const SolverScalars *S, double *partials) {
-  if (S->halt) return;
-  const float a = S->alpha_f;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  float n2 = 0.f;
-  if (i < vh) {
-    cf pv[4][3], av[4][3], xv[4][3], rv[4][3];
-    PT<PREC>::load_spinor(p, vh, i, pv);
-    PT<PREC>::load_spinor(Ap, vh, i, av);
-    load_f32(xs, vh, i, xv);
-    load_f32(rs, vh, i, rv);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      cf &x = xv[k / 3][k % 3], &r = rv[k / 3][k % 3];
-      const cf pp = pv[k / 3][k % 3], aa = av[k / 3][k % 3];
-      x.re = fmaf(a, pp.re, x.re);
-      x.im = fmaf(a, pp.im, x.im);
-      r.re = fmaf(-a, aa.re, r.re);
-      r.im = fmaf(-a, aa.im, r.im);
-      n2 = fmaf(r.re, r.re, fmaf(r.im, r.im, n2));
-    }
-    store_f32(xs, vh, i, xv);
-    store_f32(rs, vh, i, rv);
-  }
-  const double s = block_sum_f(n2);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-template <int PREC>
 __global__ void mixed_xpay_kernel(void *__restrict__ p, const float4 *__restrict__ rs, int64_t vh,
                                   const SolverScalars *S) {
   if (S->halt) return;
@@ -156,16 +125,6 @@ __global__ void mixed_after_update_kernel(const double *partials, int n, SolverS
 }
 
 static unsigned site_blocks(int64_t vh) { return (unsigned)((vh + kBlasThreads - 1) / kBlasThreads); }
-
-cudaError_t launch_mixed_update(int hop_prec, float4 *xs, float4 *rs, const void *p, const void *Ap,
-                                int64_t vh, const SolverScalars *S, double *partials, cudaStream_t s) {
-  note_launch();
-  if (hop_prec == PREC_F16N)
-    mixed_update_kernel<PREC_F16N><<<site_blocks(vh), kBlasThreads, 0, s>>>(xs, rs, p, Ap, vh, S, partials);
-  else
-    mixed_update_kernel<PREC_F32><<<site_blocks(vh), kBlasThreads, 0, s>>>(xs, rs, p, Ap, vh, S, partials);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_mixed_xpay(int hop_prec, void *p, const float4 *rs, int64_t vh,
                               const SolverScalars *S, cudaStream_t s) {

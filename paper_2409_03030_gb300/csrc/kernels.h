@@ -89,13 +89,8 @@ cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const flo
 // p = r + beta p (skipped when S->done)
 cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
                            cudaStream_t s);
-// y += x
-cudaError_t launch_dw_add(float4 *y, const float4 *x, int64_t n, cudaStream_t s);
 
 // ---- mixed precision (inner CG in FP32 or FP16+norm, even parity) ----------
-// x_s (FP32) += alpha p; r_s (FP32) -= alpha Ap; partials ||r_s||^2 (guarded by S->halt)
-cudaError_t launch_mixed_update(int hop_prec, float4 *xs, float4 *rs, const void *p, const void *Ap,
-                                int64_t vh, const SolverScalars *S, double *partials, cudaStream_t s);
 // p = r_s + beta p in the hop precision (guarded)
 cudaError_t launch_mixed_xpay(int hop_prec, void *p, const float4 *rs, int64_t vh,
                               const SolverScalars *S, cudaStream_t s);
