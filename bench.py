@@ -142,9 +142,11 @@ def peaks():
 
 # FP32 lane operations (add, mul or fma, each on one lane) per output site of
 # the plain double-word hop, counted from its arithmetic: per hop, projection
-# 6 x 9, link conjugation 9 x 2, mat-vec 2 x 3 x (2 x 28 + 8), reconstruction
-# 2 x 3 x 17 packed two-lane operations; epilogue 12 x 10; times 2 lanes.
-DW_HOP_LANE_OPS = 2 * (8 * (6 * 9 + 9 * 2 + 2 * 3 * (2 * 28 + 8) + 2 * 3 * 17) + 12 * 10)
+# 6 x 9, link conjugation 9 x 2, mat-vec 2 x 3 x (2 x 17 + 2) (offset-grid
+# sums: 5 + 6 + 6 per sum of three products, 2 to join A + iB) and
+# reconstruction 2 x 3 x 17 packed two-lane operations; epilogue 12 x 10
+# packed; times 2 lanes; plus the grid bounds, 2 x 5 + 1 scalar per hop.
+DW_HOP_LANE_OPS = 2 * (8 * (6 * 9 + 9 * 2 + 2 * 3 * (2 * 17 + 2) + 2 * 3 * 17) + 12 * 10) + 8 * (2 * 5 + 1)
 NOMINAL_HBM_GBS = 7900.0
 
 
@@ -703,15 +705,16 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32x2 (double-word, FP64-class)", "data": "synthetic",
             "config": workload_config(),
-            "roofline": {"bound": "alu", "achieved": round(alu_achieved, 2), "peak": round(alu_peak, 2),
-                         "unit": "Tops/s (FP32 lane operations)", "frac": round(alu_achieved / alu_peak, 4),
-                         "traffic": traffic, "kernel": "hop_dwp_kernel (double-word plain hop)",
-                         "ops_per_site": DW_HOP_LANE_OPS,
-                         "peak_kind": "SMs x 128 FP32 lanes x maximum SM clock",
-                         "hbm": {"achieved": round(dw_achieved, 1), "peak": hbm, "unit": "GB/s",
-                                 "frac": round(dw_achieved / hbm, 4),
-                                 "frac_nominal": round(dw_achieved / NOMINAL_HBM_GBS, 4),
-                                 "peak_kind": f"{peak_kind} copy bandwidth (burst); nominal 7.9 TB/s"}},
+            "roofline": {"bound": "hbm", "achieved": round(dw_achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(dw_achieved / hbm, 4), "traffic": traffic,
+                         "kernel": "hop_dwp_kernel (double-word plain hop)",
+                         "bytes_per_site": HOP_BYTES["dw"],
+                         "frac_nominal": round(dw_achieved / NOMINAL_HBM_GBS, 4),
+                         "peak_kind": f"{peak_kind} copy bandwidth (burst); nominal 7.9 TB/s",
+                         "alu": {"achieved": round(alu_achieved, 2), "peak": round(alu_peak, 2),
+                                 "unit": "Tops/s (FP32 lane operations)",
+                                 "frac": round(alu_achieved / alu_peak, 4), "ops_per_site": DW_HOP_LANE_OPS,
+                                 "peak_kind": "SMs x 128 FP32 lanes x maximum SM clock"}},
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 2), "unit": "GB/s",
                     "h2d_bytes_per_step": int(b.nbytes), "d2h_bytes_per_step": int(b.nbytes)},

@@ -174,7 +174,7 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
   for (int a = 0; a < 3; ++a) {
     const p2 col[3] = {M[0][a], M[1][a], M[2][a]};
     p2 Gc[3];
-    matvec_half_p(U, col, Gc);  // G_ia = sum_b U_ib M_ba
+    matvec_half_ts(U, col, Gc);  // G_ia = sum_b U_ib M_ba
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const p2 q = p2_norm(acc2_get(acc2_first(Fm, p2_norm(Gc[i]))));

@@ -3,28 +3,47 @@
 //
 // Every complex double-word operation runs its real and imaginary lanes in
 // one fma/add/mul.rn.f32x2: projection and reconstruction by sign-carrying
-// TwoSums, the SU(3) product W h = h.re W + i (h.im W) as compensated sums
-// with broadcast half-spinor multipliers.  (Folding the link's signs into the
+// TwoSums, the SU(3) product W h = h.re W + i (h.im W) as sums of exact
+// products on a fixed offset grid with broadcast half-spinor multipliers.  (Folding the link's signs into the
 // multipliers instead saves FP32 multiplies but costs registers: the kernel
 // then spills and runs slower on sm_103.)
 //
-// Neighbour spinors of the next hop are prefetched into shared memory with
-// cp.async (two stages, chunk-major [k][thread], each thread touching only
-// its own column); links are loaded straight into registers ahead of use.
+// Neighbour spinors and links of the next hop are prefetched into shared
+// memory with cp.async (chunk-major [k][thread], each thread touching only
+// its own column).
 #pragma once
 #include "dw2.cuh"
 #include "hop_dw.cuh"
 
 namespace jqcd {
 
-constexpr int kDwpStageChunks = 12;  // one double-word spinor per thread and stage
-constexpr size_t kDwpSmem = 2ull * kDwpStageChunks * kHopThreads * 16;
+constexpr int kDwpStageChunks = 12;  // one double-word spinor per thread
+constexpr int kDwpLinkChunks = 9;    // one double-word link per thread and stage
+// one neighbour-spinor stage and two link stages, chunk-major [k][thread]
+constexpr size_t kDwpSmem = (size_t)(kDwpStageChunks + 2 * kDwpLinkChunks) * kHopThreads * 16;
 
-// Issue the copies of the neighbour spinor of one hop into a stage.
+// Issue the copies of the neighbour spinor of one hop into its stage.
 __device__ __forceinline__ void stage_hop_p(float4 *st, const float4 *in, int64_t vh, int64_t nb) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int k = 0; k < 12; ++k) cp_async16(st + k * kHopThreads + tid, in + k * vh + nb, true);
+}
+
+// Issue the copies of the link of hop d (mu = d/2, backward when d is odd)
+// into a link stage, element (a, b) at chunk 3a + b: U_mu(x) for a forward
+// hop, the transpose of U_mu(x - mu) (conjugated at use) for a backward one.
+__device__ __forceinline__ void stage_link_p(float4 *st, const float4 *gauge, int64_t vh, int p, int d,
+                                             int64_t idx, int64_t nb) {
+  const int tid = threadIdx.x;
+  const int mu = d >> 1;
+  const bool bwd = (d & 1) != 0;
+  const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
+  const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      cp_async16(st + (a * 3 + b) * kHopThreads + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
 }
 
 __device__ __forceinline__ p2 ld_p2(const float4 *p) {
@@ -46,13 +65,10 @@ __device__ __forceinline__ void project_p(const p2 (&psi)[4][3], p2 (&h)[2][3], 
   }
 }
 
-// r[a] = sum_b W_ab h[b] = A + i B with A = sum_b h.re W_ab and
-// B = sum_b h.im W_ab for one spin of the half-spinor: two compensated sums
-// of exact products against the same link lanes (half-spinor components
-// broadcast to both lanes), joined by one TwoSum with B's lanes swapped and
-// its new real lane negated.  No copy of i W is formed, which keeps 36
-// registers free.
-__device__ __forceinline__ void matvec_half_p(const p2 (&W)[3][3], const p2 (&h)[3], p2 (&r)[3]) {
+// r[a] = sum_b W_ab h[b] with TwoSum-compensated sums of exact products
+// (twelve packed operations per product, error about 2^-48 |W||h|): the
+// accumulation of the staggered hop and of the force kernel.
+__device__ __forceinline__ void matvec_half_ts(const p2 (&W)[3][3], const p2 (&h)[3], p2 (&r)[3]) {
   mul2 mr[3], mi[3];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
@@ -71,6 +87,85 @@ __device__ __forceinline__ void matvec_half_p(const p2 (&W)[3][3], const p2 (&h)
     // i B = (-B.im, B.re): swap the lanes, flip the sign of lane 0
     constexpr f2 kLane0 = 0x0000000080000000ull;
     r[a] = p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0});
+  }
+}
+
+// Largest |component| of the link's high words, the bound its products need.
+__device__ __forceinline__ float link_max_hi(const p2 (&W)[3][3]) {
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    float u, v;
+    f2_split(W[k / 3][k % 3].h, u, v);
+    m = fmaxf(m, fmaxf(fabsf(u), fabsf(v)));
+  }
+  return m;
+}
+
+// One exact-product step of an offset-grid sum: T = T0 + (partial sum) stays
+// in the binade [sigma, 2 sigma), so the fma rounds the exact high product
+// onto that binade's fixed grid, T - T_new is exact (Sterbenz lemma) and one
+// more fma returns the part of the product below the grid to the low-order
+// sum c, together with the two cross products of the low words.
+__device__ __forceinline__ void grid_mad(f2 &T, f2 &c, const mul2 &A, p2 B, bool first) {
+  const f2 Tn = f2_fma(A.h, B.h, T);
+  const f2 d = f2_fma(A.h, B.h, f2_sub(T, Tn));  // product - (Tn - T), rounded
+  f2 t = first ? d : f2_add(c, d);
+  t = f2_fma(A.h, B.l, t);
+  c = f2_fma(A.l, B.h, t);
+  T = Tn;
+}
+
+// r[a] = sum_b W_ab h[b] = A + i B with A = sum_b h.re W_ab and
+// B = sum_b h.im W_ab for one spin of the half-spinor (half-spinor
+// components broadcast to both lanes against the same link lanes).  Both
+// sums run on one fixed grid: sigma is a power of two with every partial sum
+// below sigma/2 in magnitude (bound wmax * max(sum_b |h_b.re|, sum_b |h_b.im|),
+// raised by 2^-19 to cover its own rounding and that of the grid steps); A
+// starts at (T0, T0) and B at (-T0, T0), T0 = 1.5 sigma, so every
+// accumulator lane stays in a binade of magnitude [sigma, 2 sigma).  The
+// high words of A + i B = (A.re - B.im, A.im + B.re) are then differences of
+// two such lanes with the offsets cancelling: exact, multiples of the grid
+// step below sigma in magnitude.  The low words carry everything below the
+// grid.  Six packed
+// operations per product instead of the twelve of a TwoSum accumulation; the
+// low words are coarser (about 2^-48 sigma per operation), giving a
+// relative error of a few 1e-14 per product W h.
+__device__ __forceinline__ void matvec_half_p(const p2 (&W)[3][3], float wmax, const p2 (&h)[3],
+                                              p2 (&r)[3]) {
+  mul2 mr[3], mi[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    mr[b] = mul2{f2_lo(h[b].h), f2_lo(h[b].l)};
+    mi[b] = mul2{f2_hi(h[b].h), f2_hi(h[b].l)};
+  }
+  f2 TA0, TB0;
+  {
+    float r0, i0, r1, i1, r2, i2;
+    f2_split(h[0].h, r0, i0);
+    f2_split(h[1].h, r1, i1);
+    f2_split(h[2].h, r2, i2);
+    const float sr = fabsf(r0) + fabsf(r1) + fabsf(r2);
+    const float si = fabsf(i0) + fabsf(i1) + fabsf(i2);
+    const float m = fmaxf(sr, si) * wmax;
+    // sigma = 2^(e + 2) for m in [2^e, 2^(e+1)); T0 = 1.5 sigma
+    const unsigned tb = (__float_as_uint(m) & 0x7f800000u) + (2u << 23) + (1u << 22);
+    const float t0 = __uint_as_float(tb);
+    TA0 = f2_make(t0, t0);
+    TB0 = f2_make(-t0, t0);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    f2 TA = TA0, TB = TB0, cA = 0ull, cB = 0ull;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      grid_mad(TA, cA, mr[b], W[a][b], b == 0);
+      grid_mad(TB, cB, mi[b], W[a][b], b == 0);
+    }
+    // i B = (-B.im, B.re): swap the lanes, flip the sign of lane 0; the high
+    // lanes are (T0 + A.re) - (T0 + B.im) and (T0 + A.im) + (-T0 + B.re)
+    constexpr f2 kLane0 = 0x0000000080000000ull;
+    r[a] = p2{f2_add(TA, f2_swap(TB) ^ kLane0), f2_add(cA, f2_swap(cB) ^ kLane0)};
   }
 }
 
@@ -102,8 +197,13 @@ __device__ __forceinline__ void reconstruct_half_mu(int mu, const p2 (&r)[3], p2
 
 // acc = (H_{p,1-p} in)(idx) for output site idx of parity p (DAG: the
 // adjoint hop), unnormalised double-word accumulators.  dsm: this block's
-// 2 * kDwpStageChunks * kHopThreads chunks of shared memory; blockDim.x must
-// be kHopThreads.
+// kDwpSmem bytes of shared memory; blockDim.x must be kHopThreads.
+//
+// Copies run one hop ahead: the links of hop d + 1 are issued when hop d
+// starts (two link stages), the neighbour spinor of hop d + 1 as soon as hop
+// d's has been read into registers and projected (one stage).  Every thread
+// reads and overwrites only its own column, so no block barrier is needed;
+// the completed-group wait of each hop covers both of its copies.
 template <bool DAG>
 __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, const float4 *gauge,
                                              const Geom &g, int p, int64_t idx, p2 (&acc)[4][3]) {
@@ -115,9 +215,11 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[a][c] = p2{0ull, 0ull};
   const int tid = threadIdx.x;
+  float4 *const lnk = dsm + kDwpStageChunks * kHopThreads;  // two link stages
   bool neg_next;
   int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
   stage_hop_p(dsm, in, vh, nb);
+  stage_link_p(lnk, gauge, vh, p, 0, idx, nb);
   cp_async_commit();
 #pragma unroll 1
   for (int d = 0; d < 8; ++d) {
@@ -125,28 +227,21 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
     const int mu = d >> 1;
     const bool bwd = (d & 1) != 0;
     const f2 cc = f2_make(1.f, bwd ? -1.f : 1.f);  // conjugation of the adjoint link
-    p2 W[3][3];
-    {  // link straight to registers, ahead of its use
-      const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 9) * vh + (bwd ? nb : idx);
-      const int sa = bwd ? 1 : 3, sb = bwd ? 3 : 1;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2 *>(L + (int64_t)(a * sa + b * sb) * vh));
-          W[a][b] = p2{v.x, v.y};
-        }
-    }
-    if (d < 7) {
+    if (d < 7) {  // the other link stage was read during hop d - 1
       nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-      stage_hop_p(dsm + ((d + 1) & 1) * kDwpStageChunks * kHopThreads, in, vh, nb);
+      stage_link_p(lnk + ((d + 1) & 1) * kDwpLinkChunks * kHopThreads, gauge, vh, p, d + 1, idx, nb);
     }
     cp_async_commit();
-    cp_async_wait1();  // this thread's copies of hop d have landed
-    const float4 *st = dsm + (d & 1) * kDwpStageChunks * kHopThreads + tid;
+    cp_async_wait1();  // this thread's spinor and link copies of hop d have landed
     p2 psi[4][3];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(st + k * kHopThreads);
+    for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(dsm + k * kHopThreads + tid);
+    p2 W[3][3];
+    {
+      const float4 *ls = lnk + (d & 1) * kDwpLinkChunks * kHopThreads + tid;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = ld_p2(ls + k * kHopThreads);
+    }
     const float S = (bwd != DAG) ? 1.f : -1.f;
     p2 h[2][3];
     switch (mu) {
@@ -155,6 +250,8 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
       case 2: project_p<2>(psi, h, S); break;
       default: project_p<3>(psi, h, S);
     }
+    if (d < 7) stage_hop_p(dsm, in, vh, nb);  // the spinor stage has been read
+    cp_async_commit();
     if (neg) {
       const f2 mm = f2_make(-1.f, -1.f);
 #pragma unroll
@@ -164,11 +261,13 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
     }
 #pragma unroll
     for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
+    // bound of the link's high words, raised by 2^-19 (see matvec_half_p)
+    const float wmax = link_max_hi(W) * 1.0000019f;
     {  // spin 0 of the half-spinor, then spin 1: one three-colour result live
       p2 r[3];
-      matvec_half_p(W, h[0], r);
+      matvec_half_p(W, wmax, h[0], r);
       reconstruct_half_mu<0>(mu, r, acc, S);
-      matvec_half_p(W, h[1], r);
+      matvec_half_p(W, wmax, h[1], r);
       reconstruct_half_mu<1>(mu, r, acc, S);
     }
   }

@@ -75,7 +75,7 @@ __device__ __forceinline__ void stag_hop_sum(const Geom &g, int p, int64_t cb, c
       for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
     }
     p2 r[3];
-    matvec_half_p(W, h, r);
+    matvec_half_ts(W, h, r);
     // sign: eta, boundary, +forward / -backward, and -1 for the adjoint
     float sg = stag_eta(mu, x, y, z) * (neg ? -1.f : 1.f) * (bwd ? -1.f : 1.f);
     if (DAG) sg = -sg;
