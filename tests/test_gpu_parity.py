@@ -93,6 +93,54 @@ def test_hop_vs_oracle(jq, dims, prec, dagger):
     g.free()
 
 
+@pytest.mark.parametrize("case", ["nonunitary", "scaled_up", "scaled_down", "mixed_scales", "zero_block"])
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_hop_dw_magnitudes(jq, case, dagger):
+    """Double-word hop at inputs that stress its offset-grid SU(3) sums, whose
+    grid step is set per site and hop from max|link| and the half-spinor's
+    magnitude: link components far above 1 (general complex matrices), spinors
+    scaled by 2^60 and 2^-60, neighbours 2^80 apart in one launch (time slices
+    0-3 at 2^40, 4-7 at 2^-40), and an all-zero region, whose outputs must be
+    exact zeros.  Sites whose 8 neighbours share one scale are compared
+    against the oracle per scale class, at the double-word gate."""
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 8)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=31)
+    psi = synth.gaussian_spinor(dims, seed=32)
+    if case == "nonunitary":
+        rng = np.random.default_rng(33)
+        U = 3.0 * (rng.normal(size=U.shape) + 1j * rng.normal(size=U.shape))
+    elif case == "scaled_up":
+        psi = psi * 2.0 ** 60
+    elif case == "scaled_down":
+        psi = psi * 2.0 ** -60
+    elif case in ("mixed_scales", "zero_block"):
+        t = np.arange(dims[3])[None, :, None, None, None, None]
+        low = 0.0 if case == "zero_block" else 2.0 ** -40
+        psi = psi * np.where(t < 4, 2.0 ** 40, low)
+    g = ctx.gauge_upload(dims, U, t_antiperiodic=True)
+    pe, po = g.pack(psi, 0)
+    for p in (0, 1):
+        want = oracle.hop(dims, U, psi, dagger=bool(dagger), out_parity=p)
+        out = g.empty(0)
+        g.dslash_eo(0, p, dagger, po if p == 0 else pe, None, out, 0.0, 1.0)
+        ev = out if p == 0 else g.empty(0).zero_()
+        od = out if p == 1 else g.empty(0).zero_()
+        got = only_parity(dims, g.unpack(ev, od, 0), p)
+        if case in ("mixed_scales", "zero_block"):
+            for ts in ((1, 2), (5, 6)):  # output slices whose neighbours share one scale
+                sl = (slice(None), slice(ts[0], ts[1] + 1))
+                if case == "zero_block" and ts == (5, 6):
+                    assert np.all(got[sl] == 0)
+                    continue
+                assert rel(got[sl], want[sl]) <= TOL[0], (p, ts, rel(got[sl], want[sl]))
+            # slices on a scale boundary: error against the large scale
+            assert np.linalg.norm((got - want).ravel()) <= TOL[0] * np.linalg.norm(want.ravel())
+        else:
+            assert rel(got, want) <= TOL[0], (p, rel(got, want))
+    g.free()
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 10)])
 @pytest.mark.parametrize("prec", PRECS)
 def test_mdagm_vs_oracle(jq, dims, prec):
