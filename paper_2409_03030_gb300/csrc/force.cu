@@ -15,7 +15,7 @@
 // products, h_s conj(w_s)^T, with h the projected half-spinor of X and
 // w_s = Y_s + conj-phase * Y_alpha for the lower spins alpha that map to s.
 // Arithmetic: the packed two-lane double-word operations of the hop
-// (compensated sums of exact products, hop_dwp.cuh).
+// (sums of exact products on a fixed offset grid, hop_dwp.cuh).
 #include <cuda_runtime.h>
 
 #include "fields.cuh"
@@ -31,7 +31,14 @@ namespace {
 
 constexpr int kForceThreads = 128;
 constexpr int kForceOwnChunks = 24;  // X and Y of the thread's own site
-constexpr size_t kForceSmem = (size_t)kForceOwnChunks * kForceThreads * 16;  // 48 KB
+constexpr int kForceNbChunks = 12;   // the neighbour spinor of the next part
+constexpr size_t kForceSmem = (size_t)(kForceOwnChunks + kForceNbChunks) * kForceThreads * 16;  // 72 KB
+
+// Issue the copies of one double-word spinor of site i into a stage column.
+__device__ __forceinline__ void stage_spinor_force(float4 *st, const float4 *f, int64_t vh, int64_t i) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) cp_async16(st + k * kForceThreads, f + k * vh + i, false);
+}
 
 // a + phase<PH> b for complex double-word pairs (PH: 0 -> 1, 1 -> i, 2 -> -1,
 // 3 -> -i); i b = (-b.im, b.re).
@@ -61,15 +68,6 @@ __device__ __forceinline__ void adjoint_half_p(const p2 (&y)[4][3], p2 (&w)[2][3
   for (int c = 0; c < 3; ++c) {
     w[T::k2][c] = p2_add_phase<C2>(w[T::k2][c], y[2][c]);
     w[T::k3][c] = p2_add_phase<C3>(w[T::k3][c], y[3][c]);
-  }
-}
-
-__device__ __forceinline__ void load_dw_spinor_p(const float4 *base, int64_t vh, int64_t i, p2 (&s)[4][3]) {
-  const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(base) + i;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    const ulonglong2 v = __ldg(q + k * vh);
-    s[k / 3][k % 3] = p2{v.x, v.y};
   }
 }
 
@@ -117,10 +115,14 @@ struct FieldPair {
 // once in the instruction stream (the per-direction copies overflowed the
 // instruction cache).
 // own: this thread's column of the block's shared memory, X(x) in chunks
-// 0..11 and Y(x) in chunks 12..23 (stride kForceThreads).
+// 0..11 and Y(x) in chunks 12..23 (stride kForceThreads).  nst: the column of
+// the neighbour stage, holding X(x + mu) (copies issued by the caller or the
+// previous direction) when the call starts; Y(x + mu) is copied in during
+// part 0 and X(x + mu + 1) during part 1, each as soon as the stage has been
+// read.
 __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int x, int y, int z, int t, int mu,
-                                           const FieldPair &F, const float4 *own, const float4 *gauge,
-                                           float2 two_kappa, float4 *out) {
+                                           const FieldPair &F, const float4 *own, float4 *nst,
+                                           const float4 *gauge, float2 two_kappa, float4 *out) {
   const int64_t vh = g.vh;
   bool neg;
   const int64_t nb = hop_neighbour(g, x, y, z, t, 2 * mu, neg);  // x + mu, parity 1-p
@@ -132,7 +134,16 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
     p2 v[2][3], c[2][3];
     {
       p2 s4[4][3];
-      load_dw_spinor_p(part ? Yn : Xn, vh, nb, s4);
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // only this thread's column is read
+#pragma unroll
+      for (int k = 0; k < 12; ++k) s4[k / 3][k % 3] = ld_p2(nst + k * kForceThreads);
+      if (part == 0) {
+        stage_spinor_force(nst, Yn, vh, nb);
+      } else if (mu < 3) {
+        bool neg1;
+        stage_spinor_force(nst, Xn, vh, hop_neighbour(g, x, y, z, t, 2 * mu + 2, neg1));
+      }
+      cp_async_commit();
       if (part) adjoint_rt(mu, 1, s4, v);
       else project_rt(mu, s4, v, -1.f);
       {
@@ -143,16 +154,45 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
       if (part) project_rt(mu, s4, c, 1.f);
       else adjoint_rt(mu, -1, s4, c);
     }
+    // One offset grid for the part's nine entries (as in matvec_half_p): every
+    // partial sum is below max|v.hi| * max_a max(|c_0a.re| + |c_1a.re|,
+    // |c_0a.im| + |c_1a.im|), raised by 2^-19, and sigma is the power of two
+    // above twice that; A starts at (1.5 sigma, 1.5 sigma), B at
+    // (-1.5 sigma, 1.5 sigma).
+    f2 TA0, TB0;
+    {
+      float vm = 0.f, cm = 0.f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float u, w;
+        f2_split(v[k / 3][k % 3].h, u, w);
+        vm = fmaxf(vm, fmaxf(fabsf(u), fabsf(w)));
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        float r0, i0, r1, i1;
+        f2_split(c[0][a].h, r0, i0);
+        f2_split(c[1][a].h, r1, i1);
+        cm = fmaxf(cm, fmaxf(fabsf(r0) + fabsf(r1), fabsf(i0) + fabsf(i1)));
+      }
+      const float m = vm * cm * 1.0000019f;
+      const float t0 = __uint_as_float((__float_as_uint(m) & 0x7f800000u) + (2u << 23) + (1u << 22));
+      TA0 = f2_make(t0, t0);
+      TB0 = f2_make(-t0, t0);
+    }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const mul2 r0 = conj_re(c[0][a]), r1 = conj_re(c[1][a]);
       const mul2 i0 = conj_im(c[0][a]), i1 = conj_im(c[1][a]);
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        acc2 A = acc2_first(r0, v[0][b]), B = acc2_first(i0, v[0][b]);
-        acc2_mad(A, r1, v[1][b]);
-        acc2_mad(B, i1, v[1][b]);
-        const p2 P = p2_norm(p2_add(acc2_get(A), p2{f2_swap(B.s) ^ kLane0, f2_swap(B.c) ^ kLane0}));
+        f2 TA = TA0, TB = TB0, cA = 0ull, cB = 0ull;
+        grid_mad(TA, cA, r0, v[0][b], true);
+        grid_mad(TA, cA, r1, v[1][b], false);
+        grid_mad(TB, cB, i0, v[0][b], true);
+        grid_mad(TB, cB, i1, v[1][b], false);
+        // A + i B; the offsets cancel exactly in the high words
+        const p2 P{f2_add(TA, f2_swap(TB) ^ kLane0), f2_add(cA, f2_swap(cB) ^ kLane0)};
         M[b][a] = part ? p2_norm(p2_add(M[b][a], P)) : P;
       }
     }
@@ -166,6 +206,7 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
       U[k / 3][k % 3] = p2{v.x, v.y};
     }
   }
+  const float umax = link_max_hi(U) * 1.0000019f;  // bound of the grid mat-vec
   const float fs = neg ? -1.f : 1.f;  // boundary sign, exact
   const f2 fh = f2_make(fs * two_kappa.x, fs * two_kappa.x);
   const mul2 Fm{fh, f2_make(fs * two_kappa.y, fs * two_kappa.y)};
@@ -174,7 +215,7 @@ __device__ __forceinline__ void force_link(const Geom &g, int p, int64_t cb, int
   for (int a = 0; a < 3; ++a) {
     const p2 col[3] = {M[0][a], M[1][a], M[2][a]};
     p2 Gc[3];
-    matvec_half_ts(U, col, Gc);  // G_ia = sum_b U_ib M_ba
+    matvec_half_p(U, umax, col, Gc);  // G_ia = sum_b U_ib M_ba
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
       const p2 q = p2_norm(acc2_get(acc2_first(Fm, p2_norm(Gc[i]))));
@@ -197,17 +238,18 @@ __global__ void __launch_bounds__(kForceThreads, 3) force_kernel(Geom g, FieldPa
   const int64_t cb = q - (int64_t)p * g.vh;
   const float4 *Xh = p ? F.xo : F.xe, *Yh = p ? F.yo : F.ye;
   float4 *own = fsm + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    cp_async16(own + k * kForceThreads, Xh + k * g.vh + cb, false);
-    cp_async16(own + (12 + k) * kForceThreads, Yh + k * g.vh + cb, false);
-  }
-  cp_async_commit();
+  float4 *nst = fsm + kForceOwnChunks * kForceThreads + threadIdx.x;
   int x, y, z, t;
   cb_coords(g, cb, p, x, y, z, t);
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // only this thread's column is read
+  stage_spinor_force(own, Xh, g.vh, cb);
+  stage_spinor_force(own + 12 * kForceThreads, Yh, g.vh, cb);
+  {
+    bool neg0;
+    stage_spinor_force(nst, p ? F.xe : F.xo, g.vh, hop_neighbour(g, x, y, z, t, 0, neg0));  // X(x + 0)
+  }
+  cp_async_commit();
 #pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) force_link(g, p, cb, x, y, z, t, mu, F, own, gauge, two_kappa, out);
+  for (int mu = 0; mu < 4; ++mu) force_link(g, p, cb, x, y, z, t, mu, F, own, nst, gauge, two_kappa, out);
 }
 
 // out = gamma5 in on a whole-lattice double-word spinor (chunks k = 3*spin + c;
@@ -271,6 +313,13 @@ __global__ void linkfield_unpack_kernel(Geom g, const float4 *__restrict__ dwf, 
 cudaError_t launch_fermi_force(const Geom &g, const float4 *xe, const float4 *xo, const float4 *ye,
                                const float4 *yo, const float4 *gauge_dw, double kappa, float4 *out,
                                cudaStream_t s) {
+  static bool configured = false;  // 72 KB of dynamic shared memory needs the opt-in
+  if (!configured) {
+    const cudaError_t e = cudaFuncSetAttribute(force_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)kForceSmem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   note_launch();
   const float2 tk = dw_split_host(2.0 * kappa);
   force_kernel<<<(unsigned)((2 * g.vh + kForceThreads - 1) / kForceThreads), kForceThreads, kForceSmem, s>>>(

@@ -67,7 +67,7 @@ __device__ __forceinline__ void project_p(const p2 (&psi)[4][3], p2 (&h)[2][3], 
 
 // r[a] = sum_b W_ab h[b] with TwoSum-compensated sums of exact products
 // (twelve packed operations per product, error about 2^-48 |W||h|): the
-// accumulation of the staggered hop and of the force kernel.
+// accumulation of the staggered hop, which is bound by HBM bandwidth.
 __device__ __forceinline__ void matvec_half_ts(const p2 (&W)[3][3], const p2 (&h)[3], p2 (&r)[3]) {
   mul2 mr[3], mi[3];
 #pragma unroll
