@@ -41,7 +41,19 @@ __device__ __forceinline__ dw dw_from_double(double v) {
 
 __device__ __forceinline__ double sum_partials(const double *partials, int n) {
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v += partials[i];
+  // all of a thread's loads are in flight before its first add; the adds keep
+  // the fixed order i = tid, tid + blockDim.x, ... (out-of-range slots add 0)
+  constexpr int kU = 16;
+  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
+    double t[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * (int)blockDim.x;
+      t[u] = i < n ? partials[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v += t[u];
+  }
   return block_sum_d(v);
 }
 

@@ -259,12 +259,29 @@ __global__ void stag_xpay_norm_kernel(float4 *__restrict__ p, const float4 *__re
 // alpha = ||r||^2 / <p, (m^2 - D_eo D_oe) p> with <p, A p> = m^2 ||p||^2 + ||D_oe p||^2
 // (D_eo^dag = -D_oe): the two norms come as per-block partials of the first
 // hop (pt) and of the p update (pp); breakdown when the sum is not positive.
+// This thread's share of sum(a[0..n)) in the fixed order i = tid, tid +
+// blockDim.x, ...; all of its loads are in flight before its first add
+// (out-of-range slots add 0).
+__device__ __forceinline__ double thread_sum(const double *a, int n) {
+  constexpr int kU = 16;
+  double v = 0.0;
+  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
+    double t[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * (int)blockDim.x;
+      t[u] = i < n ? a[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v += t[u];
+  }
+  return v;
+}
+
 __global__ void stag_alpha_kernel(const double *pt, int nt, const double *pp, int np, double m2,
                                   SolverScalars *S) {
   if (S->halt) return;
-  double vt = 0.0, vp = 0.0;
-  for (int i = threadIdx.x; i < nt; i += blockDim.x) vt += pt[i];
-  for (int i = threadIdx.x; i < np; i += blockDim.x) vp += pp[i];
+  double vt = thread_sum(pt, nt), vp = thread_sum(pp, np);
   vt = block_sum_d(vt);
   vp = block_sum_d(vp);
   if (threadIdx.x == 0) {
