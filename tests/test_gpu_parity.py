@@ -93,6 +93,27 @@ def test_hop_vs_oracle(jq, dims, prec, dagger):
     g.free()
 
 
+@pytest.mark.parametrize("mode", ["dw", "mixed_f16"])
+def test_solve_bitwise_repeatable(jq, mode):
+    """Reductions are fixed-order (per-block partials, then one single-block
+    pass that issues all of a thread's loads before adding them in order), so
+    the same solve run twice gives bit-identical solutions, iteration counts
+    and residuals.  16^3x64: 1024 hop-block partials, four per thread in the
+    single-block pass."""
+    jqcd, ctx = jq
+    dims = (16, 16, 16, 64)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=81)
+    b = synth.gaussian_spinor(dims, seed=82)
+    g = ctx.gauge_upload(dims, U)
+    x1, i1, s1 = g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[mode])
+    x2, i2, s2 = g.cg_solve(b, 0.12, tol=1e-10, mode=jqcd.MODES[mode])
+    assert s1 == 0 and s2 == 0
+    assert i1["iters"] == i2["iters"] and i1["reliable_updates"] == i2["reliable_updates"]
+    assert i1["true_rel_resid"] == i2["true_rel_resid"] and i1["true_rel_resid"] <= 1e-10
+    assert np.array_equal(x1, x2)
+    g.free()
+
+
 @pytest.mark.parametrize("case", ["nonunitary", "scaled_up", "scaled_down", "mixed_scales", "zero_block"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_hop_dw_magnitudes(jq, case, dagger):
