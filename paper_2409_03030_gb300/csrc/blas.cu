@@ -8,6 +8,7 @@
 
 #include "dw.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -92,6 +93,7 @@ __global__ void dw_cg_update_kernel(float4 *__restrict__ x, float4 *__restrict__
 
 __global__ void dw_xpay_kernel(float4 *__restrict__ p, const float4 *__restrict__ r, int64_t n,
                                const SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -132,6 +134,7 @@ __global__ void finalize_sum_kernel(const double *partials, int n, double *out) 
 }
 
 __global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const double pAp = sum_partials(partials, n);
   if (threadIdx.x == 0) {
@@ -151,6 +154,7 @@ __global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S)
 }
 
 __global__ void cg_beta_kernel(const double *partials, int n, SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const double rr_new = sum_partials(partials, n);
   if (threadIdx.x == 0) {
@@ -223,18 +227,15 @@ cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const flo
 cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
                            cudaStream_t s) {
   note_launch();
-  dw_xpay_kernel<<<blas_blocks(n), kBlasThreads, 0, s>>>(p, r, n, S);
-  return cudaGetLastError();
+  return launch_pdl(dw_xpay_kernel, blas_blocks(n), kBlasThreads, 0, s, p, r, n, S);
 }
 cudaError_t launch_cg_alpha(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
   note_launch();
-  cg_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
-  return cudaGetLastError();
+  return launch_pdl(cg_alpha_kernel, 1, kReduceThreads, 0, s, partials, n, S);
 }
 cudaError_t launch_cg_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
   note_launch();
-  cg_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
-  return cudaGetLastError();
+  return launch_pdl(cg_beta_kernel, 1, kReduceThreads, 0, s, partials, n, S);
 }
 cudaError_t launch_cg_start(const double *partials, int n, SolverScalars *S, double tol2,
                             int max_iters, double delta2, cudaStream_t s) {

@@ -13,6 +13,7 @@
 
 #include "fields.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -28,6 +29,7 @@ __device__ __forceinline__ void store_f32(float4 *base, int64_t vh, int64_t i, c
 template <int PREC>
 __global__ void mixed_xpay_kernel(void *__restrict__ p, const float4 *__restrict__ rs, int64_t vh,
                                   const SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const float b = S->beta_f;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -99,6 +101,7 @@ __device__ __forceinline__ double sum_partials_m(const double *partials, int n) 
 }
 
 __global__ void mixed_beta_kernel(const double *partials, int n, SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const double rr_new = sum_partials_m(partials, n);
   if (threadIdx.x == 0) {
@@ -142,10 +145,9 @@ cudaError_t launch_mixed_xpay(int hop_prec, void *p, const float4 *rs, int64_t v
                               const SolverScalars *S, cudaStream_t s) {
   note_launch();
   if (hop_prec == PREC_F16N)
-    mixed_xpay_kernel<PREC_F16N><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh, S);
+    return launch_pdl(mixed_xpay_kernel<PREC_F16N>, site_blocks(vh), kBlasThreads, 0, s, p, rs, vh, S);
   else
-    mixed_xpay_kernel<PREC_F32><<<site_blocks(vh), kBlasThreads, 0, s>>>(p, rs, vh, S);
-  return cudaGetLastError();
+    return launch_pdl(mixed_xpay_kernel<PREC_F32>, site_blocks(vh), kBlasThreads, 0, s, p, rs, vh, S);
 }
 
 cudaError_t launch_mixed_copy(int hop_prec, void *p, const float4 *rs, int64_t vh, cudaStream_t s) {
@@ -171,8 +173,7 @@ cudaError_t launch_dw_add_f32(float4 *x, float4 *xs, int64_t vh, cudaStream_t s)
 
 cudaError_t launch_mixed_beta(const double *partials, int n, SolverScalars *S, cudaStream_t s) {
   note_launch();
-  mixed_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, n, S);
-  return cudaGetLastError();
+  return launch_pdl(mixed_beta_kernel, 1, kReduceThreads, 0, s, partials, n, S);
 }
 
 cudaError_t launch_mixed_after_update(const double *partials, int n, SolverScalars *S,

@@ -12,6 +12,7 @@
 #include "fields.cuh"
 #include "hop.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "hop_dw.cuh"
 #include "hop_dwp.cuh"
 #include "hop_lp.cuh"
@@ -72,6 +73,7 @@ template <int PREC, bool DAG, bool AXPY, bool NORM>
 __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
   typedef PT<PREC> T;
   typedef typename T::C C;
+  pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = idx < P.g.vh;
@@ -119,6 +121,7 @@ template <int PREC, bool DAG, bool AXPY, bool NORM>
 __global__ void __launch_bounds__(kHopThreads) hop_lp_kernel(const HopParams P) {
   typedef PT<PREC> T;
   extern __shared__ float4 lsm[];
+  pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   dwacc nrm{0.f, 0.f};
@@ -158,10 +161,10 @@ static cudaError_t launch_hop_t(const HopParams &P, cudaStream_t s) {
   // FP16: staged (measured faster); FP32: plain loads (its six-chunk stages
   // cost more occupancy than the prefetch gains); FP64: plain.
   if (PREC == PREC_F16N)
-    hop_lp_kernel<PREC_F16N, DAG, AXPY, NORM><<<blocks, kHopThreads, lp_stage_smem<PREC_F16N>(), s>>>(P);
+    return launch_pdl(hop_lp_kernel<PREC_F16N, DAG, AXPY, NORM>, blocks, kHopThreads,
+                      lp_stage_smem<PREC_F16N>(), s, P);
   else
-    hop_kernel<PREC, DAG, AXPY, NORM><<<blocks, kHopThreads, 0, s>>>(P);
-  return cudaGetLastError();
+    return launch_pdl(hop_kernel<PREC, DAG, AXPY, NORM>, blocks, kHopThreads, 0, s, P);
 }
 
 template <int PREC>
@@ -191,6 +194,7 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
 template <bool DAG, bool AXPY, bool NORM>
 __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kernel(const HopParams P) {
   extern __shared__ float4 dsm[];
+  pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   dwacc nrm{0.f, 0.f};
@@ -217,8 +221,7 @@ static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P);
-  return cudaGetLastError();
+  return launch_pdl(kern, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P);
 }
 
 static cudaError_t launch_hop_dw(const HopParams &P, bool dag, bool axpy, bool norm, cudaStream_t s) {

@@ -15,6 +15,7 @@
 #include "hop_dwp.cuh"
 #include "hop_lp.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "solver.h"
 
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(kHopThreads, 3)
     hop_dwp_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
                       float4 *__restrict__ r, const float2 *__restrict__ alpha) {
   extern __shared__ float4 dsm[];
+  pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   dwacc nrm{0.f, 0.f};
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(kHopThreads)
                      float4 *__restrict__ rs, const SolverScalars *__restrict__ S) {
   typedef PT<PREC> T;
   extern __shared__ float4 lsm[];
+  pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   float n2 = 0.f;
@@ -127,8 +130,8 @@ __global__ void __launch_bounds__(kHopThreads)
 template <int PREC>
 cudaError_t launch_lp_cg_t(const HopParams &P, const void *p, float4 *xs, float4 *rs,
                            const SolverScalars *S, cudaStream_t s) {
-  hop_lp_cg_kernel<PREC><<<hop_blocks(P.g.vh), kHopThreads, lp_stage_smem<PREC>(), s>>>(P, p, xs, rs, S);
-  return cudaGetLastError();
+  return launch_pdl(hop_lp_cg_kernel<PREC>, hop_blocks(P.g.vh), kHopThreads, lp_stage_smem<PREC>(), s, P, p,
+                    xs, rs, S);
 }
 
 }  // namespace
@@ -154,8 +157,7 @@ static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  hop_dwp_cg_kernel<XUPD><<<hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s>>>(P, p, x, r, alpha);
-  return cudaGetLastError();
+  return launch_pdl(hop_dwp_cg_kernel<XUPD>, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P, p, x, r, alpha);
 }
 
 cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,
