@@ -25,6 +25,7 @@
 #include "dw.cuh"
 #include "kernels.h"
 #include "multishift.h"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "solver.h"
 
@@ -85,6 +86,7 @@ __global__ void ms_start_kernel(const double *partials, int n, MsScalars *S, dou
 }
 
 __global__ void ms_alpha_kernel(const double *partials, int n, MsScalars *S) {
+  pdl_enter();
   if (S->halt) {  // a queued iteration after the halt: the last x_i update is done
     if (threadIdx.x == 0) S->final_x = 0;
     return;
@@ -107,6 +109,7 @@ __global__ void ms_alpha_kernel(const double *partials, int n, MsScalars *S) {
 }
 
 __global__ void ms_beta_kernel(const double *partials, int n, MsScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   const double rr_new = sum_partials(partials, n);
   if (threadIdx.x == 0) {
@@ -146,6 +149,7 @@ __global__ void ms_xp_kernel(float4 *__restrict__ pb, const float4 *__restrict__
   __shared__ float4 cp[kMsMaxShifts];  // (zeta.h, zeta.l, beta.h, beta.l)
   __shared__ float2 cx[kMsMaxShifts];  // alpha_i (h, l)
   __shared__ int ax[kMsMaxShifts], ap[kMsMaxShifts];
+  pdl_enter();
   if (S->halt && !S->final_x) return;  // uniform across the grid
   const int ns = S->nshift;
   for (int i = threadIdx.x; i < ns; i += blockDim.x) {
@@ -343,16 +347,15 @@ cudaError_t launch_ms_start(const double *partials, int n, MsScalars *S, double 
 
 cudaError_t launch_ms_alpha(const double *partials, int nhop, MsScalars *S, cudaStream_t s) {
   note_launch();
-  ms_alpha_kernel<<<1, kReduceThreads, 0, s>>>(partials, nhop, S);
-  return cudaGetLastError();
+  return launch_pdl(ms_alpha_kernel, 1, kReduceThreads, 0, s, partials, nhop, S);
 }
 
 cudaError_t launch_ms_beta_xp(const double *partials, int nhop, int nblas, MsScalars *S, const MsVectors &V,
                               const float4 *r, float4 *pb, int64_t n, cudaStream_t s) {
   note_launch(2);
-  ms_beta_kernel<<<1, kReduceThreads, 0, s>>>(partials, nhop, S);
-  ms_xp_kernel<<<nblas, kBlasThreads, 0, s>>>(pb, r, V, n, S);
-  return cudaGetLastError();
+  const cudaError_t e = launch_pdl(ms_beta_kernel, 1, kReduceThreads, 0, s, partials, nhop, S);
+  if (e != cudaSuccess) return e;
+  return launch_pdl(ms_xp_kernel, nblas, kBlasThreads, 0, s, pb, r, V, n, S);
 }
 
 cudaError_t launch_ms_resid(const float4 *rhs, const float4 *Ax, const float4 *x, double sigma, int64_t n,

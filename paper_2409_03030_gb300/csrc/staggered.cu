@@ -19,6 +19,7 @@
 
 #include "hop_dwp.cuh"
 #include "kernels.h"
+#include "pdl.cuh"
 #include "reduce.cuh"
 #include "solver.h"
 #include "staggered.h"
@@ -93,6 +94,7 @@ __global__ void __launch_bounds__(kStagThreads) stag_hop_kernel(Geom g, int p, c
                                                                 const float4 *__restrict__ gauge, float2 a_split,
                                                                 float2 b_split, double *partials,
                                                                 const int *guard) {
+  pdl_enter();
   if (guard && *guard) return;  // uniform across the grid
   const int64_t cb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t vh = g.vh;
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(kStagThreads)
     stag_hop_cg_kernel(Geom g, const float4 *__restrict__ t, const float4 *__restrict__ pv,
                        float4 *__restrict__ xs, float4 *__restrict__ r, const float4 *__restrict__ gauge,
                        float2 a_split, float2 b_split, const SolverScalars *__restrict__ S, double *partials) {
+  pdl_enter();
   if (S->halt) return;  // uniform across the grid
   const int64_t cb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t vh = g.vh;
@@ -240,6 +243,7 @@ __global__ void __launch_bounds__(kStagThreads)
 // p = r + beta p (beta = S->beta_dw) with the block partial of ||p||^2.
 __global__ void stag_xpay_norm_kernel(float4 *__restrict__ p, const float4 *__restrict__ r, int64_t n,
                                       const SolverScalars *S, double *partials) {
+  pdl_enter();
   if (S->halt) return;  // uniform across the grid
   const dw be = dw_make(S->beta_dw.x, S->beta_dw.y);
   dwacc A{0.f, 0.f};
@@ -280,6 +284,7 @@ __device__ __forceinline__ double thread_sum(const double *a, int n) {
 
 __global__ void stag_alpha_kernel(const double *pt, int nt, const double *pp, int np, double m2,
                                   SolverScalars *S) {
+  pdl_enter();
   if (S->halt) return;
   double vt = thread_sum(pt, nt), vp = thread_sum(pp, np);
   vt = block_sum_d(vt);
@@ -313,20 +318,19 @@ cudaError_t launch_stag_hop(const Geom &g, int out_parity, bool dagger, const fl
   const unsigned nb = stag_blocks(g.vh);
   const int key = (dagger ? 4 : 0) | (x ? 2 : 0) | (partials ? 1 : 0);
 #define STAG_LAUNCH(D, A, N) \
-  stag_hop_kernel<D, A, N><<<nb, kStagThreads, 0, s>>>(g, out_parity, in, x, out, gauge_dw, as, bs, partials, \
-                                                       guard)
+  return launch_pdl(stag_hop_kernel<D, A, N>, nb, kStagThreads, 0, s, g, out_parity, in, x, out, gauge_dw, as, bs, \
+                    partials, guard)
   switch (key) {
-    case 0: STAG_LAUNCH(false, false, false); break;
-    case 1: STAG_LAUNCH(false, false, true); break;
-    case 2: STAG_LAUNCH(false, true, false); break;
-    case 3: STAG_LAUNCH(false, true, true); break;
-    case 4: STAG_LAUNCH(true, false, false); break;
-    case 5: STAG_LAUNCH(true, false, true); break;
-    case 6: STAG_LAUNCH(true, true, false); break;
+    case 0: STAG_LAUNCH(false, false, false);
+    case 1: STAG_LAUNCH(false, false, true);
+    case 2: STAG_LAUNCH(false, true, false);
+    case 3: STAG_LAUNCH(false, true, true);
+    case 4: STAG_LAUNCH(true, false, false);
+    case 5: STAG_LAUNCH(true, false, true);
+    case 6: STAG_LAUNCH(true, true, false);
     default: STAG_LAUNCH(true, true, true);
   }
 #undef STAG_LAUNCH
-  return cudaGetLastError();
 }
 
 cudaError_t launch_stag_pack(const Geom &g, const double *canon, float4 *even, float4 *odd, cudaStream_t s) {
@@ -412,15 +416,13 @@ jqcd_status solve_staggered(GaugeEntry &G, double mass, const jqcd_solve_params 
         // hop applies the update and forms ||r||^2; beta; p = r + beta p, ||p||^2
         CKT(launch_stag_hop(G.g, 1, false, p, nullptr, t, U, 0.0, 1.0, part_t, s, &S->halt));
         note_launch();
-        stag_alpha_kernel<<<1, kReduceThreads, 0, s>>>(part_t, nstag, part_p, nblas, m2, S);
+        CKT(launch_pdl(stag_alpha_kernel, 1, kReduceThreads, 0, s, part_t, nstag, part_p, nblas, m2, S));
         note_launch();
-        stag_hop_cg_kernel<<<nstag, kStagThreads, 0, s>>>(G.g, t, p, xe, r, U, dw_split_host(m2),
-                                                          dw_split_host(-1.0), S, part_t);
-        CKT(cudaGetLastError());
+        CKT(launch_pdl(stag_hop_cg_kernel, nstag, kStagThreads, 0, s, G.g, t, p, xe, r, U, dw_split_host(m2),
+                       dw_split_host(-1.0), S, part_t));
         CKT(launch_cg_beta(part_t, nstag, S, s));
         note_launch();
-        stag_xpay_norm_kernel<<<nblas, kBlasThreads, 0, s>>>(p, r, n, S, part_p);
-        CKT(cudaGetLastError());
+        CKT(launch_pdl(stag_xpay_norm_kernel, nblas, kBlasThreads, 0, s, p, r, n, S, part_p));
       }
       CKT(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
       CKT(cudaStreamSynchronize(s));
