@@ -14,6 +14,8 @@ components up to ~12) and spinors scaled by 2^-60 ... 2^60:
   * the high words of A + iB join exactly ((T0 + A.re) - (T0 + B.im) and
     (T0 + A.im) + (-T0 + B.re));
   * the double-word result agrees with the exact product to a few 1e-14.
+The force kernel's outer products P_ba = sum_s v_sb conj(c_sa), nine entries
+on one grid per part, are checked the same way.
 FP32 rounding is emulated exactly with Python fractions (round to nearest
 even, binary32 normal range), so no GPU is involved.
 """
@@ -147,3 +149,68 @@ def test_grid_matvec_zero_half_spinor():
     zero = (Fraction(0), Fraction(0))
     got = grid_matvec(W, [(zero, zero)] * 3)
     assert all(v == Fraction(0) for r in got for part in r for v in part)
+
+
+def grid_outer(v, c):
+    """P_ba = sum_s v_sb conj(c_sa) for the two spins s of a force part, all
+    nine entries on one grid: its bound is max|v.hi| times
+    max_a max(|c_0a.re| + |c_1a.re|, |c_0a.im| + |c_1a.im|), raised by 2^-19.
+    v, c: 2 x 3 of ((re.h, re.l), (im.h, im.l)).  Asserts the exact steps."""
+    vm = max(abs(v[s][b][k][0]) for s in range(2) for b in range(3) for k in range(2))
+    cm = max(max(rn32(abs(c[0][a][0][0]) + abs(c[1][a][0][0])), rn32(abs(c[0][a][1][0]) + abs(c[1][a][1][0])))
+             for a in range(3))
+    m = rn32(rn32(vm * cm) * rn32(Fraction(1) + Fraction(1, 2 ** 19)))
+    sigma = 4 * pow2_floor(m) if m > 0 else Fraction(2) ** -125
+    t0 = Fraction(3, 2) * sigma
+    P = {}
+    for a in range(3):
+        for b in range(3):
+            lanes = {}
+            # A: multipliers Re c_sa (conj keeps it); B: multipliers -Im c_sa
+            for which, start in ((0, (t0, t0)), (1, (-t0, t0))):
+                res = []
+                for lane in (0, 1):
+                    T, acc = start[lane], Fraction(0)
+                    for s in range(2):
+                        mh, ml = c[s][a][which]
+                        if which == 1:
+                            mh, ml = -mh, -ml
+                        wh, wl = v[s][b][lane]
+                        Tn = rn32(mh * wh + T)
+                        q = T - Tn
+                        assert is_f32(q) and sigma <= abs(Tn) < 2 * sigma
+                        d = rn32(mh * wh + q)
+                        t = d if s == 0 else rn32(acc + d)
+                        acc = rn32(ml * wh + rn32(mh * wl + t))
+                        T = Tn
+                    res.append((T, acc))
+                lanes[which] = res
+            (ATre, Acre), (ATim, Acim) = lanes[0]
+            (BTre, Bcre), (BTim, Bcim) = lanes[1]
+            hre, him = ATre - BTim, ATim + BTre
+            assert is_f32(hre) and is_f32(him)
+            P[b, a] = (hre + rn32(Acre - Bcim), him + rn32(Acim + Bcre))
+    return P
+
+
+@pytest.mark.parametrize("scale_exp", [-40, 0, 40])
+def test_grid_outer_products_of_the_force(scale_exp):
+    rng = np.random.default_rng(2000 + scale_exp)
+    for _ in range(3):
+        vc = (rng.normal(size=(2, 3)) + 1j * rng.normal(size=(2, 3))) * 2.0 ** scale_exp
+        cc = rng.normal(size=(2, 3)) + 1j * rng.normal(size=(2, 3))
+        v = [[(split_dw(vc[s, b].real), split_dw(vc[s, b].imag)) for b in range(3)] for s in range(2)]
+        c = [[(split_dw(cc[s, a].real), split_dw(cc[s, a].imag)) for a in range(3)] for s in range(2)]
+        P = grid_outer(v, c)
+        num = den = Fraction(0)
+        for a in range(3):
+            for b in range(3):
+                ere = eim = Fraction(0)
+                for s in range(2):
+                    vr, vi = v[s][b][0][0] + v[s][b][0][1], v[s][b][1][0] + v[s][b][1][1]
+                    cr, ci = c[s][a][0][0] + c[s][a][0][1], c[s][a][1][0] + c[s][a][1][1]
+                    ere += vr * cr + vi * ci  # v conj(c)
+                    eim += vi * cr - vr * ci
+                num += (P[b, a][0] - ere) ** 2 + (P[b, a][1] - eim) ** 2
+                den += ere ** 2 + eim ** 2
+        assert math.sqrt(float(num / den)) <= 3e-13
