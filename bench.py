@@ -15,11 +15,21 @@ output site (spin projection, SU(3) times half-spinor, reconstruction and
 accumulation over the 8 directions; axpy terms not counted) per second.
 e2e   = the same quantity through jqcd_cg_solve with host buffers in pinned
 memory (copy of b in, copy of x out, inside the timed region).
-roofline = the double-word hop kernel timed alone on the same lattice.  It is
-bound by the FP32 datapath (error-free double-word arithmetic), so the
-roofline is its FP32 lane operations per second against SMs x 128 lanes x
-clock; its HBM fraction (the metric's "Dslash GB/s vs HBM peak") rides along.
-cpu_baseline / --impl reference = the FP64 CPU oracle on host cores.
+roofline = the double-word hop kernel timed alone on the same lattice (mean of
+back-to-back launches, CUDA events on its stream), reported against HBM: its
+algorithmic bytes per launch over the measured copy bandwidth (the metric's
+"Dslash GB/s vs HBM peak").  Its FP32-datapath fraction (error-free
+double-word arithmetic: FP32 lane operations per second against SMs x 128
+lanes x clock) rides along under roofline.alu.  roofline.traffic is ncu's
+DRAM bytes per launch from the committed profile summary, used only while
+the kernel sources hash to the captured value (roofline.traffic_source).
+cg = CG seconds to 1e-10 per solver mode (double-word, plain FP64, mixed FP32
+and FP16 inner) on the workload and on 32^3x64, each workload solution's
+error against the FP64 oracle's solution (err_vs_oracle) and each 32^3x64
+solution's against the plain FP64 GPU solve's (err_vs_f64).
+cpu_baseline = the FP64 CPU oracle's complete solve of the workload system
+on the host cores (its solution gives err_vs_oracle); --impl reference = the
+oracle's CG iterations on the same system.
 
 Multi-GPU (torchrun): each rank solves its own replica (independent problems,
 weak scaling, no collective on the data path).
@@ -59,6 +69,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config2", action="store_true",
                     help="skip the 32^3x64 mixed-vs-double-word CG comparison")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="leave out the per-mode err_vs_oracle of the workload solves")
     ap.add_argument("--no-batch", action="store_true", help="skip the 24-solve batch")
     ap.add_argument("--serve-host", default="pinned", choices=["pinned", "pageable"],
                     help="host memory of the serving stream's sources and solutions")
@@ -102,6 +114,23 @@ def time_oracle_cg(U, b, iters, threads=0):
     vh = vol(DIMS) // 2
     hop_bytes = (iters + 2) * vh * (4 * 1536 + 2 * 192)
     return hop_bytes / dt / 1e9, dt, used
+
+
+def time_oracle_solve(U, b, tol):
+    """The oracle's complete even-odd solve of the workload system D x = b to
+    `tol` on all the threads it uses by default.  Returns (GB/s of hop bytes
+    at the GPU's accounting, seconds, threads, x, CG iterations, system
+    residual).  Hop bytes: source preparation (3 hops), (iters + 2)
+    applications of Mhat^dag Mhat (start and true residual included) and the
+    reconstruction (1 hop)."""
+    import oracle
+    threads = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    x, iters, res, _, _ = oracle.solve(DIMS, U, b, KAPPA, eo=True, tol=tol)
+    dt = time.perf_counter() - t0
+    vh = vol(DIMS) // 2
+    hop_bytes = (iters + 2) * vh * (4 * 1536 + 2 * 192) + vh * (4 * 1536 + 3 * 192)
+    return hop_bytes / dt / 1e9, dt, threads, x, iters, res
 
 
 def kernel_hash():
@@ -649,29 +678,38 @@ def run_gpu(args):
             t.append(a0.elapsed_time(a1) * 1e-3)
         return statistics.median(t), info
 
-    def cg_table(gg, be_, bo_, kappa, n):
+    def cg_table(gg, be_, bo_, kappa, n, keep=None):
+        """Per mode: median solve time, iterations, residuals.  keep: dict
+        that receives each mode's solution (host, canonical order)."""
         xe_, xo_ = gg.empty(jqcd.PREC_DW), gg.empty(jqcd.PREC_DW)
         out = {}
-        for name, mode in [("dw", jqcd.CG_DW), ("mixed_f32", jqcd.CG_MIXED_F32),
-                           ("mixed_f16", jqcd.CG_MIXED_F16)]:
+        for name, mode in [("dw", jqcd.CG_DW), ("f64", jqcd.CG_F64),
+                           ("mixed_f32", jqcd.CG_MIXED_F32), ("mixed_f16", jqcd.CG_MIXED_F16)]:
             t, info = time_solves(gg, be_, bo_, xe_, xo_, kappa, mode, n)
             out[name] = {"s": round(t, 5), "iters": info["iters"],
                          "reliable_updates": info["reliable_updates"],
                          "true_rel_resid": info["true_rel_resid"],
                          "full_rel_resid": info["full_rel_resid"]}
-        out["speedup_mixed_f16_vs_dw"] = round(out["dw"]["s"] / out["mixed_f16"]["s"], 3)
-        out["speedup_mixed_f32_vs_dw"] = round(out["dw"]["s"] / out["mixed_f32"]["s"], 3)
+            if keep is not None:
+                keep[name] = gg.unpack(xe_, xo_, jqcd.PREC_DW, stream=stream)
+        for m in ("mixed_f16", "mixed_f32"):
+            out[f"speedup_{m}_vs_f64"] = round(out["f64"]["s"] / out[m]["s"], 3)
+            out[f"speedup_{m}_vs_dw"] = round(out["dw"]["s"] / out[m]["s"], 3)
+        out["speedup_dw_vs_f64"] = round(out["f64"]["s"] / out["dw"]["s"], 3)
         return out
 
-    cg_work = cg_table(g, be, bo, KAPPA, 3)
+    work_solutions = {}
+    cg_work = cg_table(g, be, bo, KAPPA, 3, keep=work_solutions)
     cg_c2 = None
+    c2_solutions = {}
+    d2 = (32, 32, 32, 64)
     if not args.no_config2:
-        d2 = (32, 32, 32, 64)
         g2 = ctx.gauge_upload(d2, synth.gauge(d2, "expi", eps=0.4, seed=11))
+        b2 = synth.gaussian_spinor(d2, seed=12)
         with torch.cuda.stream(stream):
-            b2e, b2o = g2.pack(synth.gaussian_spinor(d2, seed=12), jqcd.PREC_DW, stream=stream)
+            b2e, b2o = g2.pack(b2, jqcd.PREC_DW, stream=stream)
         stream.synchronize()
-        cg_c2 = cg_table(g2, b2e, b2o, 0.122, 3)
+        cg_c2 = cg_table(g2, b2e, b2o, 0.122, 3, keep=c2_solutions)
         sweep["32x32x32x64"] = hop_sweep(g2, d2, synth.gaussian_spinor(d2, seed=12))
         cg_c2["workload"] = "32^3x64, exp(i*0.4*H) links, kappa 0.122, even-odd, tol 1e-10"
         g2.free()
@@ -684,18 +722,37 @@ def run_gpu(args):
     serve = (bench_serve(ctx, jqcd, synth, np, args.serve_requests, host=args.serve_host)
              if args.serve_requests > 0 else None)
 
+    # 32^3x64: each mode's solution against the plain FP64 GPU solve's
+    if cg_c2 is not None and "f64" in c2_solutions:
+        x64 = c2_solutions["f64"]
+        n64 = float(np.linalg.norm(x64))
+        for name, xs in c2_solutions.items():
+            if name != "f64":
+                cg_c2[name]["err_vs_f64"] = float(np.linalg.norm(xs - x64)) / n64
+    c2_solutions = None
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        _, dt1, _ = time_oracle_cg(U, b, 1)  # calibrate: ~10 s sample
-        iters = int(min(30, max(1, round(10.0 / max(dt1 / 3.0, 1e-3)) - 2)))
-        v, dt, threads = time_oracle_cg(U, b, iters)
+        # the oracle solves the bench's own system (tol 1e-12), after every GPU
+        # timing of the run; its solution also gives each GPU mode's error
+        v, dt, threads, xo, it_o, res_o = time_oracle_solve(U, b, 1e-12)
         v1, dt1s, _ = time_oracle_cg(U, b, 1, threads=1)  # one thread, one iteration
         cpu = {"value": round(v, 3), "unit": "GB/s", "cores": threads, "kind": "oracle",
-               "sample": sample_description(iters) + f", {dt:.1f} s",
+               "sample": (f"oracle even-odd solve of the workload system to 1e-12 "
+                          f"(textbook CG, {it_o} iterations, system residual {res_o:.2e}), "
+                          f"{dt:.1f} s"),
                "single_thread": {"value": round(v1, 3), "unit": "GB/s", "cores": 1,
                                  "sample": sample_description(1) + f", {dt1s:.1f} s"},
                "gpu_speedup": {"vs_all_cores": round(value / v, 1),
                                "vs_one_core": round(value / v1, 1)}}
+        if not args.no_oracle_error:
+            nrm = float(np.linalg.norm(xo))
+            for name, xs in work_solutions.items():
+                cg_work[name]["err_vs_oracle"] = float(np.linalg.norm(xs - xo)) / nrm
+            cg_work["err_definition"] = ("||x - x_oracle|| / ||x_oracle|| over the whole lattice, "
+                                         "x_oracle the FP64 oracle's solution of D x = b to 1e-12 "
+                                         "(the cpu_baseline solve)")
+    work_solutions = None
 
     if rank == 0:
         line = {
@@ -707,6 +764,10 @@ def run_gpu(args):
             "config": workload_config(),
             "roofline": {"bound": "hbm", "achieved": round(dw_achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(dw_achieved / hbm, 4), "traffic": traffic,
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per "
+                                            "launch, profiles/hop_dw_24x24x24x48.md (kernel "
+                                            "sources hash-matched); not measured in this run"
+                                            if traffic is not None else None),
                          "kernel": "hop_dwp_kernel (double-word plain hop)",
                          "bytes_per_site": HOP_BYTES["dw"],
                          "frac_nominal": round(dw_achieved / NOMINAL_HBM_GBS, 4),

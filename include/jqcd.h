@@ -161,7 +161,10 @@ JQCD_API jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t pr
  * parity are rejected with JQCD_EINVAL.
  * The first call on a device that asks for a norm looks up the array's
  * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.
+ * first call before any stream capture.  The address is kept for the life of
+ * the process: resetting the device (cudaDeviceReset) or otherwise
+ * re-creating its primary context while the library is loaded is not
+ * supported by this entry point.
  * All calls share the one array and each call overwrites what it reads, so
  * nothing needs clearing, but calls whose work overlaps on the GPU (other
  * streams, other host threads) race on it: serialise them.
@@ -189,7 +192,9 @@ JQCD_API jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t 
 /* Solver modes. */
 enum {
   JQCD_CG_DW = 0,        /* every vector and operator in double-word precision */
-  JQCD_CG_F64 = 1,       /* native FP64 operator and vectors */
+  JQCD_CG_F64 = 1,       /* plain FP64 CG: every vector, hop (native DFMA, the
+                            JQCD_PREC_F64 layout) and reduction in IEEE double;
+                            eo = 0 or 1; no reliable updates */
   JQCD_CG_MIXED_F32 = 2, /* FP32 inner CG, double-word reliable updates */
   JQCD_CG_MIXED_F16 = 3  /* FP16+norm inner operator, FP32 inner vectors,
                             double-word reliable updates */
@@ -233,7 +238,10 @@ JQCD_API jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_
 
 /* The same solve on device-resident fields: b_even, b_odd, x_even, x_odd are
  * caller-owned device buffers in the JQCD_PREC_DW layout (x is used as the
- * start vector when params->use_x0).  Synchronises `stream` before return. */
+ * start vector when params->use_x0).  Synchronises `stream` before return.
+ * In mode JQCD_CG_F64, b is widened exactly to FP64, the solve runs in FP64
+ * and x is rounded back to double-word (jqcd_cg_solve instead packs the host
+ * FP64 b straight into the FP64 layout, so it rounds nowhere). */
 JQCD_API jqcd_status jqcd_cg_solve_dev(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                               const void *b_even, const void *b_odd, void *x_even, void *x_odd,
                               jqcd_solve_info *info, void *stream);

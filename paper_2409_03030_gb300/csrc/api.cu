@@ -272,7 +272,8 @@ jqcd_status jqcd_dslash_eo(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, int32
   if (norm2_dev) CK(G->ensure_reduce(), "workspace alloc");
   HopParams P = G->hop_params(prec, out_parity, in, x, out, a, b, norm2_dev ? G->partials : nullptr);
   CK(launch_hop(prec, P, dagger != 0, x != nullptr, norm2_dev != nullptr, s), "hop launch");
-  if (norm2_dev) CK(launch_finalize_sum(G->partials, (int)hop_blocks(G->g.vh), norm2_dev, s), "norm");
+  if (norm2_dev)
+    CK(launch_finalize_sum(G->partials, (int)hop_norm_partials(prec, G->g.vh), norm2_dev, s), "norm");
   return JQCD_OK;
 }
 
@@ -290,7 +291,8 @@ jqcd_status jqcd_mdagm(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, double ka
                  norm2_dev ? G->partials : nullptr, nullptr, (cudaStream_t)stream),
      "mdagm");
   if (norm2_dev)
-    CK(launch_finalize_sum(G->partials, (int)hop_blocks(G->g.vh), norm2_dev, (cudaStream_t)stream), "norm");
+    CK(launch_finalize_sum(G->partials, (int)hop_norm_partials(prec, G->g.vh), norm2_dev,
+                           (cudaStream_t)stream), "norm");
   return JQCD_OK;
 }
 
@@ -313,6 +315,38 @@ jqcd_status jqcd_dirac_apply(jqcd_ctx *ctx, uint64_t gauge_id, int32_t prec, dou
   return JQCD_OK;
 }
 
+// jqcd_cg_solve in mode JQCD_CG_F64: the canonical FP64 b (and start vector)
+// is packed straight into the FP64 layout and the FP64 solution unpacked from
+// it, so no step of the solve rounds below IEEE double.
+static jqcd_status cg_solve_f64(jqcd_ctx *ctx, GaugeEntry *G, const jqcd_solve_params *params,
+                                const double *b, double *x, jqcd_solve_info *info,
+                                std::chrono::steady_clock::time_point t0) {
+  cudaStream_t s = ctx->stream;
+  const int64_t nh = 12 * G->g.vh;  // complex numbers per parity
+  CK(G->ensure_f64(), "solver workspace alloc");
+  CK(cudaMemcpyAsync(G->canon, b, G->canon_bytes(), cudaMemcpyHostToDevice, s), "b H2D");
+  CK(launch_spinor_pack(G->g, PREC_F64, G->canon, G->fb, G->fb + nh, s), "b pack");
+  if (params->use_x0) {
+    CK(cudaMemcpyAsync(G->canon, x, G->canon_bytes(), cudaMemcpyHostToDevice, s), "x0 H2D");
+    CK(launch_spinor_pack(G->g, PREC_F64, G->canon, G->fsol, G->fsol + nh, s), "x0 pack");
+  }
+  jqcd_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  std::string msg;
+  jqcd_status st = solve_resident_f64(*G, *params, s, &inf, &msg);
+  if (st == JQCD_ECUDA) ctx->poisoned = true;
+  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+    CK(launch_spinor_unpack(G->g, PREC_F64, G->fsol, G->fsol + nh, G->canon, s), "x unpack");
+    CK(cudaMemcpyAsync(x, G->canon, G->canon_bytes(), cudaMemcpyDeviceToHost, s), "x D2H");
+    CK(cudaStreamSynchronize(s), "solve sync");
+  }
+  inf.status = st;
+  inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  if (st != JQCD_OK) return fail(ctx, st, "cg_solve: %s", msg.c_str());
+  return JQCD_OK;
+}
+
 jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_params *params,
                           const double *b, double *x, jqcd_solve_info *info) {
   JQCD_RANGE();
@@ -323,6 +357,7 @@ jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_par
   if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
   if (!params || !b || !x) return fail(ctx, JQCD_EINVAL, "cg_solve: bad argument");
   cudaStream_t s = ctx->stream;
+  if (params->mode == JQCD_CG_F64) return cg_solve_f64(ctx, G, params, b, x, info, t0);
   CK(G->ensure_solver(), "solver workspace alloc");
   // host -> device: canonical b (and x0) into the solver's double-word vectors
   CK(cudaMemcpyAsync(G->canon, b, G->canon_bytes(), cudaMemcpyHostToDevice, s), "b H2D");
@@ -564,13 +599,15 @@ extern "C" jqcd_status jqcd_dslash_eo_noalloc(jqcd_ctx *ctx, uint64_t gauge_id, 
                                               int32_t out_parity, int32_t dagger, const void *in,
                                               const void *x, void *out, double a, double b,
                                               double *norm2_dev, void *stream) {
+  JQCD_RANGE();
   jqcd_status st = check_ctx(ctx);
   if (st) return st;
   GaugeEntry *G = find_gauge(ctx, gauge_id);
   if (!G) return fail(ctx, JQCD_ENOTFOUND, "unknown gauge id");
   if (!in || !out || in == out || (out_parity != 0 && out_parity != 1) || !valid_prec(prec))
     return fail(ctx, JQCD_EINVAL, "dslash_eo_noalloc: bad argument");
-  if (G->g.vh > (int64_t)JQCD_NOALLOC_MAX_SITES_PER_PARITY)
+  if (G->g.vh > (int64_t)JQCD_NOALLOC_MAX_SITES_PER_PARITY ||
+      hop_norm_partials(prec, G->g.vh) > (unsigned)kNoAllocMaxBlocks)
     return fail(ctx, JQCD_EINVAL,
                 "dslash_eo_noalloc: %lld sites per parity exceed the fixed scratch limit of %d",
                 (long long)G->g.vh, JQCD_NOALLOC_MAX_SITES_PER_PARITY);
@@ -583,7 +620,8 @@ extern "C" jqcd_status jqcd_dslash_eo_noalloc(jqcd_ctx *ctx, uint64_t gauge_id, 
   // same call, so nothing in the scratch has to be cleared first.
   HopParams P = G->hop_params(prec, out_parity, in, x, out, a, b, scratch);
   CK(launch_hop(prec, P, dagger != 0, x != nullptr, norm2_dev != nullptr, s), "hop launch");
-  if (norm2_dev) CK(launch_finalize_sum(scratch, (int)hop_blocks(G->g.vh), norm2_dev, s), "norm");
+  if (norm2_dev)
+    CK(launch_finalize_sum(scratch, (int)hop_norm_partials(prec, G->g.vh), norm2_dev, s), "norm");
   return JQCD_OK;
 }
 

@@ -78,6 +78,7 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = idx < P.g.vh;
   dwacc nrm{0.f, 0.f};
+  double nrm64 = 0.0;  // FP64 hops accumulate their norm in FP64
   if (active) {
     int x, y, z, t;
     cb_coords(P.g, idx, P.out_parity, x, y, z, t);
@@ -107,10 +108,13 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
         for (int c = 0; c < 3; ++c) o[s][c] = T::scale(b, acc[s][c]);
     }
     T::store_spinor(P.out, P.g.vh, idx, o);
-    if (NORM) nrm = site_norm2<PREC>(o);
+    if (NORM) {
+      if constexpr (PREC == PREC_F64) nrm64 = site_norm2_d(o);
+      else nrm = site_norm2<PREC>(o);
+    }
   }
   if (NORM) {
-    const double s = block_sum_dw(nrm);
+    const double s = PREC == PREC_F64 ? block_sum_d(nrm64) : block_sum_dw(nrm);
     if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
   }
 }
@@ -211,16 +215,78 @@ __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kern
   }
 }
 
+// Small lattices: two threads per output site (dwp_pair_combine), so the
+// grid holds twice as many warps when one thread per site cannot fill the
+// GPU.  Blocks of kHopThreads threads cover kHopThreads / 2 sites.
+template <bool DAG, bool AXPY, bool NORM>
+__global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp2_kernel(const HopParams P) {
+  extern __shared__ float4 dsm[];
+  pdl_enter();
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = gid >> 1;
+  const int q = (int)(gid & 1);
+  const bool active = idx < P.g.vh;  // the same for both threads of a site
+  p2 acc[4][3];
+  if (active) {
+    dwp_hop_dirs<DAG>(dsm, reinterpret_cast<const float4 *>(P.in),
+                      reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q, 2, 4, acc);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[a][c] = p2{0ull, 0ull};
+  }
+  p2 o[6];
+  dwp_pair_combine(acc, q, o);  // every lane of the warp takes part
+  dwacc nrm{0.f, 0.f};
+  if (active)
+    nrm = dwp_store_chunks<AXPY, NORM, 6>(o, 6 * q, reinterpret_cast<float4 *>(P.out),
+                                          reinterpret_cast<const float4 *>(P.x), P.g.vh, idx,
+                                          P.a_split, P.b_split);
+  if (NORM) {
+    const double s = block_sum_dw(nrm);
+    if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+  }
+}
+
+// Two threads per site pay off only while their grid fits in one wave of
+// resident blocks (measured on GB300: 8^4 hop 9.6 -> 7.5 us; at 16^4, where
+// the split grid needs 1.12 waves, 19.1 -> 18.6 us and the solve slower;
+// 16^3x32 at 2.25 waves 24.8 -> 30.4 us).
+bool dw_hop_split(int64_t vh) {
+  static const int64_t max_vh = [] {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      return (int64_t)0;
+    return (int64_t)sms * JQCD_DWP_MIN_BLOCKS * kHopThreads / 2;
+  }();
+  return vh <= max_vh && vh <= JQCD_DWP_SPLIT_MAX_VH;
+}
+
+unsigned dw_hop_blocks(int64_t vh) {
+  return dw_hop_split(vh) ? (unsigned)((2 * vh + kHopThreads - 1) / kHopThreads) : hop_blocks(vh);
+}
+
+unsigned hop_norm_partials(int prec, int64_t vh) {
+  return prec == PREC_DW ? dw_hop_blocks(vh) : hop_blocks(vh);
+}
+
 template <bool DAG, bool AXPY, bool NORM>
 static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
   note_launch();
   static bool configured = false;  // one attribute call per instantiation
   auto kern = hop_dwp_kernel<DAG, AXPY, NORM>;
+  auto kern2 = hop_dwp2_kernel<DAG, AXPY, NORM>;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if (dw_hop_split(P.g.vh)) return launch_pdl(kern2, dw_hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P);
   return launch_pdl(kern, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P);
 }
 

@@ -23,14 +23,16 @@ namespace jqcd {
 
 namespace {
 
-// q = a*w + b*acc is (Ap)(idx); x += alpha p (XUPD) and r -= alpha q in place;
-// returns this thread's ||r||^2.  Every operand is a 16-byte double-word chunk.
-template <bool XUPD>
-__device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float4 *__restrict__ w_base,
+// q = a*w + b*v is (Ap)(idx) for the NC components k0 .. k0 + NC - 1 of the
+// site; x += alpha p (XUPD) and r -= alpha q in place; returns their
+// contribution to ||r||^2.  Every operand is a 16-byte double-word chunk.
+template <bool XUPD, int NC>
+__device__ __forceinline__ dwacc dwp_store_cg(const p2 (&v)[NC], int k0, const float4 *__restrict__ w_base,
                                               const float4 *__restrict__ p_base,
                                               float4 *__restrict__ x_base, float4 *__restrict__ r_base,
                                               int64_t vh, int64_t idx, float2 a_split, float2 b_split,
                                               float2 alpha) {
+  idx += (int64_t)k0 * vh;
   const mul2 Bm{f2_make(b_split.x, b_split.x), f2_make(b_split.y, b_split.y)};
   const mul2 Am{f2_make(a_split.x, a_split.x), f2_make(a_split.y, a_split.y)};
   const mul2 Al{f2_make(alpha.x, alpha.x), f2_make(alpha.y, alpha.y)};
@@ -41,9 +43,9 @@ __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&acc)[4][3], const float
   ulonglong2 *__restrict__ rp = reinterpret_cast<ulonglong2 *>(r_base) + idx;
   acc2 nq{0ull, 0ull};
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
+  for (int k = 0; k < NC; ++k) {
     const ulonglong2 wv = __ldg(wp + k * vh), rv = rp[k * vh];
-    acc2 R = acc2_first(Bm, p2_norm(acc[k / 3][k % 3]));
+    acc2 R = acc2_first(Bm, p2_norm(v[k]));
     acc2_mad(R, Am, p2{wv.x, wv.y});
     const p2 q = p2_norm(acc2_get(R));
     if (XUPD) {
@@ -78,9 +80,45 @@ __global__ void __launch_bounds__(kHopThreads, 3)
     p2 acc[4][3];
     dwp_hop_site<true>(dsm, reinterpret_cast<const float4 *>(P.in),
                        reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
-    nrm = dwp_store_cg<XUPD>(acc, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx, P.a_split,
-                             P.b_split, *alpha);
+    p2 v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = acc[k / 3][k % 3];
+    nrm = dwp_store_cg<XUPD, 12>(v, 0, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx,
+                                 P.a_split, P.b_split, *alpha);
   }
+  const double s = block_sum_dw(nrm);
+  if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+}
+
+// The same with two threads per output site (small lattices, see
+// dwp_pair_combine): thread q updates components 6q .. 6q + 5.
+template <bool XUPD>
+__global__ void __launch_bounds__(kHopThreads, 3)
+    hop_dwp2_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
+                       float4 *__restrict__ r, const float2 *__restrict__ alpha) {
+  extern __shared__ float4 dsm[];
+  pdl_enter();
+  if (P.guard && *P.guard) return;  // uniform across the grid
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = gid >> 1;
+  const int q = (int)(gid & 1);
+  const bool active = idx < P.g.vh;
+  p2 acc[4][3];
+  if (active) {
+    dwp_hop_dirs<true>(dsm, reinterpret_cast<const float4 *>(P.in),
+                       reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q, 2, 4, acc);
+  } else {
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) acc[a][c] = p2{0ull, 0ull};
+  }
+  p2 o[6];
+  dwp_pair_combine(acc, q, o);
+  dwacc nrm{0.f, 0.f};
+  if (active)
+    nrm = dwp_store_cg<XUPD, 6>(o, 6 * q, reinterpret_cast<const float4 *>(P.x), p, xs, r, P.g.vh, idx,
+                                P.a_split, P.b_split, *alpha);
   const double s = block_sum_dw(nrm);
   if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
 }
@@ -154,9 +192,15 @@ static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDwpSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hop_dwp2_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kDwpSmem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  if (dw_hop_split(P.g.vh))
+    return launch_pdl(hop_dwp2_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P, p, x,
+                      r, alpha);
   return launch_pdl(hop_dwp_cg_kernel<XUPD>, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P, p, x, r, alpha);
 }
 

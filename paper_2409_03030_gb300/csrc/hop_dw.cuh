@@ -19,12 +19,15 @@ template <> __device__ __forceinline__ dwacc site_norm2<PREC_DW>(const cw (&o)[4
   }
   return A;
 }
-template <> __device__ __forceinline__ dwacc site_norm2<PREC_F64>(const cd (&o)[4][3]) {
+// FP64 sum of squares of an FP64 site (the native FP64 hop's norm).
+__device__ __forceinline__ double site_norm2_d(const cd (&o)[4][3]) {
   double s = 0.;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) s += o[k / 3][k % 3].re * o[k / 3][k % 3].re + o[k / 3][k % 3].im * o[k / 3][k % 3].im;
-  float h = (float)s;
-  return dwacc{h, (float)(s - (double)h)};
+  for (int k = 0; k < 12; ++k) {
+    s = fma(o[k / 3][k % 3].re, o[k / 3][k % 3].re, s);
+    s = fma(o[k / 3][k % 3].im, o[k / 3][k % 3].im, s);
+  }
+  return s;
 }
 template <int PREC> __device__ __forceinline__ dwacc site_norm2_f(const cf (&o)[4][3]) {
   float s = 0.f;

@@ -195,18 +195,22 @@ __device__ __forceinline__ void reconstruct_half_mu(int mu, const p2 (&r)[3], p2
   }
 }
 
-// acc = (H_{p,1-p} in)(idx) for output site idx of parity p (DAG: the
-// adjoint hop), unnormalised double-word accumulators.  dsm: this block's
-// kDwpSmem bytes of shared memory; blockDim.x must be kHopThreads.
+// acc = the sum over the hops d = d0, d0 + dstep, ... (nd of them; hop d
+// has mu = d/2 and is backward when d is odd) of H_{p,1-p} in at output site
+// idx of parity p (DAG: the adjoint hop), unnormalised double-word
+// accumulators.  All eight hops (d0 = 0, dstep = 1, nd = 8) give
+// (H_{p,1-p} in)(idx).  dsm: this block's kDwpSmem bytes of shared memory;
+// blockDim.x must be kHopThreads.
 //
-// Copies run one hop ahead: the links of hop d + 1 are issued when hop d
-// starts (two link stages), the neighbour spinor of hop d + 1 as soon as hop
-// d's has been read into registers and projected (one stage).  Every thread
-// reads and overwrites only its own column, so no block barrier is needed;
-// the completed-group wait of each hop covers both of its copies.
+// Copies run one hop ahead: the links of the next hop are issued when hop d
+// starts (two link stages), the neighbour spinor of the next hop as soon as
+// hop d's has been read into registers and projected (one stage).  Every
+// thread reads and overwrites only its own column, so no block barrier is
+// needed; the completed-group wait of each hop covers both of its copies.
 template <bool DAG>
-__device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, const float4 *gauge,
-                                             const Geom &g, int p, int64_t idx, p2 (&acc)[4][3]) {
+__device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, const float4 *gauge,
+                                             const Geom &g, int p, int64_t idx, int d0, int dstep,
+                                             int nd, p2 (&acc)[4][3]) {
   const int64_t vh = g.vh;
   int x, y, z, t;
   cb_coords(g, idx, p, x, y, z, t);
@@ -217,19 +221,21 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
   const int tid = threadIdx.x;
   float4 *const lnk = dsm + kDwpStageChunks * kHopThreads;  // two link stages
   bool neg_next;
-  int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
+  int64_t nb = hop_neighbour(g, x, y, z, t, d0, neg_next);
   stage_hop_p(dsm, in, vh, nb);
-  stage_link_p(lnk, gauge, vh, p, 0, idx, nb);
+  stage_link_p(lnk, gauge, vh, p, d0, idx, nb);
   cp_async_commit();
 #pragma unroll 1
-  for (int d = 0; d < 8; ++d) {
+  for (int j = 0; j < nd; ++j) {
+    const int d = d0 + j * dstep;
     const bool neg = neg_next;
     const int mu = d >> 1;
     const bool bwd = (d & 1) != 0;
     const f2 cc = f2_make(1.f, bwd ? -1.f : 1.f);  // conjugation of the adjoint link
-    if (d < 7) {  // the other link stage was read during hop d - 1
-      nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-      stage_link_p(lnk + ((d + 1) & 1) * kDwpLinkChunks * kHopThreads, gauge, vh, p, d + 1, idx, nb);
+    const bool more = j + 1 < nd;
+    if (more) {  // the other link stage was read during the previous hop
+      nb = hop_neighbour(g, x, y, z, t, d + dstep, neg_next);
+      stage_link_p(lnk + ((j + 1) & 1) * kDwpLinkChunks * kHopThreads, gauge, vh, p, d + dstep, idx, nb);
     }
     cp_async_commit();
     cp_async_wait1();  // this thread's spinor and link copies of hop d have landed
@@ -238,7 +244,7 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
     for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(dsm + k * kHopThreads + tid);
     p2 W[3][3];
     {
-      const float4 *ls = lnk + (d & 1) * kDwpLinkChunks * kHopThreads + tid;
+      const float4 *ls = lnk + (j & 1) * kDwpLinkChunks * kHopThreads + tid;
 #pragma unroll
       for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = ld_p2(ls + k * kHopThreads);
     }
@@ -250,7 +256,7 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
       case 2: project_p<2>(psi, h, S); break;
       default: project_p<3>(psi, h, S);
     }
-    if (d < 7) stage_hop_p(dsm, in, vh, nb);  // the spinor stage has been read
+    if (more) stage_hop_p(dsm, in, vh, nb);  // the spinor stage has been read
     cp_async_commit();
     if (neg) {
       const f2 mm = f2_make(-1.f, -1.f);
@@ -273,30 +279,56 @@ __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, cons
   }
 }
 
-// out = a x + b acc (AXPY) or b acc, each a double-word scalar given as a
-// (hi, lo) float pair; returns this site's ||out||^2 when NORM.
-template <bool AXPY, bool NORM>
-__device__ __forceinline__ dwacc dwp_store(const p2 (&acc)[4][3], float4 *out_base,
-                                           const float4 *x_base, int64_t vh, int64_t idx,
-                                           float2 a_split, float2 b_split) {
+// (H_{p,1-p} in)(idx): all eight hops in one thread.
+template <bool DAG>
+__device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, const float4 *gauge,
+                                             const Geom &g, int p, int64_t idx, p2 (&acc)[4][3]) {
+  dwp_hop_dirs<DAG>(dsm, in, gauge, g, p, idx, 0, 1, 8, acc);
+}
+
+// Two threads per output site (lanes 2i and 2i + 1 of a warp, q = lane & 1):
+// thread q runs the forward (q = 0) or backward (q = 1) hops of the four
+// directions, then the pair exchanges partial sums so that thread q holds
+// the whole result of spins 2q and 2q + 1, components 6q .. 6q + 5 in the
+// order of the spinor layout.  Every lane of the warp must call this.
+__device__ __forceinline__ void dwp_pair_combine(const p2 (&acc)[4][3], int q, p2 (&o)[6]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const p2 up = acc[k / 3][k % 3], dn = acc[2 + k / 3][k % 3];
+    const p2 keep = q ? dn : up, send = q ? up : dn;
+    p2 recv;
+    recv.h = __shfl_xor_sync(0xffffffffu, send.h, 1);
+    recv.l = __shfl_xor_sync(0xffffffffu, send.l, 1);
+    o[k] = p2_add(keep, recv);
+  }
+}
+
+// out = a x + b v (AXPY) or b v for NC consecutive components k0 .. k0 + NC - 1
+// of the site's spinor, each scalar a double-word (hi, lo) float pair;
+// returns their contribution to ||out||^2 when NORM.
+template <bool AXPY, bool NORM, int NC>
+__device__ __forceinline__ dwacc dwp_store_chunks(const p2 (&v)[NC], int k0, float4 *out_base,
+                                                  const float4 *x_base, int64_t vh, int64_t idx,
+                                                  float2 a_split, float2 b_split) {
   const f2 bh = f2_make(b_split.x, b_split.x);
   const mul2 Bm{bh, f2_make(b_split.y, b_split.y)};
   const f2 ah = f2_make(a_split.x, a_split.x);
   const mul2 Am{ah, f2_make(a_split.y, a_split.y)};
   acc2 nq{0ull, 0ull};
-  ulonglong2 *__restrict__ o = reinterpret_cast<ulonglong2 *>(out_base) + idx;
-  p2 xs[12];
+  ulonglong2 *__restrict__ o = reinterpret_cast<ulonglong2 *>(out_base) + idx + (int64_t)k0 * vh;
+  p2 xs[NC];
   if (AXPY) {  // all loads before the first store
-    const ulonglong2 *__restrict__ xp = reinterpret_cast<const ulonglong2 *>(x_base) + idx;
+    const ulonglong2 *__restrict__ xp =
+        reinterpret_cast<const ulonglong2 *>(x_base) + idx + (int64_t)k0 * vh;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const ulonglong2 v = __ldg(xp + k * vh);
-      xs[k] = p2{v.x, v.y};
+    for (int k = 0; k < NC; ++k) {
+      const ulonglong2 u = __ldg(xp + k * vh);
+      xs[k] = p2{u.x, u.y};
     }
   }
 #pragma unroll
-  for (int k = 0; k < 12; ++k) {
-    acc2 R = acc2_first(Bm, p2_norm(acc[k / 3][k % 3]));
+  for (int k = 0; k < NC; ++k) {
+    acc2 R = acc2_first(Bm, p2_norm(v[k]));
     if (AXPY) acc2_mad(R, Am, xs[k]);
     const p2 q = p2_norm(acc2_get(R));
     o[k * vh] = make_ulonglong2(q.h, q.l);
@@ -316,6 +348,18 @@ __device__ __forceinline__ dwacc dwp_store(const p2 (&acc)[4][3], float4 *out_ba
     nrm = dwacc{s, __fadd_rn(__fadd_rn(c0, c1), e)};
   }
   return nrm;
+}
+
+// out = a x + b acc (AXPY) or b acc for the whole site; returns ||out||^2
+// when NORM.
+template <bool AXPY, bool NORM>
+__device__ __forceinline__ dwacc dwp_store(const p2 (&acc)[4][3], float4 *out_base,
+                                           const float4 *x_base, int64_t vh, int64_t idx,
+                                           float2 a_split, float2 b_split) {
+  p2 v[12];
+#pragma unroll
+  for (int k = 0; k < 12; ++k) v[k] = acc[k / 3][k % 3];
+  return dwp_store_chunks<AXPY, NORM, 12>(v, 0, out_base, x_base, vh, idx, a_split, b_split);
 }
 
 }  // namespace jqcd

@@ -28,9 +28,21 @@ struct HopParams {
 };
 
 // out_p = a x_p + b H_{p,1-p} in (dag: adjoint hop); partials get per-block
-// ||out||^2 when norm.
+// ||out||^2 when norm: hop_norm_partials(prec, vh) of them.
 cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool norm,
                        cudaStream_t s);
+
+// The double-word hops run two threads per output site on lattices small
+// enough that the two-thread grid fits in one wave of resident blocks (and
+// of at most JQCD_DWP_SPLIT_MAX_VH sites per parity), where one thread per
+// site leaves the GPU short of warps; their grids (and per-block partial
+// sums) are then twice as many blocks.
+#ifndef JQCD_DWP_SPLIT_MAX_VH
+#define JQCD_DWP_SPLIT_MAX_VH 65536
+#endif
+bool dw_hop_split(int64_t vh);
+unsigned dw_hop_blocks(int64_t vh);                 // blocks of a double-word hop launch
+unsigned hop_norm_partials(int prec, int64_t vh);   // partials of a hop launch with norm
 
 // ---- layouts ----------------------------------------------------------------
 // Canonical FP64 links on the device -> every device layout requested
@@ -89,6 +101,24 @@ cudaError_t launch_dw_cg_update(float4 *x, float4 *r, const float4 *p, const flo
 // p = r + beta p (skipped when S->done)
 cudaError_t launch_dw_xpay(float4 *p, const float4 *r, int64_t n, const SolverScalars *S,
                            cudaStream_t s);
+
+// ---- native FP64 vectors (blas_f64.cu): flat double2 = one complex FP64 ----
+cudaError_t launch_f64_copy(double2 *dst, const double2 *src, int64_t n, cudaStream_t s);
+cudaError_t launch_f64_zero(double2 *dst, int64_t n, cudaStream_t s);
+cudaError_t launch_f64_norm2(const double2 *a, int64_t n, double *partials, cudaStream_t s);
+// r = b - y, partials of ||r||^2
+cudaError_t launch_f64_xmy_norm(double2 *r, const double2 *b, const double2 *y, int64_t n,
+                                double *partials, cudaStream_t s);
+// x += alpha p; r -= alpha Ap; partials ||r||^2 (alpha = S->alpha; skipped when S->halt)
+cudaError_t launch_f64_cg_update(double2 *x, double2 *r, const double2 *p, const double2 *Ap,
+                                 int64_t n, const SolverScalars *S, double *partials,
+                                 cudaStream_t s);
+// p = r + beta p (beta = S->beta; skipped when S->halt)
+cudaError_t launch_f64_xpay(double2 *p, const double2 *r, int64_t n, const SolverScalars *S,
+                            cudaStream_t s);
+// double-word <-> FP64 complex vectors of n elements (widening is exact)
+cudaError_t launch_dw_to_f64(double2 *dst, const float4 *src, int64_t n, cudaStream_t s);
+cudaError_t launch_f64_to_dw(float4 *dst, const double2 *src, int64_t n, cudaStream_t s);
 
 // ---- mixed precision (inner CG in FP32 or FP16+norm, even parity) ----------
 // p = r_s + beta p in the hop precision (guarded)

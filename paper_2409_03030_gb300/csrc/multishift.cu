@@ -243,7 +243,7 @@ jqcd_status solve_multishift(GaugeEntry &G, const jqcd_solve_params &P, int nshi
   const int64_t vh = G.g.vh;
   const int64_t n = 12 * vh;  // complex double-word numbers of one parity
   const int nblas = (int)blas_blocks(n);
-  const int nhop = (int)hop_blocks(vh);
+  const int nhop = (int)dw_hop_blocks(vh);  // partials of the double-word hops
   float4 *rhs = G.vec_even(G.vrhs), *r = G.vec_even(G.vr), *pb = G.vec_even(G.vp), *Ap = G.vec_even(G.vAp);
   MsVectors V;
   memset(&V, 0, sizeof V);

@@ -49,7 +49,7 @@ cudaError_t GaugeEntry::ensure_canon() {
 }
 
 int GaugeEntry::n_partials() const {
-  return 2 * (int)hop_blocks(g.vh) + (int)blas_blocks(24 * g.vh) + 64;
+  return 2 * (int)dw_hop_blocks(g.vh) + (int)blas_blocks(24 * g.vh) + 64;
 }
 
 cudaError_t GaugeEntry::ensure_reduce() {
@@ -101,6 +101,16 @@ cudaError_t GaugeEntry::ensure_mixed(int hop_prec) {
   void **vs[] = {&mp[k], &mw[k], &mt[k]};
   for (void **v : vs)
     if (e == cudaSuccess && !*v) e = alloc(v, hb);
+  return e;
+}
+
+cudaError_t GaugeEntry::ensure_f64() {
+  cudaError_t e = ensure_canon();
+  if (e == cudaSuccess) e = ensure_reduce();
+  const size_t full = 2 * spinor_parity_bytes(PREC_F64, g.vh);
+  double2 **vs[] = {&fb, &fsol, &fr, &fp, &fAp, &fw, &ft, &frhs};
+  for (double2 **v : vs)
+    if (e == cudaSuccess && !*v) e = alloc_t(v, full);
   return e;
 }
 
@@ -156,10 +166,10 @@ cudaError_t apply_mdagm(const GaugeEntry &G, int prec, double kappa, const void 
 namespace {
 
 // Whole-lattice D (or D^dag) on double-word vectors: out = in - kappa H in,
-// optional per-block partials of ||out||^2 (2 * hop_blocks entries).
+// optional per-block partials of ||out||^2 (2 * dw_hop_blocks entries).
 cudaError_t apply_dirac_dw(const GaugeEntry &G, double kappa, bool dag, float4 *in, float4 *out,
                            double *partials, const int *guard, cudaStream_t s) {
-  const int nb = (int)hop_blocks(G.g.vh);
+  const int nb = (int)dw_hop_blocks(G.g.vh);
   HopParams Pe = G.hop_params(PREC_DW, 0, G.vec_odd(in), G.vec_even(in), G.vec_even(out), 1.0,
                               -kappa, partials);
   Pe.guard = guard;
@@ -206,7 +216,7 @@ struct DwSystem {
 // and forms ||r||^2 itself (Ap is never stored), beta, p = r + beta p.
 cudaError_t dw_eo_cg_iteration(GaugeEntry &G, double kappa, SolverScalars *S, cudaStream_t s) {
   const double k2 = -kappa * kappa;
-  const int nb = (int)hop_blocks(G.g.vh);
+  const int nb = (int)dw_hop_blocks(G.g.vh);
   const int *guard = &S->halt;
   float4 *t = G.vec_odd(G.vt), *w = G.vec_even(G.vw);
   HopParams P = G.hop_params(PREC_DW, 1, G.vp, nullptr, t, 0.0, 1.0, nullptr);
@@ -264,6 +274,38 @@ cudaError_t lp_eo_cg_iteration(GaugeEntry &G, int hp, int mk, double kappa, Solv
   return launch_mixed_xpay(hp, p, (const float4 *)G.mr, G.g.vh, S, s);
 }
 
+// ---- native FP64 system (JQCD_CG_F64) -------------------------------------
+double2 *f64_even(double2 *v) { return v; }
+double2 *f64_odd(const GaugeEntry &G, double2 *v) { return v + 12 * G.g.vh; }
+
+// Whole-lattice D (or D^dag) on FP64 vectors: out = in - kappa H in, optional
+// per-block partials of ||out||^2 (2 * hop_blocks entries).
+cudaError_t apply_dirac_f64(const GaugeEntry &G, double kappa, bool dag, double2 *in, double2 *out,
+                            double *partials, const int *guard, cudaStream_t s) {
+  const int nb = (int)hop_blocks(G.g.vh);
+  HopParams Pe = G.hop_params(PREC_F64, 0, f64_odd(G, in), f64_even(in), f64_even(out), 1.0,
+                              -kappa, partials);
+  Pe.guard = guard;
+  cudaError_t e = launch_hop(PREC_F64, Pe, dag, true, partials != nullptr, s);
+  if (e) return e;
+  HopParams Po = G.hop_params(PREC_F64, 1, f64_even(in), f64_odd(G, in), f64_odd(G, out), 1.0,
+                              -kappa, partials ? partials + nb : nullptr);
+  Po.guard = guard;
+  return launch_hop(PREC_F64, Po, dag, true, partials != nullptr, s);
+}
+
+// out = A in for the FP64 CG system (A = Mhat^dag Mhat on the even sites, or
+// D^dag D on the whole lattice); partials <- ||M in||^2 per hop block.
+cudaError_t apply_a_f64(GaugeEntry &G, double kappa, bool eo, double2 *in, double2 *out,
+                        double *partials, const int *guard, cudaStream_t s) {
+  if (eo)
+    return apply_mdagm(G, PREC_F64, kappa, in, out, f64_odd(G, G.ft), f64_even(G.fw), partials,
+                       guard, s);
+  cudaError_t e = apply_dirac_f64(G, kappa, false, in, G.fw, partials, guard, s);
+  if (e) return e;
+  return apply_dirac_f64(G, kappa, true, G.fw, out, nullptr, guard, s);
+}
+
 }  // namespace
 
 // Bytes per output site of one hop in precision `prec` (+ the axpy operand).
@@ -284,7 +326,7 @@ static jqcd_status solve_cg(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
   const bool mixed = P.mode == JQCD_CG_MIXED_F32 || P.mode == JQCD_CG_MIXED_F16;
   const int hp = P.mode == JQCD_CG_MIXED_F16 ? PREC_F16N : PREC_F32;
   const int mk = hp == PREC_F16N ? 1 : 0;  // index of the hop-precision vectors
-  DwSystem A{G, P.kappa, eo, s, (eo ? 12 : 24) * G.g.vh, (eo ? 1 : 2) * (int)hop_blocks(G.g.vh)};
+  DwSystem A{G, P.kappa, eo, s, (eo ? 12 : 24) * G.g.vh, (eo ? 1 : 2) * (int)dw_hop_blocks(G.g.vh)};
   const int nblas = (int)blas_blocks(A.n);
   const double tol2 = P.tol * P.tol;
   const double delta = P.delta > 0.0 ? P.delta : 0.01;
@@ -447,14 +489,185 @@ static jqcd_status solve_cg(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
 #undef CKS
 }
 
-jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
-                           jqcd_solve_info *info, std::string *msg) {
+// Plain conjugate gradient in native FP64: every vector, operator and
+// reduction in IEEE double (the hop is hop_kernel<PREC_F64>, the vector
+// kernels blas_f64.cu).  Same iteration, stopping rule, true-residual check
+// and restarts as the double-word solver; b in G.fb, x (start vector when
+// use_x0) and the solution in G.fsol, whole lattice in the JQCD_PREC_F64
+// layout.  One iteration is eight launches: t = H_oe p; w = p - k^2 H_eo t
+// with ||w||^2; alpha; t = H^dag_oe w; Ap = w - k^2 H^dag_eo t; x, r, ||r||^2;
+// beta; p = r + beta p.
+static jqcd_status solve_cg_f64(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                                jqcd_solve_info *info, std::string *msg) {
+  const bool eo = P.eo != 0;
+  const int64_t vh = G.g.vh;
+  const int64_t n = (eo ? 12 : 24) * vh;  // complex elements of the system's vectors
+  const int nblas = (int)blas_blocks(n);
+  const int nhop = (eo ? 1 : 2) * (int)hop_blocks(vh);
+  const double tol2 = P.tol * P.tol;
+  const double k2 = -P.kappa * P.kappa;
+  SolverScalars *S = G.S;
+  long long hops = 0;
+  double hop_bytes = 0.0;
+  auto count = [&](int plain, int axpy) {
+    hops += plain + axpy;
+    hop_bytes += (double)vh * (1536.0 * (plain + axpy) + 192.0 * axpy);
+  };
+  auto count_a = [&]() { count(eo ? 2 : 0, eo ? 2 : 4); };
+#define CKS(call)                                              \
+  do {                                                         \
+    cudaError_t e_ = (call);                                   \
+    if (e_ != cudaSuccess) {                                   \
+      *msg = cudaGetErrorString(e_);                           \
+      return e_ == cudaErrorMemoryAllocation ? JQCD_ENOMEM : JQCD_ECUDA; \
+    }                                                          \
+  } while (0)
+  CKS(G.ensure_f64());
+  CKS(cudaEventRecord(G.ev0, s));
+  CKS(cudaMemsetAsync(S, 0, sizeof(SolverScalars), s));
+  CKS(launch_f64_norm2(G.fb, 24 * vh, G.partials, s));  // ||b||^2 of D x = b
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * vh), &S->b2, s));
+  if (eo) {
+    // bhat_e = b_e + kappa H_eo b_o (into fw even); rhs = Mhat^dag bhat
+    HopParams Pb = G.hop_params(PREC_F64, 0, f64_odd(G, G.fb), f64_even(G.fb), f64_even(G.fw), 1.0,
+                                P.kappa, nullptr);
+    CKS(launch_hop(PREC_F64, Pb, false, true, false, s));
+    HopParams P1 = G.hop_params(PREC_F64, 1, f64_even(G.fw), nullptr, f64_odd(G, G.ft), 0.0, 1.0,
+                                nullptr);
+    CKS(launch_hop(PREC_F64, P1, true, false, false, s));
+    HopParams P2 = G.hop_params(PREC_F64, 0, f64_odd(G, G.ft), f64_even(G.fw), f64_even(G.frhs),
+                                1.0, k2, nullptr);
+    CKS(launch_hop(PREC_F64, P2, true, true, false, s));
+    count(2, 1);
+  } else {
+    CKS(apply_dirac_f64(G, P.kappa, true, G.fb, G.frhs, nullptr, nullptr, s));  // rhs = D^dag b
+    count(0, 2);
+  }
+  CKS(launch_f64_norm2(G.frhs, n, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, nblas, &S->rhs2, s));
+  if (P.use_x0) {
+    CKS(apply_a_f64(G, P.kappa, eo, G.fsol, G.fAp, nullptr, nullptr, s));
+    count_a();
+    CKS(launch_f64_xmy_norm(G.fr, G.frhs, G.fAp, n, G.partials, s));
+  } else {
+    CKS(launch_f64_zero(G.fsol, 24 * vh, s));
+    CKS(launch_f64_copy(G.fr, G.frhs, n, s));
+    CKS(launch_f64_norm2(G.fr, n, G.partials, s));
+  }
+  CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, 0.0, s));
+  CKS(launch_f64_copy(G.fp, G.fr, n, s));
+
+  int restarts = 0;
+  jqcd_status st = JQCD_OK;
+  const int *guard = &S->halt;
+  for (;;) {
+    for (;;) {
+      for (int k = 0; k < kCheckEvery; ++k) {
+        CKS(apply_a_f64(G, P.kappa, eo, G.fp, G.fAp, G.partials, guard, s));
+        CKS(launch_cg_alpha(G.partials, nhop, S, s));
+        CKS(launch_f64_cg_update(G.fsol, G.fr, G.fp, G.fAp, n, S, G.partials, s));
+        CKS(launch_cg_beta(G.partials, nblas, S, s));
+        CKS(launch_f64_xpay(G.fp, G.fr, n, S, s));
+      }
+      CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+      CKS(cudaStreamSynchronize(s));
+      if (P.verbose >= 3)
+        fprintf(stderr, "jqcd cg (fp64): iter %d  |r|/|rhs| = %.3e\n", G.S_host->iters,
+                G.S_host->rhs2 > 0 ? std::sqrt(G.S_host->rr / G.S_host->rhs2) : 0.0);
+      if (G.S_host->done || G.S_host->iters >= P.maxiter) break;
+    }
+    if (G.S_host->done == 2) {
+      *msg = "CG breakdown (<p,Ap> <= 0 or not finite)";
+      st = JQCD_EBREAKDOWN;
+      break;
+    }
+    // true residual of the CG system
+    CKS(apply_a_f64(G, P.kappa, eo, G.fsol, G.fAp, nullptr, nullptr, s));
+    count_a();
+    CKS(launch_f64_xmy_norm(G.fr, G.frhs, G.fAp, n, G.partials, s));
+    CKS(launch_finalize_sum(G.partials, nblas, &S->true_rr, s));
+    CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+    CKS(cudaStreamSynchronize(s));
+    if (G.S_host->true_rr <= tol2 * G.S_host->rhs2) break;
+    if (G.S_host->iters >= P.maxiter || restarts >= kMaxRestarts) {
+      st = JQCD_ENOCONV;
+      *msg = "maximum iterations reached";
+      break;
+    }
+    ++restarts;  // restart from x with the recomputed residual
+    CKS(launch_cg_start(G.partials, nblas, S, tol2, P.maxiter, 0.0, s));
+    CKS(launch_f64_copy(G.fp, G.fr, n, s));
+  }
+  if (eo) {  // x_o = b_o + kappa H_oe x_e
+    HopParams Pr = G.hop_params(PREC_F64, 1, f64_even(G.fsol), f64_odd(G, G.fb),
+                                f64_odd(G, G.fsol), 1.0, P.kappa, nullptr);
+    CKS(launch_hop(PREC_F64, Pr, false, true, false, s));
+    count(0, 1);
+  }
+  CKS(cudaEventRecord(G.ev1, s));
+  // ||b - D x||^2 (not part of the timed solve)
+  CKS(apply_dirac_f64(G, P.kappa, false, G.fsol, G.fw, nullptr, nullptr, s));
+  CKS(launch_f64_xmy_norm(G.fAp, G.fb, G.fw, 24 * vh, G.partials, s));
+  CKS(launch_finalize_sum(G.partials, (int)blas_blocks(24 * vh), &S->full_rr, s));
+  CKS(cudaMemcpyAsync(G.S_host, S, sizeof(SolverScalars), cudaMemcpyDeviceToHost, s));
+  CKS(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  CKS(cudaEventElapsedTime(&ms, G.ev0, G.ev1));
+  const SolverScalars &H = *G.S_host;
+  for (int i = 0; i < H.iters; ++i) count_a();  // loop hops: four per completed iteration
+  info->iters = H.iters;
+  info->restarts = restarts;
+  info->reliable_updates = 0;
+  info->true_rel_resid = H.rhs2 > 0 ? std::sqrt(H.true_rr / H.rhs2) : 0.0;
+  info->full_rel_resid = H.b2 > 0 ? std::sqrt(H.full_rr / H.b2) : 0.0;
+  info->gpu_seconds = ms * 1e-3;
+  info->hop_count = (double)hops;
+  info->hop_bytes = hop_bytes;
+  return st;
+#undef CKS
+}
+
+static jqcd_status check_params(const jqcd_solve_params &P, std::string *msg) {
   if (!(P.tol > 0.0) || P.maxiter < 1 || !(P.kappa >= 0.0)) {
     *msg = "bad solve parameters (tol > 0, maxiter >= 1, kappa >= 0)";
     return JQCD_EINVAL;
   }
+  return JQCD_OK;
+}
+
+jqcd_status solve_resident_f64(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                               jqcd_solve_info *info, std::string *msg) {
+  jqcd_status st = check_params(P, msg);
+  if (st) return st;
+  return solve_cg_f64(G, P, s, info, msg);
+}
+
+jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                           jqcd_solve_info *info, std::string *msg) {
+  jqcd_status st = check_params(P, msg);
+  if (st) return st;
   switch (P.mode) {
     case JQCD_CG_DW: return solve_cg(G, P, s, info, msg);
+    case JQCD_CG_F64: {
+      // double-word b (and start vector) widened exactly to FP64, the FP64
+      // solution rounded back to double-word
+      cudaError_t e = G.ensure_f64();
+      if (e == cudaSuccess) e = launch_dw_to_f64(G.fb, G.vb, 24 * G.g.vh, s);
+      if (e == cudaSuccess && P.use_x0) e = launch_dw_to_f64(G.fsol, G.vsol, 24 * G.g.vh, s);
+      if (e != cudaSuccess) {
+        *msg = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? JQCD_ENOMEM : JQCD_ECUDA;
+      }
+      st = solve_cg_f64(G, P, s, info, msg);
+      if (st == JQCD_OK || st == JQCD_ENOCONV) {
+        e = launch_f64_to_dw(G.vsol, G.fsol, 24 * G.g.vh, s);
+        if (e != cudaSuccess) {
+          *msg = cudaGetErrorString(e);
+          return JQCD_ECUDA;
+        }
+      }
+      return st;
+    }
     case JQCD_CG_MIXED_F32:
     case JQCD_CG_MIXED_F16:
       if (!P.eo) {

@@ -108,8 +108,15 @@ cudaError_t launch_hop_lp_cg(int prec, const HopParams &P, const void *p, float4
                              const SolverScalars *S, cudaStream_t s);
 
 // Run the solve of D x = b for the double-word b in G.vb; the solution is
-// left in G.vsol (whole lattice, double-word).
+// left in G.vsol (whole lattice, double-word).  Mode JQCD_CG_F64 widens b to
+// FP64, solves in FP64 and rounds the solution back to double-word.
 jqcd_status solve_resident(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
                            jqcd_solve_info *info, std::string *msg);
+
+// The native FP64 solve (mode JQCD_CG_F64, any eo) of D x = b for the FP64 b
+// in G.fb (whole lattice, JQCD_PREC_F64 layout); start vector (use_x0) and
+// solution in G.fsol.  The caller has run G.ensure_f64().
+jqcd_status solve_resident_f64(GaugeEntry &G, const jqcd_solve_params &P, cudaStream_t s,
+                               jqcd_solve_info *info, std::string *msg);
 
 }  // namespace jqcd

@@ -23,6 +23,7 @@ PREC_DW, PREC_F32, PREC_F16N, PREC_F64 = 0, 1, 2, 3
 CG_DW, CG_F64, CG_MIXED_F32, CG_MIXED_F16 = 0, 1, 2, 3
 PRECS = {"dw": PREC_DW, "f32": PREC_F32, "f16n": PREC_F16N, "f64": PREC_F64}
 MODES = {"dw": CG_DW, "f64": CG_F64, "mixed_f32": CG_MIXED_F32, "mixed_f16": CG_MIXED_F16}
+NOALLOC_MAX_SITES_PER_PARITY = 16384 * 128  # JQCD_NOALLOC_MAX_SITES_PER_PARITY
 
 
 class JqcdError(RuntimeError):

@@ -72,6 +72,29 @@ def test_struct_layout_matches_c(tmp_path):
     assert got == want
 
 
+def test_constants_match_header(tmp_path):
+    """Status codes, precisions, solver modes and the allocation-free limit of
+    the binding equal the header's values (compiled with gcc)."""
+    from paper_2409_03030_gb300 import jqcd
+    names = ["JQCD_OK", "JQCD_EINVAL", "JQCD_ENOMEM", "JQCD_ECUDA", "JQCD_ENOCONV", "JQCD_EBUSY",
+             "JQCD_ETIMEOUT", "JQCD_ENOTFOUND", "JQCD_EBREAKDOWN", "JQCD_PENDING", "JQCD_PREC_DW",
+             "JQCD_PREC_F32", "JQCD_PREC_F16N", "JQCD_PREC_F64", "JQCD_CG_DW", "JQCD_CG_F64",
+             "JQCD_CG_MIXED_F32", "JQCD_CG_MIXED_F16", "JQCD_NOALLOC_MAX_SITES_PER_PARITY"]
+    src = tmp_path / "consts.c"
+    src.write_text('#include "jqcd.h"\n#include <stdio.h>\nint main(void){'
+                   + "".join(f'printf("%ld\\n", (long)({n}));' for n in names) + "return 0;}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    want = [jqcd.OK, jqcd.EINVAL, jqcd.ENOMEM, jqcd.ECUDA, jqcd.ENOCONV, jqcd.EBUSY, jqcd.ETIMEOUT,
+            jqcd.ENOTFOUND, jqcd.EBREAKDOWN, jqcd.PENDING, jqcd.PREC_DW, jqcd.PREC_F32,
+            jqcd.PREC_F16N, jqcd.PREC_F64, jqcd.CG_DW, jqcd.CG_F64, jqcd.CG_MIXED_F32,
+            jqcd.CG_MIXED_F16, jqcd.NOALLOC_MAX_SITES_PER_PARITY]
+    assert got == want
+
+
 def test_init_without_gpu_fails_cleanly():
     torch = pytest.importorskip("torch")
     if torch.cuda.is_available():

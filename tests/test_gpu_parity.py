@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conditioning import free_cond_eo
 from paper_2409_03030_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -162,6 +163,38 @@ def test_hop_dw_magnitudes(jq, case, dagger):
     g.free()
 
 
+@pytest.mark.parametrize("dagger", [0, 1])
+def test_hop_dw_one_thread_per_site_ragged(jq, dagger):
+    """Double-word hop above the two-threads-per-site size (10^3x134: 67,000
+    sites per parity, a ragged last block of one thread per site), with the
+    fused axpy and norm, against the oracle.  Every smaller lattice of these
+    tests runs the two-threads-per-site kernels."""
+    jqcd, ctx = jq
+    import torch
+    dims = (10, 10, 10, 134)
+    assert np.prod(dims) // 2 > 65536 and (np.prod(dims) // 2) % 128 != 0
+    U = synth.gauge(dims, "expi", eps=0.3, seed=41)
+    g = ctx.gauge_upload(dims, U, t_antiperiodic=True)
+    psi = synth.gaussian_spinor(dims, seed=42)
+    xs = synth.gaussian_spinor(dims, seed=43)
+    pe, po = g.pack(psi, 0)
+    xe, xo = g.pack(xs, 0)
+    norm = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for p in (0, 1):
+        want = 0.7 * only_parity(dims, xs, p) - 0.12 * oracle.hop(dims, U, psi, dagger=bool(dagger),
+                                                                   out_parity=p)
+        out = g.empty(0)
+        g.dslash_eo(0, p, dagger, po if p == 0 else pe, xe if p == 0 else xo, out, 0.7, -0.12,
+                    norm2=norm)
+        ev = out if p == 0 else g.empty(0).zero_()
+        od = out if p == 1 else g.empty(0).zero_()
+        got = only_parity(dims, g.unpack(ev, od, 0), p)
+        assert rel(got, want) <= TOL[0], (p, rel(got, want))
+        n_want = np.linalg.norm(got) ** 2
+        assert abs(norm.item() - n_want) <= 1e-11 * n_want
+    g.free()
+
+
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 6, 6, 10)])
 @pytest.mark.parametrize("prec", PRECS)
 def test_mdagm_vs_oracle(jq, dims, prec):
@@ -300,7 +333,8 @@ def test_hop_full_size_sampled(jq):
 def test_mixed_cg_16x4(jq, mode):
     """Mixed-precision CG (FP32 or FP16+norm inner, double-word reliable
     updates) reaches the requested true residual of the even-odd system, and
-    agrees with the double-word solve within the conditioning bound."""
+    agrees with the FP64 oracle's solution and with the double-word solve
+    within the conditioning bound cond * (both residuals)."""
     jqcd, ctx = jq
     dims = (16, 16, 16, 16)
     U = synth.gauge(dims, "expi", eps=0.3, seed=2)
@@ -311,15 +345,110 @@ def test_mixed_cg_16x4(jq, mode):
     res = system_residual(dims, U, b, x, 0.12, True)
     assert res <= 1e-10 * (1 + 1e-6), res
     assert abs(info["true_rel_resid"] - res) <= 1e-2 * 1e-10 + 1e-14
+    xo, _, res_o, _, conv = oracle.solve(dims, U, b, 0.12, eo=True, tol=1e-13)
+    assert conv
+    bound = free_cond_eo(dims, 0.12) * (res + res_o)
+    err = rel(only_parity(dims, x, 0), only_parity(dims, xo, 0))
+    assert err <= bound, (err, bound)
     xd, info_d, st_d = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.CG_DW)
     assert rel(x, xd) < 1e-7
     g.free()
 
 
+@pytest.mark.parametrize("eo", [False, True])
+def test_cg_f64_config0_4x4(jq, eo):
+    """Plain FP64 CG (JQCD_CG_F64: native FP64 hops, vectors and reductions):
+    4^4 Haar links, kappa 0.10, tol 1e-12, whole-lattice D^dag D and even-odd.
+    FP64 on both sides: the library's own true residual agrees with the
+    oracle's recomputation to 1e-3 of tol, and x with the oracle's solution."""
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, "haar", seed=1)
+    b = synth.gaussian_spinor(dims, seed=1)
+    g = ctx.gauge_upload(dims, U)
+    tol = 1e-12
+    x, info, st = g.cg_solve(b, 0.10, tol=tol, eo=eo, mode=jqcd.CG_F64)
+    assert st == 0 and info["iters"] > 0 and info["reliable_updates"] == 0
+    res = system_residual(dims, U, b, x, 0.10, eo)
+    assert res <= tol * (1 + 1e-6), res
+    assert abs(info["true_rel_resid"] - res) <= 1e-3 * tol
+    full = rel(oracle.dirac(dims, U, x, 0.10), b)
+    assert abs(info["full_rel_resid"] - full) <= 1e-14
+    xo, *_ = oracle.solve(dims, U, b, 0.10, eo=eo, tol=1e-13)
+    assert rel(x, xo) < 1e-10
+    xd, _, _ = g.cg_solve(b, 0.10, tol=tol, eo=eo, mode=jqcd.CG_DW)
+    assert rel(x, xd) < 1e-10
+    g.free()
+
+
+def test_cg_f64_config1_16x4(jq):
+    """16^4, exp(i 0.3 H) links, kappa 0.12, even-odd, tol 1e-10 in plain FP64:
+    the oracle's residual, the oracle's solution within cond * residuals, and
+    the device-buffer entry (double-word b widened to FP64, x rounded back)
+    giving the same solution to the double-word rounding of b and x."""
+    jqcd, ctx = jq
+    dims = (16, 16, 16, 16)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=2)
+    b = synth.gaussian_spinor(dims, seed=3)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-10, eo=True, mode=jqcd.CG_F64)
+    assert st == 0
+    res = system_residual(dims, U, b, x, 0.12, True)
+    assert res <= 1e-10 * (1 + 1e-6), res
+    assert abs(info["true_rel_resid"] - res) <= 1e-3 * 1e-10
+    xo, _, res_o, _, conv = oracle.solve(dims, U, b, 0.12, eo=True, tol=1e-13)
+    err = rel(only_parity(dims, x, 0), only_parity(dims, xo, 0))
+    assert err <= free_cond_eo(dims, 0.12) * (res + res_o), err
+    be, bo = g.pack(b, jqcd.PREC_DW)
+    xe, xo_dev = g.empty(jqcd.PREC_DW), g.empty(jqcd.PREC_DW)
+    info_d, st_d = g.cg_solve_dev(be, bo, xe, xo_dev, 0.12, tol=1e-10, eo=True, mode=jqcd.CG_F64)
+    assert st_d == 0
+    xdev = g.unpack(xe, xo_dev, jqcd.PREC_DW)
+    assert rel(xdev, x) <= 1e-9
+    g.free()
+
+
+def test_cg_f64_zero_source_and_limits(jq):
+    jqcd, ctx = jq
+    dims = (4, 4, 4, 4)
+    U = synth.gauge(dims, "haar", seed=5)
+    g = ctx.gauge_upload(dims, U)
+    for eo in (True, False):
+        x, info, st = g.cg_solve(np.zeros(synth.spinor_shape(dims), complex), 0.1, tol=1e-10,
+                                 eo=eo, mode=jqcd.CG_F64)
+        assert st == 0 and info["iters"] == 0 and not np.any(x)
+    b = synth.gaussian_spinor(dims, seed=6)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-15, maxiter=3, mode=jqcd.CG_F64, check=False)
+    assert st == jqcd.ENOCONV and info["iters"] >= 3
+    # restart from the returned iterate (use_x0) reaches the tolerance
+    x2, info2, st2 = g.cg_solve(b, 0.12, tol=1e-12, mode=jqcd.CG_F64, x0=x)
+    assert st2 == 0 and system_residual(dims, U, b, x2, 0.12, True) <= 1e-12 * (1 + 1e-6)
+    g.free()
+
+
+@pytest.mark.parametrize("mode", ["dw", "mixed_f16", "mixed_f32", "f64"])
+def test_tight_tol_24x48_oracle_residual(jq, mode):
+    """tol 1e-12 on the 24^3x48 lattice (exp(i 0.3 H), kappa 0.12): the CG
+    system's residual recomputed in FP64 by the oracle from the returned x
+    meets the tolerance, in every solver mode."""
+    jqcd, ctx = jq
+    dims = (24, 24, 24, 48)
+    U = synth.gauge(dims, "expi", eps=0.3, seed=1)
+    b = synth.gaussian_spinor(dims, seed=2)
+    g = ctx.gauge_upload(dims, U)
+    x, info, st = g.cg_solve(b, 0.12, tol=1e-12, eo=True, mode=jqcd.MODES[mode])
+    assert st == 0
+    res = system_residual(dims, U, b, x, 0.12, True)
+    assert res <= 1e-12 * (1 + 1e-6), (res, info["true_rel_resid"])
+    g.free()
+
+
 def test_mixed_cg_config2_32x64(jq):
-    """32^3x64, exp(i 0.4 H) links, kappa 0.122: FP16+norm mixed CG to 1e-10.
-    Full size: the oracle recomputes the CG system's residual from the GPU
-    solution (one Mhat^dag Mhat application in FP64)."""
+    """32^3x64, exp(i 0.4 H) links, kappa 0.122: FP16+norm mixed CG and plain
+    FP64 CG to 1e-10.  Full size: the oracle recomputes the CG system's
+    residual from each GPU solution, and solves the system itself to 1e-12;
+    each GPU solution agrees with the oracle's within cond * residuals, and
+    the two GPU solutions with each other."""
     jqcd, ctx = jq
     dims = (32, 32, 32, 64)
     U = synth.gauge(dims, "expi", eps=0.4, seed=4)
@@ -329,6 +458,17 @@ def test_mixed_cg_config2_32x64(jq):
     assert st == 0
     res = system_residual(dims, U, b, x, 0.122, True)
     assert res <= 1e-10 * (1 + 1e-6), res
+    x64, info64, st64 = g.cg_solve(b, 0.122, tol=1e-10, eo=True, mode=jqcd.CG_F64)
+    assert st64 == 0
+    res64 = system_residual(dims, U, b, x64, 0.122, True)
+    assert res64 <= 1e-10 * (1 + 1e-6), res64
+    xo, _, res_o, _, conv = oracle.solve(dims, U, b, 0.122, eo=True, tol=1e-12)
+    assert conv
+    cond = free_cond_eo(dims, 0.122)
+    xe, x64e, xoe = (only_parity(dims, v, 0) for v in (x, x64, xo))
+    assert rel(xe, xoe) <= cond * (res + res_o), (rel(xe, xoe), cond)
+    assert rel(x64e, xoe) <= cond * (res64 + res_o), (rel(x64e, xoe), cond)
+    assert rel(xe, x64e) <= cond * (res + res64)
     g.free()
 
 
