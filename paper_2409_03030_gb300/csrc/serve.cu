@@ -1,18 +1,26 @@
 // Solve server: continuous batching of CG solves on one GPU.
 //
 // jqcd_serve_submit queues a request (thread-safe, never blocks on the GPU).
-// One scheduler thread owns a BatchEngine on its own stream and loops:
-//   admit queued requests while a slot is free and the device memory the
-//   request needs (its slot buffers) fits the byte budget -> advance every
-//   admitted solve together by a few batched iterations -> queue the
-//   reconstruction of the solves that finished and the copy of x to the
-//   caller's buffer -> report the requests whose copy has completed (latency
-//   recorded).  Sources and solutions move on the engine's copy stream, so
-//   with pinned host buffers they overlap the iterations of other requests.
-// Requests that arrive while others iterate join at the next iteration
-// boundary; their work shares the same kernel launches (and, on the same
-// gauge field, the same link loads).  Admission is FIFO: a request that does
-// not fit waits until earlier ones finish.
+// Requests go to one of two lanes by lattice size: solves of at most
+// kSmallLaneMaxVh sites per parity to the small lane, the others to the
+// large lane.  Each lane has its own BatchEngine, stream and scheduler
+// thread, and loops:
+//   admit queued requests while a slot is free and the device memory of all
+//   slot buffers of both lanes, plus what this request adds, fits the byte
+//   budget -> advance every admitted solve of the lane together by a few
+//   batched iterations -> queue the reconstruction of the solves that
+//   finished and the copy of x to the caller's buffer -> report the requests
+//   whose copy has completed (latency recorded).
+// The small lane's stream has the highest stream priority, so the block
+// scheduler starts its kernels ahead of waiting blocks of the large lane's:
+// a small solve iterates at its own pace instead of in lockstep with the
+// iterations of a 2-million-site solve, and the two lanes' work overlaps on
+// the GPU.  Sources and solutions move on each engine's copy stream, so with
+// pinned host buffers they overlap the iterations of other requests.
+// Requests that arrive while others iterate join their lane at the next
+// iteration boundary; their work shares the same kernel launches (and, on
+// the same gauge field, the same link loads).  Admission is FIFO per lane: a
+// request that does not fit waits until earlier ones finish.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,6 +47,8 @@ double wall() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 constexpr int kItersPerStep = 8;
+constexpr int64_t kSmallLaneMaxVh = 65536;  // 16^3x32 and smaller
+constexpr int kLanes = 2;                  // 0: small lattices, 1: the rest
 }  // namespace
 
 struct ServeTicket {
@@ -50,6 +60,16 @@ struct ServeTicket {
   jqcd_solve_info info{};
   size_t footprint = 0;
   int slot = -1;
+  int lane = 0;
+};
+
+struct ServeLane {
+  cudaStream_t stream = nullptr;
+  std::unique_ptr<BatchEngine> engine;
+  std::thread thread;
+  std::deque<uint64_t> queue;          // waiting tickets, FIFO (guarded by Server::mu)
+  std::map<int, uint64_t> slot_ticket;  // engine slot -> ticket (guarded by Server::mu)
+  size_t alloc = 0;  // device bytes of this lane's slot buffers, admissions in flight included
 };
 
 struct Server {
@@ -58,9 +78,7 @@ struct Server {
   int hp = PREC_F16N;
   size_t budget = 0;
   int max_queue = 0;
-  cudaStream_t stream = nullptr;
-  std::unique_ptr<BatchEngine> engine;
-  std::thread thread;
+  ServeLane lanes[kLanes];
   std::mutex mu;
   std::condition_variable cv;
   bool stop = false;
@@ -68,9 +86,7 @@ struct Server {
   bool failed = false;
   std::string error;
   uint64_t next_ticket = 1;
-  std::deque<uint64_t> queue;                       // waiting tickets, FIFO
   std::map<uint64_t, std::unique_ptr<ServeTicket>> tickets;
-  std::map<int, uint64_t> slot_ticket;              // engine slot -> ticket
   size_t peak_alloc = 0;                            // peak device bytes of slot buffers
   int peak_active = 0;
   int peak_queue = 0;                               // most requests waiting at once
@@ -78,18 +94,46 @@ struct Server {
   std::vector<double> latencies;
   int64_t rejected = 0;
 
-  void loop();
+  size_t total_alloc() const {  // caller holds mu
+    size_t a = 0;
+    for (const ServeLane &L : lanes) a += L.alloc;
+    return a;
+  }
+  int total_active() const {  // caller holds mu
+    int n = 0;
+    for (const ServeLane &L : lanes) n += (int)L.slot_ticket.size();
+    return n;
+  }
+  int total_queued() const {  // caller holds mu
+    int n = 0;
+    for (const ServeLane &L : lanes) n += (int)L.queue.size();
+    return n;
+  }
+  void fail(const std::string &msg) {  // caller holds mu
+    failed = true;
+    error = msg;
+    for (auto &kv : tickets)
+      if (kv.second->state != 2) {
+        kv.second->state = 2;
+        kv.second->status = JQCD_ECUDA;
+      }
+    cv.notify_all();
+  }
+  void loop(int lane);
 };
 
-void Server::loop() {
+void Server::loop(int li) {
   cudaSetDevice(device);
+  ServeLane &L = lanes[li];
+  BatchEngine *engine = L.engine.get();
   std::vector<int> finished;
   for (;;) {
     std::vector<std::pair<uint64_t, ServeTicket *>> admit;
     {
       std::unique_lock<std::mutex> lk(mu);
+      if (failed) return;  // the other lane hit an error
       const bool idle = engine->running() == 0;
-      if (idle && queue.empty()) {
+      if (idle && L.queue.empty()) {
         if (engine->draining() == 0) {
           if (stop) return;
           cv.wait_for(lk, std::chrono::milliseconds(2));
@@ -99,70 +143,69 @@ void Server::loop() {
       }
       if (stop && wall() > stop_deadline) {  // drain took too long: give up
         for (auto &kv : tickets)
-          if (kv.second->state != 2) {
+          if (kv.second->lane == li && kv.second->state != 2) {
             kv.second->state = 2;
             kv.second->status = JQCD_ETIMEOUT;
           }
         failed = true;
         error = "requests still running at the stop deadline";
+        cv.notify_all();
         return;
       }
       // FIFO admission: a free slot and a device-memory budget that covers
-      // every slot buffer allocated so far plus what this request adds
-      int64_t planned = 0;
-      std::vector<int> taken;
-      while (!queue.empty() && (int)taken.size() < engine->max_slots()) {
-        ServeTicket *T = tickets[queue.front()].get();
+      // every slot buffer of both lanes plus what this request adds
+      while (!L.queue.empty()) {
+        ServeTicket *T = tickets[L.queue.front()].get();
         if (T->footprint > budget) {  // can never fit
           T->state = 2;
           T->status = JQCD_ENOMEM;
           T->t_done = wall();
           ++rejected;
-          queue.pop_front();
+          L.queue.pop_front();
           continue;
         }
         int64_t extra = 0;
         int slot = engine->pick_slot(T->G->g.vh, &extra);
-        if (slot >= 0 && std::find(taken.begin(), taken.end(), slot) != taken.end()) break;
         if (slot < 0) break;
-        if ((int64_t)engine->allocated_bytes() + planned + extra > (int64_t)budget) {
+        if ((int64_t)total_alloc() + extra > (int64_t)budget) {
           // idle slots may be holding buffers from earlier, larger requests
           engine->release_idle(slot);
+          L.alloc = engine->allocated_bytes();
           slot = engine->pick_slot(T->G->g.vh, &extra);
-          if (slot < 0 || (int64_t)engine->allocated_bytes() + planned + extra > (int64_t)budget) break;
+          if (slot < 0 || (int64_t)total_alloc() + extra > (int64_t)budget) break;
         }
-        planned += extra;
-        taken.push_back(slot);
+        L.alloc += (size_t)extra;  // reserved until the admission has allocated it
         T->slot = slot;
-        admit.push_back({queue.front(), T});
-        queue.pop_front();
+        admit.push_back({L.queue.front(), T});
+        L.queue.pop_front();
         break;  // one admission per pass: pick_slot sees the new slot state next time
       }
     }
     cudaError_t e = cudaSuccess;
     for (auto &a : admit) {
       ServeTicket *T = a.second;
-      nvtxRangePushA("serve admit");
+      nvtxRangePushA(li == 0 ? "serve admit (small lane)" : "serve admit");
       e = engine->admit(T->slot, T->G, T->req.params, T->req.b);
       nvtxRangePop();
-      if (e) break;
       std::lock_guard<std::mutex> lk(mu);
+      L.alloc = engine->allocated_bytes();
+      if (e) break;
       T->state = 1;
       T->t_admit = wall();
-      slot_ticket[T->slot] = a.first;
-      peak_alloc = std::max(peak_alloc, engine->allocated_bytes());
-      peak_active = std::max(peak_active, (int)slot_ticket.size());
+      L.slot_ticket[T->slot] = a.first;
+      peak_alloc = std::max(peak_alloc, total_alloc());
+      peak_active = std::max(peak_active, total_active());
     }
     // keep admitting while requests fit before spending time on iterations
     if (!e && !admit.empty()) {
       std::lock_guard<std::mutex> lk(mu);
-      if (!queue.empty() && (int)slot_ticket.size() < engine->max_slots()) {
+      if (!L.queue.empty() && (int)L.slot_ticket.size() < engine->max_slots()) {
         int64_t extra = 0;
-        const int slot = engine->pick_slot(tickets[queue.front()]->G->g.vh, &extra);
-        if (slot >= 0 && (int64_t)engine->allocated_bytes() + extra <= (int64_t)budget) continue;
+        const int slot = engine->pick_slot(tickets[L.queue.front()]->G->g.vh, &extra);
+        if (slot >= 0 && (int64_t)total_alloc() + extra <= (int64_t)budget) continue;
       }
     }
-    nvtxRangePushA("serve iterate");
+    nvtxRangePushA(li == 0 ? "serve iterate (small lane)" : "serve iterate");
     if (!e && engine->running() > 0) e = engine->run(kItersPerStep);
     finished.clear();
     if (!e) e = engine->poll(&finished);
@@ -174,7 +217,7 @@ void Server::loop() {
       ServeTicket *T;
       {
         std::lock_guard<std::mutex> lk(mu);
-        T = tickets[slot_ticket[slot]].get();
+        T = tickets[L.slot_ticket[slot]].get();
       }
       e = engine->collect_async(slot, T->req.x);
     }
@@ -182,7 +225,7 @@ void Server::loop() {
     std::vector<std::pair<int, uint64_t>> drained;
     if (!e) {
       std::lock_guard<std::mutex> lk(mu);
-      for (auto &kv : slot_ticket)
+      for (auto &kv : L.slot_ticket)
         if (engine->drained(kv.first)) drained.push_back(kv);
     }
     for (auto &d : drained) {
@@ -196,19 +239,13 @@ void Server::loop() {
       T->info = inf;
       T->status = inf.status;
       T->state = 2;
-      slot_ticket.erase(d.first);
+      L.slot_ticket.erase(d.first);
       latencies.push_back(T->t_done - T->t_submit);
       t_last = T->t_done;
     }
     if (e) {
       std::lock_guard<std::mutex> lk(mu);
-      failed = true;
-      error = cudaGetErrorString(e);
-      for (auto &kv : tickets)
-        if (kv.second->state != 2) {
-          kv.second->state = 2;
-          kv.second->status = JQCD_ECUDA;
-        }
+      fail(cudaGetErrorString(e));
       return;
     }
   }
@@ -222,13 +259,25 @@ Server *serve_create(int device, int sm_count, int hp, size_t budget, int max_sl
   S->hp = hp;
   S->budget = budget;
   S->max_queue = max_queue;
-  cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
-  if (e) { *err = cudaGetErrorString(e); return nullptr; }
-  S->engine.reset(new BatchEngine(hp, max_slots, S->stream, sm_count));
-  e = S->engine->init();
-  if (e) { *err = cudaGetErrorString(e); return nullptr; }
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  for (int li = 0; li < kLanes && !e; ++li) {
+    ServeLane &L = S->lanes[li];
+    e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, li == 0 ? greatest : least);
+    if (e) break;
+    L.engine.reset(new BatchEngine(hp, max_slots, L.stream, sm_count));
+    e = L.engine->init();
+  }
+  if (e) {
+    *err = cudaGetErrorString(e);
+    for (ServeLane &L : S->lanes) {
+      L.engine.reset();
+      if (L.stream) cudaStreamDestroy(L.stream);
+    }
+    return nullptr;
+  }
   Server *raw = S.get();
-  S->thread = std::thread([raw] { raw->loop(); });
+  for (int li = 0; li < kLanes; ++li) S->lanes[li].thread = std::thread([raw, li] { raw->loop(li); });
   return S.release();
 }
 
@@ -238,17 +287,19 @@ jqcd_status serve_submit(Server *S, GaugeEntry *G, const jqcd_request &r, uint64
   T->G = G;
   T->t_submit = wall();
   T->footprint = SlotBuffers::footprint(G->g.vh, S->hp);
+  T->lane = G->g.vh <= kSmallLaneMaxVh ? 0 : 1;
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->failed) return JQCD_ECUDA;
   if (S->stop) return JQCD_EINVAL;
-  if (S->max_queue > 0 && (int)S->queue.size() >= S->max_queue) return JQCD_EBUSY;
+  if (S->max_queue > 0 && S->total_queued() >= S->max_queue) return JQCD_EBUSY;
   const uint64_t id = S->next_ticket++;
   if (S->t_first == 0.0) S->t_first = T->t_submit;
+  const int lane = T->lane;
   S->tickets[id] = std::move(T);
-  S->queue.push_back(id);
-  S->peak_queue = std::max(S->peak_queue, (int)S->queue.size());
+  S->lanes[lane].queue.push_back(id);
+  S->peak_queue = std::max(S->peak_queue, S->total_queued());
   *ticket = id;
-  S->cv.notify_one();
+  S->cv.notify_all();
   return JQCD_OK;
 }
 
@@ -276,9 +327,10 @@ jqcd_status serve_destroy(Server *S, jqcd_serve_stats *stats, std::string *err) 
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
     S->stop_deadline = wall() + 300.0;
-    S->cv.notify_one();
+    S->cv.notify_all();
   }
-  if (S->thread.joinable()) S->thread.join();
+  for (ServeLane &L : S->lanes)
+    if (L.thread.joinable()) L.thread.join();
   jqcd_status st = S->failed ? JQCD_ECUDA : JQCD_OK;
   if (S->failed) *err = S->error;
   if (stats) {
@@ -303,8 +355,10 @@ jqcd_status serve_destroy(Server *S, jqcd_serve_stats *stats, std::string *err) 
     stats->peak_active = S->peak_active;
     stats->peak_queue = S->peak_queue;
   }
-  S->engine.reset();
-  if (S->stream) cudaStreamDestroy(S->stream);
+  for (ServeLane &L : S->lanes) {
+    L.engine.reset();
+    if (L.stream) cudaStreamDestroy(L.stream);
+  }
   delete S;
   return st;
 }
