@@ -98,6 +98,8 @@ BatchArgs BatchEngine::args() const {
   A.ntiles = d_ntiles_;
   A.lp_tiles = d_lp_tiles_;
   A.n_lp_tiles = d_n_lp_tiles_;
+  A.lp2_tiles = d_lp_tiles_ ? d_lp_tiles_ + max_lp_tiles_ : nullptr;  // second half of the buffer
+  A.n_lp2_tiles = d_n_lp2_tiles_;
   A.any_update = d_any_update_;
   A.nslots = (int)slots_.size();
   return A;
@@ -106,10 +108,10 @@ BatchArgs BatchEngine::args() const {
 BatchEngine::~BatchEngine() {
   cudaStreamSynchronize(s_);
   if (cs_) cudaStreamSynchronize(cs_);
-  if (graph_) cudaGraphExecDestroy(graph_);
+  drop_graphs();
   for (void *p : {(void *)d_slots_, (void *)d_S_, (void *)d_groups_, (void *)d_tiles_,
                   (void *)d_ntiles_, (void *)d_lp_tiles_, (void *)d_n_lp_tiles_,
-                  (void *)d_any_update_})
+                  (void *)d_n_lp2_tiles_, (void *)d_any_update_})
     if (p) cudaFree(p);
   for (auto *v : {&ev_in_, &ev_out_, &ev_done_})
     for (cudaEvent_t ev : *v) cudaEventDestroy(ev);
@@ -131,6 +133,8 @@ cudaError_t BatchEngine::init() {
   if (!e) e = cudaMalloc(&d_ntiles_, sizeof(int));
   if (!e) e = cudaMalloc(&d_n_lp_tiles_, sizeof(int));
   if (!e) e = cudaMemsetAsync(d_n_lp_tiles_, 0, sizeof(int), s_);
+  if (!e) e = cudaMalloc(&d_n_lp2_tiles_, sizeof(int));
+  if (!e) e = cudaMemsetAsync(d_n_lp2_tiles_, 0, sizeof(int), s_);
   if (!e) e = cudaMalloc(&d_any_update_, sizeof(int));
   if (!e) e = cudaMemsetAsync(d_S_, 0, sizeof(SolverScalars) * n, s_);
   if (!e) e = cudaMemsetAsync(d_ntiles_, 0, sizeof(int), s_);
@@ -284,23 +288,27 @@ cudaError_t BatchEngine::rebuild() {
     GroupDev &Gd = groups[it->second];
     Gd.slot[Gd.nslots++] = (int)i;
   }
-  std::vector<int2> tiles, lp_tiles;
+  std::vector<int2> tiles, lp_tiles, lp2_tiles;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const int nbk = (int)((groups[gi].g.vh + tile_sites_ - 1) / tile_sites_);
     for (int j = 0; j < nbk; ++j) tiles.push_back(make_int2((int)gi, j));
     groups[gi].tpb = 1;
     const int nlp = (int)((groups[gi].g.vh + kLpThreads - 1) / kLpThreads);
     for (int j = 0; j < nlp; ++j)
-      for (int r = 0; r < groups[gi].nslots; ++r) lp_tiles.push_back(make_int2((int)gi * 16 + r, j));
+      for (int r = 0; r < groups[gi].nslots; ++r) {
+        lp_tiles.push_back(make_int2((int)gi * 16 + r, j));
+        if (r % 2 == 0) lp2_tiles.push_back(make_int2((int)gi * 16 + r, j));
+      }
   }
   if ((int64_t)lp_tiles.size() > max_lp_tiles_) {
     if (d_lp_tiles_) cudaFree(d_lp_tiles_);
     d_lp_tiles_ = nullptr;
     const int64_t cap = std::max<int64_t>((int64_t)lp_tiles.size() * 2, 1024);
-    cudaError_t e0 = cudaMalloc(&d_lp_tiles_, sizeof(int2) * cap);
+    // per-slot items in the first half, pair items in the second
+    cudaError_t e0 = cudaMalloc(&d_lp_tiles_, 2 * sizeof(int2) * cap);
     if (e0) { max_lp_tiles_ = 0; return e0; }
     max_lp_tiles_ = cap;
-    if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }  // pointer changed
+    drop_graphs();  // pointer changed
   }
   cudaError_t e = cudaSuccess;
   if ((int64_t)tiles.size() > max_tiles_) {
@@ -310,9 +318,11 @@ cudaError_t BatchEngine::rebuild() {
     e = cudaMalloc(&d_tiles_, sizeof(int2) * cap);
     if (e) { max_tiles_ = 0; return e; }
     max_tiles_ = cap;
-    if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }  // pointer changed
+    drop_graphs();  // pointer changed
   }
   const int ntiles = (int)tiles.size();
+  n_tiles_ = ntiles;
+  n_lp_items_ = (int64_t)lp_tiles.size();
   e = cudaMemcpyAsync(d_slots_, h_slots_.data(), sizeof(SlotDev) * h_slots_.size(),
                       cudaMemcpyHostToDevice, s_);
   if (!e && !groups.empty())
@@ -326,34 +336,63 @@ cudaError_t BatchEngine::rebuild() {
     e = cudaMemcpyAsync(d_lp_tiles_, lp_tiles.data(), sizeof(int2) * lp_tiles.size(),
                         cudaMemcpyHostToDevice, s_);
   if (!e) e = cudaMemcpyAsync(d_n_lp_tiles_, &n_lp, sizeof(int), cudaMemcpyHostToDevice, s_);
+  const int n_lp2 = (int)lp2_tiles.size();
+  if (!e && n_lp2)
+    e = cudaMemcpyAsync(d_lp_tiles_ + max_lp_tiles_, lp2_tiles.data(), sizeof(int2) * lp2_tiles.size(),
+                        cudaMemcpyHostToDevice, s_);
+  if (!e) e = cudaMemcpyAsync(d_n_lp2_tiles_, &n_lp2, sizeof(int), cudaMemcpyHostToDevice, s_);
   // pageable sources: make the copies complete before the vectors go away
   if (!e) e = cudaStreamSynchronize(s_);
   if (!e) dirty_ = false;
   return e;
 }
 
+// Persistent grids no larger than the work: the tile and low-precision
+// grids are capped at the next power of two of their item counts (a few
+// solves on an 8^4 lattice have tens of items, not 2-4 x SMs), so each launch
+// asks the block scheduler for no more blocks than it can use.  One captured
+// graph is kept per (tile size, grid, low-precision grid).
+static int pow2_at_least(int64_t n) {
+  int p = 1;
+  while (p < n && p < (1 << 30)) p <<= 1;
+  return p;
+}
+
+void BatchEngine::drop_graphs() {
+  for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second.first);
+  graphs_.clear();
+  graph_ = nullptr;
+}
+
 cudaError_t BatchEngine::ensure_graph() {
-  if (graph_ && graph_ts_ == tile_sites_ && graph_grid_ == grid_ && graph_lp_grid_ == lp_grid_)
+  const int grid = std::min<int>(grid_, pow2_at_least(std::max<int64_t>(n_tiles_, 1)));
+  const int lp_grid = std::min<int>(lp_grid_, pow2_at_least(std::max<int64_t>(n_lp_items_, 1)));
+  const std::tuple<int, int, int> key{tile_sites_, grid, lp_grid};
+  auto it = graphs_.find(key);
+  if (it != graphs_.end()) {
+    graph_ = it->second.first;
+    graph_kernels_ = it->second.second;
     return cudaSuccess;
-  if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }
+  }
   const BatchArgs A = args();
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s_, cudaStreamCaptureModeThreadLocal);
   if (e) return e;
   const uint64_t before = jqcd_kernel_launches();
   for (int k = 0; k < kGraphIters && !e; ++k)
-    e = launch_batch_iteration(A, hp_, tile_sites_, grid_, lp_grid_, s_);
-  graph_kernels_ = (int64_t)(jqcd_kernel_launches() - before);
-  note_launch(-graph_kernels_);  // recorded, not run: counted at each replay instead
+    e = launch_batch_iteration(A, hp_, tile_sites_, grid, lp_grid, s_);
+  const int64_t kernels = (int64_t)(jqcd_kernel_launches() - before);
+  note_launch(-kernels);  // recorded, not run: counted at each replay instead
   cudaError_t e2 = cudaStreamEndCapture(s_, &g);
   if (e) { if (g) cudaGraphDestroy(g); return e; }
   if (e2) return e2;
-  e = cudaGraphInstantiate(&graph_, g, 0);
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
-  if (e) { graph_ = nullptr; return e; }
-  graph_ts_ = tile_sites_;
-  graph_grid_ = grid_;
-  graph_lp_grid_ = lp_grid_;
+  if (e) return e;
+  graphs_[key] = {exec, kernels};
+  graph_ = exec;
+  graph_kernels_ = kernels;
   return cudaSuccess;
 }
 

@@ -56,6 +56,8 @@ struct BatchArgs {
   const int *ntiles;
   int2 *lp_tiles;        // (16 * group + slot in group, block of kLpThreads sites)
   const int *n_lp_tiles;
+  int2 *lp2_tiles;       // the same with the first slot of each pair of a group (slots
+  const int *n_lp2_tiles;  // 0, 2, 4, ...): items of the packed low-precision stages
   int *any_update;       // nonzero when some slot requested a reliable update
   int nslots;            // descriptors allocated (grid of per-slot kernels)
 };
@@ -65,6 +67,13 @@ cudaError_t batch_configure();
 
 // Low-precision hop blocks: one thread per site, kLpThreads sites per item.
 constexpr int kLpThreads = 128;
+
+// Low-precision hop items carry two right-hand sides of a group (packed
+// two-lane arithmetic, hop_lp2.cuh) when set, one otherwise.
+#ifndef JQCD_BATCH_LP_PAIRS
+#define JQCD_BATCH_LP_PAIRS 1
+#endif
+constexpr bool kBatchLpPairs = JQCD_BATCH_LP_PAIRS != 0;
 
 // One CG iteration of every active slot (inner hop precision hp): the
 // low-precision hops on a persistent grid of lp_grid blocks of kLpThreads

@@ -4,6 +4,7 @@
 
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "batch.h"
@@ -111,6 +112,7 @@ class BatchEngine {
   int *d_ntiles_ = nullptr;
   int2 *d_lp_tiles_ = nullptr;
   int *d_n_lp_tiles_ = nullptr;
+  int *d_n_lp2_tiles_ = nullptr;  // pair items live in d_lp_tiles_ + max_lp_tiles_
   int64_t max_lp_tiles_ = 0;
   int lp_grid_ = 0;
   int *d_any_update_ = nullptr;
@@ -123,9 +125,11 @@ class BatchEngine {
   int tile_sites_ = 128;
   int grid_ = 0;
   bool dirty_ = true;
-  cudaGraphExec_t graph_ = nullptr;
-  int graph_ts_ = 0, graph_grid_ = 0, graph_lp_grid_ = 0;
+  cudaGraphExec_t graph_ = nullptr;  // the graph of the current grids (owned by graphs_)
   int64_t graph_kernels_ = 0;
+  std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs_;
+  int64_t n_tiles_ = 0, n_lp_items_ = 0;  // work items of the current active set
+  void drop_graphs();
   std::map<std::string, std::pair<int, int>> tuned_;
   double t0_ = 0.0;
 };

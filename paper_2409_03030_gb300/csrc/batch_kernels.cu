@@ -12,6 +12,7 @@
 #include "hop_dw.cuh"
 #include "hop_dwp.cuh"
 #include "hop_lp.cuh"
+#include "hop_lp2.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -30,31 +31,18 @@ __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
 // STAGE 0: t = H_oe p;  1: w = p - kappa^2 H_eo t, ||w||^2;  2: t = H^dag_oe w;
 // STAGE 3: Ap = w - kappa^2 H^dag_eo t, then (UPDATE) x_s += alpha p,
 //          r_s -= alpha Ap, ||r_s||^2 without storing Ap.
+// The per-site epilogue of a low-precision stage for one slot: acc is
+// (H in)(idx); AXPY stages add the slot's own operand, stage 3 with UPDATE
+// applies x_s += alpha p, r_s -= alpha Ap; returns this site's part of the
+// stage's norm (NORM stages).
 template <int PREC, int STAGE, bool UPDATE>
-__global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
-  extern __shared__ float4 lsm[];
-  constexpr bool DAG = STAGE >= 2;
-  constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
+__device__ __forceinline__ float lp_stage_epilogue(const cf (&acc)[4][3], const SlotDev &Sl,
+                                                   const SolverScalars &Ss, int64_t vh, int64_t idx) {
   constexpr bool AXPY = STAGE == 1 || STAGE == 3;
   constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
-  const int n = *A.n_lp_tiles;
-  for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    const int2 W = A.lp_tiles[it];
-    const GroupDev *G = A.groups + (W.x >> 4);
-    const int si = G->slot[W.x & 15];
-    if (!slot_running(A, si)) continue;  // uniform over the block
-    const SlotDev &Sl = A.slots[si];
-    const Geom g = G->g;
-    const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
-    const bool on = idx < g.vh;
-    float n2 = 0.f;
-    if (on) {
-      const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
-      const void *xv = STAGE == 1 ? Sl.p : Sl.w;
-      void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
-      cf acc[4][3];
-      lp_hop_site<PREC, DAG, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc);
-      const int64_t vh = g.vh;
+  float n2 = 0.f;
+  const void *xv = STAGE == 1 ? Sl.p : Sl.w;
+  void *out = STAGE == 0 || STAGE == 2 ? Sl.t : (STAGE == 1 ? Sl.w : Sl.Ap);
       cf o[4][3];
       if (AXPY) {
         cf xs[4][3];
@@ -70,7 +58,7 @@ __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArg
           for (int c = 0; c < 3; ++c) o[a][c] = acc[a][c];
       }
       if (STAGE == 3 && UPDATE) {
-        const float al = A.S[si].alpha_f;
+        const float al = Ss.alpha_f;
         cf pv[4][3], xv4[4][3], rv[4][3];
         PT<PREC>::load_spinor(Sl.p, vh, idx, pv);
         PT<PREC_F32>::load_spinor(Sl.xs, vh, idx, xv4);
@@ -95,10 +83,96 @@ __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArg
             n2 = fmaf(o[k / 3][k % 3].re, o[k / 3][k % 3].re, fmaf(o[k / 3][k % 3].im, o[k / 3][k % 3].im, n2));
         }
       }
+  return n2;
+}
+
+template <int PREC, int STAGE, bool UPDATE>
+__global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
+  extern __shared__ float4 lsm[];
+  constexpr bool DAG = STAGE >= 2;
+  constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
+  constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
+  const int n = *A.n_lp_tiles;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 W = A.lp_tiles[it];
+    const GroupDev *G = A.groups + (W.x >> 4);
+    const int si = G->slot[W.x & 15];
+    if (!slot_running(A, si)) continue;  // uniform over the block
+    const SlotDev &Sl = A.slots[si];
+    const Geom g = G->g;
+    const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
+    float n2 = 0.f;
+    if (idx < g.vh) {
+      const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
+      cf acc[4][3];
+      lp_hop_site<PREC, DAG, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc);
+      n2 = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, Sl, A.S[si], g.vh, idx);
     }
     if (NORM) {
       const double sum = block_sum_f(n2);
       if (threadIdx.x == 0) Sl.part[W.y] = sum;
+    }
+  }
+}
+
+// The same stages for two right-hand sides of a group per work item, in
+// packed two-lane arithmetic (hop_lp2.cuh): items are (group, first slot of
+// a pair, block of kLpThreads sites) from the pair list lp2_tiles.  An item
+// with a single running slot (an odd group, or a pair one of whose solves
+// has stopped) takes the one-lane site loop of hop_lp.cuh.
+// Resident blocks per SM the packed kernels' register budget is cut for.
+// Measured (ncu launch lists of the 24-solve batch, serialised): FP16 inner
+// operator 236 ms with one right-hand side per thread (5 blocks/SM), 267 ms
+// packed at 3 blocks/SM (155-168 registers), 222 ms packed at 4 blocks/SM
+// (128 registers, 8-160 B spilled); FP32 297, 300 and 277 ms.
+#ifndef JQCD_BATCH_LP2_MIN_BLOCKS
+#define JQCD_BATCH_LP2_MIN_BLOCKS 4
+#endif
+template <int PREC, int STAGE, bool UPDATE>
+__global__ void __launch_bounds__(kLpThreads, JQCD_BATCH_LP2_MIN_BLOCKS) batch_lp2_hop_kernel(const BatchArgs A) {
+  extern __shared__ float4 lsm[];
+  constexpr bool DAG = STAGE >= 2;
+  constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
+  constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
+  const int n = *A.n_lp2_tiles;
+  for (int it = blockIdx.x; it < n; it += gridDim.x) {
+    const int2 W = A.lp2_tiles[it];
+    const GroupDev *G = A.groups + (W.x >> 4);
+    const int r0 = W.x & 15;
+    const int s0 = G->slot[r0];
+    const int s1 = r0 + 1 < G->nslots ? G->slot[r0 + 1] : -1;
+    const bool run0 = slot_running(A, s0), run1 = s1 >= 0 && slot_running(A, s1);
+    if (!run0 && !run1) continue;  // uniform over the block
+    const int sa = run0 ? s0 : s1;
+    const int sb = run0 && run1 ? s1 : sa;
+    const bool two = run0 && run1;
+    const SlotDev &S0 = A.slots[sa], &S1 = A.slots[sb];
+    const Geom g = G->g;
+    const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
+    float n2a = 0.f, n2b = 0.f;
+    if (idx < g.vh) {
+      const void *in0 = STAGE == 0 ? S0.p : (STAGE == 2 ? S0.w : S0.t);
+      cf acc[4][3];
+      if (two) {
+        const void *in1 = STAGE == 0 ? S1.p : (STAGE == 2 ? S1.w : S1.t);
+        cp2 acc2[4][3];
+        lp2_hop_site<PREC, DAG>(lsm, in0, in1, G->gauge_f32, g, OUTP, idx, acc2);
+        lp2_lane(acc2, 0, acc);
+        n2a = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, S0, A.S[sa], g.vh, idx);
+        lp2_lane(acc2, 1, acc);
+        n2b = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, S1, A.S[sb], g.vh, idx);
+      } else {  // a single running slot: the one-lane site loop
+        lp_hop_site<PREC, DAG, true>(lsm, in0, G->gauge_f32, g, OUTP, idx, acc);
+        n2a = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, S0, A.S[sa], g.vh, idx);
+      }
+    }
+    if (NORM) {
+      const double sum0 = block_sum_f(n2a);
+      if (threadIdx.x == 0) S0.part[W.y] = sum0;
+      if (two) {
+        const double sum1 = block_sum_f(n2b);
+        if (threadIdx.x == 0) S1.part[W.y] = sum1;
+      }
     }
   }
 }
@@ -338,6 +412,21 @@ __global__ void batch_resume_kernel(const BatchArgs A) {
 }
 
 // ---- launchers -------------------------------------------------------------------
+template <int PREC>
+static cudaError_t configure_lp2() {
+  const void *k[5] = {(const void *)batch_lp2_hop_kernel<PREC, 0, false>,
+                      (const void *)batch_lp2_hop_kernel<PREC, 1, false>,
+                      (const void *)batch_lp2_hop_kernel<PREC, 2, false>,
+                      (const void *)batch_lp2_hop_kernel<PREC, 3, false>,
+                      (const void *)batch_lp2_hop_kernel<PREC, 3, true>};
+  for (const void *f : k) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lp2_stage_smem<PREC>());
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t batch_configure() {
   const void *k[4] = {(const void *)batch_dw_hop_kernel<0>, (const void *)batch_dw_hop_kernel<1>,
                       (const void *)batch_dw_hop_kernel<2>, (const void *)batch_dw_hop_kernel<3>};
@@ -345,13 +434,18 @@ cudaError_t batch_configure() {
     const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  cudaError_t e = configure_lp2<PREC_F32>();
+  if (e == cudaSuccess) e = configure_lp2<PREC_F16N>();
+  return e;
 }
 
 template <int PREC, int STAGE, bool UPDATE>
 static void lp_stage(const BatchArgs &A, int lp_grid, cudaStream_t s) {
   note_launch();
-  batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
+  if (kBatchLpPairs)
+    batch_lp2_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp2_stage_smem<PREC>(), s>>>(A);
+  else
+    batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
 }
 
 template <int PREC>
