@@ -270,20 +270,20 @@ JQCD_API jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_
                                          double *const *x, jqcd_solve_info *infos);
 
 /* ---- serving: continuous batching of solves -------------------------------
- * Requests go to one of two lanes by lattice size: at most 65,536 sites per
- * parity (16^3x32 and smaller) to the small lane, the rest to the large lane.
- * Each lane has a scheduler thread owned by the context that admits its
- * queued requests as engine slots and device memory free up, advances every
- * admitted solve of the lane together (the batched engine of
- * jqcd_cg_solve_batch), and completes each request as soon as it converges.
- * The small lane runs on a stream of the highest priority, so its solves
- * iterate at their own pace instead of in lockstep with large ones; the two
- * lanes' work overlaps on the GPU.  Requests that arrive while others run
- * join their lane at the next iteration boundary.  Admission is first come,
- * first served within a lane, by HBM footprint: a request is admitted when a
- * slot of its lane is free and the device memory held by the slot buffers of
- * both lanes, plus what this request adds, stays within hbm_budget_bytes
- * (resident gauge fields are not counted).
+ * Requests go to one of three lanes by lattice size: at most 65,536 sites
+ * per parity (16^3x32 and smaller), at most 524,288 (up to 32^3x32, e.g.
+ * 24^3x48), and larger.  Each lane has a scheduler thread owned by the
+ * context that admits its queued requests as engine slots and device memory
+ * free up, advances every admitted solve of the lane together (the batched
+ * engine of jqcd_cg_solve_batch), and completes each request as soon as it
+ * converges.  The smaller a lane's lattices, the higher its stream priority,
+ * so its solves iterate at their own pace instead of in lockstep with larger
+ * ones; the lanes' work overlaps on the GPU.  Requests that arrive while
+ * others run join their lane at the next iteration boundary.  Admission is
+ * first come, first served within a lane, by HBM footprint: a request is
+ * admitted when a slot of its lane is free and the device memory held by the
+ * slot buffers of all lanes, plus what this request adds, stays within
+ * hbm_budget_bytes (resident gauge fields are not counted).
  * Sources and solutions move on a copy stream of their own, so with pinned
  * (page-locked) host buffers they overlap the iterations of other requests;
  * pageable buffers work too, copied in order on the compute stream.
@@ -304,12 +304,12 @@ typedef struct {
   double solves_per_s;    /* completed / (last completion - first submit) */
   double wall_s;
   double peak_hbm_bytes;  /* peak device bytes held by solve slots */
-  int32_t peak_active;    /* largest number of solves iterating together (both lanes) */
+  int32_t peak_active;    /* largest number of solves iterating together (all lanes) */
   int32_t peak_queue;     /* largest number of requests waiting for admission */
 } jqcd_serve_stats;
 
 /* Start the scheduler threads.  max_slots: solves iterating together in each
- * lane (>= 1); max_queue: waiting requests of both lanes before submit
+ * lane (>= 1); max_queue: waiting requests of all lanes before submit
  * returns JQCD_EBUSY (0 = unbounded);
  * mode: JQCD_CG_MIXED_F16 or JQCD_CG_MIXED_F32.  One server per context. */
 JQCD_API jqcd_status jqcd_serve_start(jqcd_ctx *ctx, size_t hbm_budget_bytes, int32_t max_slots,

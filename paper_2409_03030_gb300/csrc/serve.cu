@@ -1,21 +1,19 @@
 // Solve server: continuous batching of CG solves on one GPU.
 //
 // jqcd_serve_submit queues a request (thread-safe, never blocks on the GPU).
-// Requests go to one of two lanes by lattice size: solves of at most
-// kSmallLaneMaxVh sites per parity to the small lane, the others to the
-// large lane.  Each lane has its own BatchEngine, stream and scheduler
-// thread, and loops:
+// Requests go to one of three lanes by lattice size: at most 65,536 sites
+// per parity (small), at most 524,288 (medium), larger (large).  Each lane
+// has its own BatchEngine, stream and scheduler thread, and loops:
 //   admit queued requests while a slot is free and the device memory of all
-//   slot buffers of both lanes, plus what this request adds, fits the byte
+//   slot buffers of all lanes, plus what this request adds, fits the byte
 //   budget -> advance every admitted solve of the lane together by a few
 //   batched iterations -> queue the reconstruction of the solves that
 //   finished and the copy of x to the caller's buffer -> report the requests
 //   whose copy has completed (latency recorded).
-// The small lane's stream has the highest stream priority, so the block
-// scheduler starts its kernels ahead of waiting blocks of the large lane's:
-// a small solve iterates at its own pace instead of in lockstep with the
-// iterations of a 2-million-site solve, and the two lanes' work overlaps on
-// the GPU.  Sources and solutions move on each engine's copy stream, so with
+// The smaller a lane's lattices, the higher its stream priority, so the
+// block scheduler starts its kernels ahead of waiting blocks of the larger
+// lanes': a solve iterates at its own pace instead of in lockstep with the
+// iterations of much larger ones, and the lanes' work overlaps on the GPU.  Sources and solutions move on each engine's copy stream, so with
 // pinned host buffers they overlap the iterations of other requests.
 // Requests that arrive while others iterate join their lane at the next
 // iteration boundary; their work shares the same kernel launches (and, on
@@ -47,8 +45,19 @@ double wall() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 constexpr int kItersPerStep = 8;
-constexpr int64_t kSmallLaneMaxVh = 65536;  // 16^3x32 and smaller
-constexpr int kLanes = 2;                  // 0: small lattices, 1: the rest
+#ifndef JQCD_SERVE_LANES
+#define JQCD_SERVE_LANES 3
+#endif
+constexpr int kLanes = JQCD_SERVE_LANES;
+// largest sites per parity of each lane but the last: 16^3x32, then 32^3x32
+constexpr int64_t kLaneMaxVhAll[2] = {65536, 524288};
+constexpr const int64_t *kLaneMaxVh = kLaneMaxVhAll;
+
+int lane_of(int64_t vh) {
+  int l = 0;
+  while (l < kLanes - 1 && vh > kLaneMaxVh[l]) ++l;
+  return l;
+}
 }  // namespace
 
 struct ServeTicket {
@@ -153,7 +162,7 @@ void Server::loop(int li) {
         return;
       }
       // FIFO admission: a free slot and a device-memory budget that covers
-      // every slot buffer of both lanes plus what this request adds
+      // every slot buffer of all lanes plus what this request adds
       while (!L.queue.empty()) {
         ServeTicket *T = tickets[L.queue.front()].get();
         if (T->footprint > budget) {  // can never fit
@@ -184,7 +193,7 @@ void Server::loop(int li) {
     cudaError_t e = cudaSuccess;
     for (auto &a : admit) {
       ServeTicket *T = a.second;
-      nvtxRangePushA(li == 0 ? "serve admit (small lane)" : "serve admit");
+      nvtxRangePushA(li == 0 ? "serve admit (small lane)" : li == 1 ? "serve admit (medium lane)" : "serve admit");
       e = engine->admit(T->slot, T->G, T->req.params, T->req.b);
       nvtxRangePop();
       std::lock_guard<std::mutex> lk(mu);
@@ -205,7 +214,7 @@ void Server::loop(int li) {
         if (slot >= 0 && (int64_t)total_alloc() + extra <= (int64_t)budget) continue;
       }
     }
-    nvtxRangePushA(li == 0 ? "serve iterate (small lane)" : "serve iterate");
+    nvtxRangePushA(li == 0 ? "serve iterate (small lane)" : li == 1 ? "serve iterate (medium lane)" : "serve iterate");
     if (!e && engine->running() > 0) e = engine->run(kItersPerStep);
     finished.clear();
     if (!e) e = engine->poll(&finished);
@@ -263,7 +272,9 @@ Server *serve_create(int device, int sm_count, int hp, size_t budget, int max_sl
   cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
   for (int li = 0; li < kLanes && !e; ++li) {
     ServeLane &L = S->lanes[li];
-    e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, li == 0 ? greatest : least);
+    // lane 0 the greatest priority, the last lane the least (numerically, greater is lower)
+    const int prio = greatest + (least - greatest) * li / (kLanes - 1);
+    e = cudaStreamCreateWithPriority(&L.stream, cudaStreamNonBlocking, prio);
     if (e) break;
     L.engine.reset(new BatchEngine(hp, max_slots, L.stream, sm_count));
     e = L.engine->init();
@@ -287,7 +298,7 @@ jqcd_status serve_submit(Server *S, GaugeEntry *G, const jqcd_request &r, uint64
   T->G = G;
   T->t_submit = wall();
   T->footprint = SlotBuffers::footprint(G->g.vh, S->hp);
-  T->lane = G->g.vh <= kSmallLaneMaxVh ? 0 : 1;
+  T->lane = lane_of(G->g.vh);
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->failed) return JQCD_ECUDA;
   if (S->stop) return JQCD_EINVAL;
