@@ -98,8 +98,10 @@ BatchArgs BatchEngine::args() const {
   A.ntiles = d_ntiles_;
   A.lp_tiles = d_lp_tiles_;
   A.n_lp_tiles = d_n_lp_tiles_;
-  A.lp2_tiles = d_lp_tiles_ ? d_lp_tiles_ + max_lp_tiles_ : nullptr;  // second half of the buffer
+  A.lp2_tiles = d_lp_tiles_ ? d_lp_tiles_ + max_lp_tiles_ : nullptr;      // second third of the buffer
   A.n_lp2_tiles = d_n_lp2_tiles_;
+  A.lp1_tiles = d_lp_tiles_ ? d_lp_tiles_ + 2 * max_lp_tiles_ : nullptr;  // last third
+  A.n_lp1_tiles = d_n_lp1_tiles_;
   A.any_update = d_any_update_;
   A.nslots = (int)slots_.size();
   return A;
@@ -111,7 +113,7 @@ BatchEngine::~BatchEngine() {
   drop_graphs();
   for (void *p : {(void *)d_slots_, (void *)d_S_, (void *)d_groups_, (void *)d_tiles_,
                   (void *)d_ntiles_, (void *)d_lp_tiles_, (void *)d_n_lp_tiles_,
-                  (void *)d_n_lp2_tiles_, (void *)d_any_update_})
+                  (void *)d_n_lp2_tiles_, (void *)d_n_lp1_tiles_, (void *)d_any_update_})
     if (p) cudaFree(p);
   for (auto *v : {&ev_in_, &ev_out_, &ev_done_})
     for (cudaEvent_t ev : *v) cudaEventDestroy(ev);
@@ -126,6 +128,9 @@ double BatchEngine::now() const {
 cudaError_t BatchEngine::init() {
   const int n = (int)slots_.size();
   cudaError_t e = batch_configure();
+  // persistent low-precision grid: one full wave of resident blocks (the
+  // autotuner of jqcd_cg_solve_batch may choose another; the server keeps it)
+  if (!e) lp_grid_ = sm_count_ * batch_lp_blocks_per_sm(hp_);
   if (!e) e = cudaMalloc(&d_slots_, sizeof(SlotDev) * n);
   if (!e) e = cudaMalloc(&d_S_, sizeof(SolverScalars) * n);
   if (!e) e = cudaMallocHost(&h_S_, sizeof(SolverScalars) * n);
@@ -135,6 +140,8 @@ cudaError_t BatchEngine::init() {
   if (!e) e = cudaMemsetAsync(d_n_lp_tiles_, 0, sizeof(int), s_);
   if (!e) e = cudaMalloc(&d_n_lp2_tiles_, sizeof(int));
   if (!e) e = cudaMemsetAsync(d_n_lp2_tiles_, 0, sizeof(int), s_);
+  if (!e) e = cudaMalloc(&d_n_lp1_tiles_, sizeof(int));
+  if (!e) e = cudaMemsetAsync(d_n_lp1_tiles_, 0, sizeof(int), s_);
   if (!e) e = cudaMalloc(&d_any_update_, sizeof(int));
   if (!e) e = cudaMemsetAsync(d_S_, 0, sizeof(SolverScalars) * n, s_);
   if (!e) e = cudaMemsetAsync(d_ntiles_, 0, sizeof(int), s_);
@@ -288,24 +295,26 @@ cudaError_t BatchEngine::rebuild() {
     GroupDev &Gd = groups[it->second];
     Gd.slot[Gd.nslots++] = (int)i;
   }
-  std::vector<int2> tiles, lp_tiles, lp2_tiles;
+  std::vector<int2> tiles, lp_tiles, lp2_tiles, lp1_tiles;
   for (size_t gi = 0; gi < groups.size(); ++gi) {
     const int nbk = (int)((groups[gi].g.vh + tile_sites_ - 1) / tile_sites_);
     for (int j = 0; j < nbk; ++j) tiles.push_back(make_int2((int)gi, j));
     groups[gi].tpb = 1;
     const int nlp = (int)((groups[gi].g.vh + kLpThreads - 1) / kLpThreads);
+    const int ns = groups[gi].nslots;
     for (int j = 0; j < nlp; ++j)
-      for (int r = 0; r < groups[gi].nslots; ++r) {
+      for (int r = 0; r < ns; ++r) {
         lp_tiles.push_back(make_int2((int)gi * 16 + r, j));
-        if (r % 2 == 0) lp2_tiles.push_back(make_int2((int)gi * 16 + r, j));
+        if (r % 2 == 0 && r + 1 < ns) lp2_tiles.push_back(make_int2((int)gi * 16 + r, j));
+        if (r % 2 == 0 && r + 1 == ns) lp1_tiles.push_back(make_int2((int)gi * 16 + r, j));
       }
   }
   if ((int64_t)lp_tiles.size() > max_lp_tiles_) {
     if (d_lp_tiles_) cudaFree(d_lp_tiles_);
     d_lp_tiles_ = nullptr;
     const int64_t cap = std::max<int64_t>((int64_t)lp_tiles.size() * 2, 1024);
-    // per-slot items in the first half, pair items in the second
-    cudaError_t e0 = cudaMalloc(&d_lp_tiles_, 2 * sizeof(int2) * cap);
+    // per-slot items in the first third, pair items in the second, single items in the last
+    cudaError_t e0 = cudaMalloc(&d_lp_tiles_, 3 * sizeof(int2) * cap);
     if (e0) { max_lp_tiles_ = 0; return e0; }
     max_lp_tiles_ = cap;
     drop_graphs();  // pointer changed
@@ -341,6 +350,13 @@ cudaError_t BatchEngine::rebuild() {
     e = cudaMemcpyAsync(d_lp_tiles_ + max_lp_tiles_, lp2_tiles.data(), sizeof(int2) * lp2_tiles.size(),
                         cudaMemcpyHostToDevice, s_);
   if (!e) e = cudaMemcpyAsync(d_n_lp2_tiles_, &n_lp2, sizeof(int), cudaMemcpyHostToDevice, s_);
+  const int n_lp1 = (int)lp1_tiles.size();
+  if (!e && n_lp1)
+    e = cudaMemcpyAsync(d_lp_tiles_ + 2 * max_lp_tiles_, lp1_tiles.data(), sizeof(int2) * lp1_tiles.size(),
+                        cudaMemcpyHostToDevice, s_);
+  if (!e) e = cudaMemcpyAsync(d_n_lp1_tiles_, &n_lp1, sizeof(int), cudaMemcpyHostToDevice, s_);
+  n_lp2_items_ = n_lp2;
+  n_lp1_items_ = n_lp1;
   // pageable sources: make the copies complete before the vectors go away
   if (!e) e = cudaStreamSynchronize(s_);
   if (!e) dirty_ = false;
@@ -364,10 +380,15 @@ void BatchEngine::drop_graphs() {
   graph_ = nullptr;
 }
 
+LpGrids BatchEngine::lp_grids(int lp_grid) const {
+  auto cap = [lp_grid](int64_t n) { return std::min<int>(lp_grid, pow2_at_least(std::max<int64_t>(n, 1))); };
+  return LpGrids{cap(n_lp_items_), cap(n_lp2_items_), cap(n_lp1_items_)};
+}
+
 cudaError_t BatchEngine::ensure_graph() {
   const int grid = std::min<int>(grid_, pow2_at_least(std::max<int64_t>(n_tiles_, 1)));
-  const int lp_grid = std::min<int>(lp_grid_, pow2_at_least(std::max<int64_t>(n_lp_items_, 1)));
-  const std::tuple<int, int, int> key{tile_sites_, grid, lp_grid};
+  const LpGrids lp = lp_grids(lp_grid_);
+  const std::tuple<int, int, int, int, int> key{tile_sites_, grid, lp.all, lp.pairs, lp.singles};
   auto it = graphs_.find(key);
   if (it != graphs_.end()) {
     graph_ = it->second.first;
@@ -380,7 +401,7 @@ cudaError_t BatchEngine::ensure_graph() {
   if (e) return e;
   const uint64_t before = jqcd_kernel_launches();
   for (int k = 0; k < kGraphIters && !e; ++k)
-    e = launch_batch_iteration(A, hp_, tile_sites_, grid, lp_grid, s_);
+    e = launch_batch_iteration(A, hp_, tile_sites_, grid, lp, s_);
   const int64_t kernels = (int64_t)(jqcd_kernel_launches() - before);
   note_launch(-kernels);  // recorded, not run: counted at each replay instead
   cudaError_t e2 = cudaStreamEndCapture(s_, &g);
@@ -545,9 +566,10 @@ cudaError_t BatchEngine::autotune() {
   const BatchArgs A = args();
   for (int m : m_cand) {
     const int grid = sm_count_ * m;
-    if ((e = launch_batch_lp_apply(A, hp_, grid, s_))) break;  // warm-up
+    const LpGrids lp = lp_grids(grid);
+    if ((e = launch_batch_lp_apply(A, hp_, lp, s_))) break;  // warm-up
     if ((e = cudaEventRecord(a, s_))) break;
-    for (int r = 0; r < 3 && !e; ++r) e = launch_batch_lp_apply(A, hp_, grid, s_);
+    for (int r = 0; r < 3 && !e; ++r) e = launch_batch_lp_apply(A, hp_, lp, s_);
     if (!e) e = cudaEventRecord(b, s_);
     if (!e) e = cudaEventSynchronize(b);
     float ms = 0.f;

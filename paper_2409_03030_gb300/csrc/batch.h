@@ -58,12 +58,19 @@ struct BatchArgs {
   const int *n_lp_tiles;
   int2 *lp2_tiles;       // the same with the first slot of each pair of a group (slots
   const int *n_lp2_tiles;  // 0, 2, 4, ...): items of the packed low-precision stages
+  int2 *lp1_tiles;       // the last slot of each group with an odd count: items of the
+  const int *n_lp1_tiles;  // one-lane low-precision stages beside the packed ones
   int *any_update;       // nonzero when some slot requested a reliable update
   int nslots;            // descriptors allocated (grid of per-slot kernels)
 };
 
 // Shared-memory limits of the batch kernels; call once before launching.
 cudaError_t batch_configure();
+
+// Blocks of the low-precision operator kernel in hop precision hp that one SM
+// holds at once (after batch_configure): a persistent grid of this many per
+// SM fills the GPU in one wave.
+int batch_lp_blocks_per_sm(int hp);
 
 // Low-precision hop blocks: one thread per site, kLpThreads sites per item.
 constexpr int kLpThreads = 128;
@@ -75,13 +82,20 @@ constexpr int kLpThreads = 128;
 #endif
 constexpr bool kBatchLpPairs = JQCD_BATCH_LP_PAIRS != 0;
 
+// Persistent grids (blocks of kLpThreads threads) of the kernels that walk
+// the per-slot items (all: the double-word reliable-update stages, and the
+// low-precision stages without pairing), the pair items and the single items.
+struct LpGrids {
+  int all, pairs, singles;
+};
+
 // One CG iteration of every active slot (inner hop precision hp): the
-// low-precision hops on a persistent grid of lp_grid blocks of kLpThreads
-// threads, the other tile kernels on `grid` blocks of `tile_sites` threads.
+// low-precision hops on the persistent grids lp, the other tile kernels on
+// `grid` blocks of `tile_sites` threads.
 cudaError_t launch_batch_iteration(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                   int lp_grid, cudaStream_t s);
+                                   const LpGrids &lp, cudaStream_t s);
 // Only the four low-precision hops of one iteration (for the autotuner; the
 // last stage also updates x_s and r_s, so run it on a copy of the state).
-cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int lp_grid, cudaStream_t s);
+cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, const LpGrids &lp, cudaStream_t s);
 
 }  // namespace jqcd

@@ -113,6 +113,7 @@ class BatchEngine {
   int2 *d_lp_tiles_ = nullptr;
   int *d_n_lp_tiles_ = nullptr;
   int *d_n_lp2_tiles_ = nullptr;  // pair items live in d_lp_tiles_ + max_lp_tiles_
+  int *d_n_lp1_tiles_ = nullptr;  // single items in d_lp_tiles_ + 2 * max_lp_tiles_
   int64_t max_lp_tiles_ = 0;
   int lp_grid_ = 0;
   int *d_any_update_ = nullptr;
@@ -127,9 +128,12 @@ class BatchEngine {
   bool dirty_ = true;
   cudaGraphExec_t graph_ = nullptr;  // the graph of the current grids (owned by graphs_)
   int64_t graph_kernels_ = 0;
-  std::map<std::tuple<int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs_;
-  int64_t n_tiles_ = 0, n_lp_items_ = 0;  // work items of the current active set
+  std::map<std::tuple<int, int, int, int, int>, std::pair<cudaGraphExec_t, int64_t>> graphs_;
+  int64_t n_tiles_ = 0, n_lp_items_ = 0, n_lp2_items_ = 0, n_lp1_items_ = 0;  // current work items
   void drop_graphs();
+  // grids of the low-precision kernels for a persistent grid of lp_grid
+  // blocks, each capped at the next power of two of its item count
+  LpGrids lp_grids(int lp_grid) const;
   std::map<std::string, std::pair<int, int>> tuned_;
   double t0_ = 0.0;
 };

@@ -86,15 +86,18 @@ __device__ __forceinline__ float lp_stage_epilogue(const cf (&acc)[4][3], const 
   return n2;
 }
 
-template <int PREC, int STAGE, bool UPDATE>
+// SINGLES: walk the single-slot items beside the packed kernel (lp1_tiles),
+// else every slot's items (lp_tiles).
+template <int PREC, int STAGE, bool UPDATE, bool SINGLES>
 __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArgs A) {
   extern __shared__ float4 lsm[];
   constexpr bool DAG = STAGE >= 2;
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
   constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
-  const int n = *A.n_lp_tiles;
+  const int n = SINGLES ? *A.n_lp1_tiles : *A.n_lp_tiles;
+  const int2 *items = SINGLES ? A.lp1_tiles : A.lp_tiles;
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    const int2 W = A.lp_tiles[it];
+    const int2 W = items[it];
     const GroupDev *G = A.groups + (W.x >> 4);
     const int si = G->slot[W.x & 15];
     if (!slot_running(A, si)) continue;  // uniform over the block
@@ -439,23 +442,42 @@ cudaError_t batch_configure() {
   return e;
 }
 
+int batch_lp_blocks_per_sm(int hp) {
+  int n = 0;
+  const cudaError_t e =
+      hp == PREC_F16N
+          ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_lp2_hop_kernel<PREC_F16N, 0, false>,
+                                                          kLpThreads, lp2_stage_smem<PREC_F16N>())
+          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_lp2_hop_kernel<PREC_F32, 0, false>,
+                                                          kLpThreads, lp2_stage_smem<PREC_F32>());
+  return (e == cudaSuccess && n > 0) ? n : 2;
+}
+
+// One low-precision stage: with pairing, the packed kernel over the pair
+// items and the one-lane kernel over the single items (a group's odd last
+// slot: in serving, most groups hold one solve); else the one-lane kernel
+// over every slot's items.
 template <int PREC, int STAGE, bool UPDATE>
-static void lp_stage(const BatchArgs &A, int lp_grid, cudaStream_t s) {
-  note_launch();
-  if (kBatchLpPairs)
-    batch_lp2_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp2_stage_smem<PREC>(), s>>>(A);
-  else
-    batch_lp_hop_kernel<PREC, STAGE, UPDATE><<<lp_grid, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
+static void lp_stage(const BatchArgs &A, const LpGrids &lp, cudaStream_t s) {
+  if (kBatchLpPairs) {
+    note_launch(2);
+    batch_lp2_hop_kernel<PREC, STAGE, UPDATE><<<lp.pairs, kLpThreads, lp2_stage_smem<PREC>(), s>>>(A);
+    batch_lp_hop_kernel<PREC, STAGE, UPDATE, true><<<lp.singles, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
+  } else {
+    note_launch();
+    batch_lp_hop_kernel<PREC, STAGE, UPDATE, false><<<lp.all, kLpThreads, lp_stage_smem<PREC>(), s>>>(A);
+  }
 }
 
 template <int PREC>
-static cudaError_t iteration(const BatchArgs &A, int ts, int grid, int lp_grid, cudaStream_t s) {
-  lp_stage<PREC, 0, false>(A, lp_grid, s);
-  lp_stage<PREC, 1, false>(A, lp_grid, s);
+static cudaError_t iteration(const BatchArgs &A, int ts, int grid, const LpGrids &lp, cudaStream_t s) {
+  const int lp_grid = lp.all;
+  lp_stage<PREC, 0, false>(A, lp, s);
+  lp_stage<PREC, 1, false>(A, lp, s);
   note_launch();
   batch_alpha_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
-  lp_stage<PREC, 2, false>(A, lp_grid, s);
-  lp_stage<PREC, 3, true>(A, lp_grid, s);  // Ap and the x_s, r_s update
+  lp_stage<PREC, 2, false>(A, lp, s);
+  lp_stage<PREC, 3, true>(A, lp, s);  // Ap and the x_s, r_s update
   note_launch();
   batch_beta_kernel<<<A.nslots, kReduceThreads, 0, s>>>(A);
   note_launch();
@@ -482,26 +504,28 @@ static cudaError_t iteration(const BatchArgs &A, int ts, int grid, int lp_grid, 
   return cudaGetLastError();
 }
 
+static bool valid(const LpGrids &lp) { return lp.all >= 1 && lp.pairs >= 1 && lp.singles >= 1; }
+
 cudaError_t launch_batch_iteration(const BatchArgs &A, int hp, int tile_sites, int grid,
-                                   int lp_grid, cudaStream_t s) {
-  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1 || lp_grid < 1)
+                                   const LpGrids &lp, cudaStream_t s) {
+  if (tile_sites < 32 || tile_sites > 256 || (tile_sites & 31) || grid < 1 || !valid(lp))
     return cudaErrorInvalidValue;
-  return hp == PREC_F16N ? iteration<PREC_F16N>(A, tile_sites, grid, lp_grid, s)
-                         : iteration<PREC_F32>(A, tile_sites, grid, lp_grid, s);
+  return hp == PREC_F16N ? iteration<PREC_F16N>(A, tile_sites, grid, lp, s)
+                         : iteration<PREC_F32>(A, tile_sites, grid, lp, s);
 }
 
-cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, int lp_grid, cudaStream_t s) {
-  if (lp_grid < 1) return cudaErrorInvalidValue;
+cudaError_t launch_batch_lp_apply(const BatchArgs &A, int hp, const LpGrids &lp, cudaStream_t s) {
+  if (!valid(lp)) return cudaErrorInvalidValue;
   if (hp == PREC_F16N) {
-    lp_stage<PREC_F16N, 0, false>(A, lp_grid, s);
-    lp_stage<PREC_F16N, 1, false>(A, lp_grid, s);
-    lp_stage<PREC_F16N, 2, false>(A, lp_grid, s);
-    lp_stage<PREC_F16N, 3, false>(A, lp_grid, s);
+    lp_stage<PREC_F16N, 0, false>(A, lp, s);
+    lp_stage<PREC_F16N, 1, false>(A, lp, s);
+    lp_stage<PREC_F16N, 2, false>(A, lp, s);
+    lp_stage<PREC_F16N, 3, false>(A, lp, s);
   } else {
-    lp_stage<PREC_F32, 0, false>(A, lp_grid, s);
-    lp_stage<PREC_F32, 1, false>(A, lp_grid, s);
-    lp_stage<PREC_F32, 2, false>(A, lp_grid, s);
-    lp_stage<PREC_F32, 3, false>(A, lp_grid, s);
+    lp_stage<PREC_F32, 0, false>(A, lp, s);
+    lp_stage<PREC_F32, 1, false>(A, lp, s);
+    lp_stage<PREC_F32, 2, false>(A, lp, s);
+    lp_stage<PREC_F32, 3, false>(A, lp, s);
   }
   return cudaGetLastError();
 }

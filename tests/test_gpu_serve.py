@@ -116,42 +116,42 @@ def test_serve_backpressure_and_budget(jq):
 
 
 def test_serve_lanes_small_requests_not_in_lockstep(jq):
-    """A 24^3x48 request (tol 1e-12) is submitted first and six 8^4 requests
+    """A 32^3x64 request (tol 1e-12) is submitted first and six 8^4 requests
     right after.  Small lattices run in their own lane on a high-priority
     stream, so each small request completes while the large one still
     iterates, in well under half of its latency (in one shared engine they
-    would advance in lockstep with the large solve's iterations).  Every
-    result passes the oracle's residual check and equals its solve alone."""
+    would advance in lockstep with the large solve's iterations, about 0.7 ms
+    each).  The same pattern runs once before, so the measured run finds its
+    engines tuned and its graphs captured.  Every result passes the oracle's
+    residual check and equals its solve alone."""
     jqcd, ctx = jq
-    dl, ds = (24, 24, 24, 48), (8, 8, 8, 8)
+    dl, ds = (32, 32, 32, 64), (8, 8, 8, 8)
     Ul = synth.gauge(dl, "expi", eps=0.3, seed=71)
     Us = synth.gauge(ds, "expi", eps=0.3, seed=72)
     gl, gs = ctx.gauge_upload(dl, Ul), ctx.gauge_upload(ds, Us)
     bl = host_buffer(synth.gaussian_spinor(dl, seed=73), True)
     bs = [host_buffer(synth.gaussian_spinor(ds, seed=74 + i), True) for i in range(6)]
     mode = jqcd.CG_MIXED_F16
-    # warm both lanes' engines (autotune, graph capture) outside the measurement
-    ctx.serve_start(16 << 30, max_slots=8, mode=mode)
-    xw = host_buffer(np.zeros_like(bl), True)
-    st, tw = ctx.serve_submit(gl, bl, xw, 0.12, 1e-8, mode=mode)
-    xw2 = host_buffer(np.zeros_like(bs[0]), True)
-    st2, tw2 = ctx.serve_submit(gs, bs[0], xw2, 0.12, 1e-8, mode=mode)
-    assert st == 0 and st2 == 0
-    wait_all(ctx, jqcd, [tw, tw2])
-    xl = host_buffer(np.full_like(bl, np.nan), True)
-    st, tl = ctx.serve_submit(gl, bl, xl, 0.12, 1e-12, mode=mode)
-    assert st == 0
-    time.sleep(0.002)
-    xs, ts = [], []
-    for b in bs:
-        x = host_buffer(np.full_like(b, np.nan), True)
-        st, t = ctx.serve_submit(gs, b, x, 0.12, 1e-10, mode=mode)
+    ctx.serve_start(32 << 30, max_slots=8, mode=mode)
+
+    def run(tol_l):
+        xl = host_buffer(np.full_like(bl, np.nan), True)
+        st, tl = ctx.serve_submit(gl, bl, xl, 0.12, tol_l, mode=mode)
         assert st == 0
-        xs.append(x)
-        ts.append(t)
-    res = wait_all(ctx, jqcd, [tl] + ts)
+        time.sleep(0.002)
+        xs, ts = [], []
+        for b in bs:
+            x = host_buffer(np.full_like(b, np.nan), True)
+            st, t = ctx.serve_submit(gs, b, x, 0.12, 1e-10, mode=mode)
+            assert st == 0
+            xs.append(x)
+            ts.append(t)
+        return xl, tl, xs, ts, wait_all(ctx, jqcd, [tl] + ts)
+
+    run(1e-8)  # warm-up: the same pattern
+    xl, tl, xs, ts, res = run(1e-12)
     stats = ctx.serve_stop()
-    assert stats["completed"] == 9 and stats["peak_active"] >= 2
+    assert stats["completed"] == 14 and stats["peak_active"] >= 2
     st, info_l = res[tl]
     assert st == 0
     assert system_residual(dl, Ul, bl, xl, 0.12, True) <= 1e-12 * (1 + 1e-6)
