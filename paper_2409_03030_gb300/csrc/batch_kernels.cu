@@ -96,8 +96,13 @@ __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArg
   constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
   const int n = SINGLES ? *A.n_lp1_tiles : *A.n_lp_tiles;
   const int2 *items = SINGLES ? A.lp1_tiles : A.lp_tiles;
+  // the next item is loaded while this one computes (a block's items are
+  // gridDim.x apart, each one a fresh L2 access at the head of a chain of
+  // dependent descriptor loads)
+  int2 Wnext = blockIdx.x < n ? items[blockIdx.x] : make_int2(0, 0);
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    const int2 W = items[it];
+    const int2 W = Wnext;
+    if (it + (int)gridDim.x < n) Wnext = items[it + gridDim.x];
     const GroupDev *G = A.groups + (W.x >> 4);
     const int si = G->slot[W.x & 15];
     if (!slot_running(A, si)) continue;  // uniform over the block
@@ -138,8 +143,10 @@ __global__ void __launch_bounds__(kLpThreads, JQCD_BATCH_LP2_MIN_BLOCKS) batch_l
   constexpr int OUTP = (STAGE == 0 || STAGE == 2) ? 1 : 0;
   constexpr bool NORM = STAGE == 1 || (STAGE == 3 && UPDATE);
   const int n = *A.n_lp2_tiles;
+  int2 Wnext = blockIdx.x < n ? A.lp2_tiles[blockIdx.x] : make_int2(0, 0);  // loaded one item ahead
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
-    const int2 W = A.lp2_tiles[it];
+    const int2 W = Wnext;
+    if (it + (int)gridDim.x < n) Wnext = A.lp2_tiles[it + gridDim.x];
     const GroupDev *G = A.groups + (W.x >> 4);
     const int r0 = W.x & 15;
     const int s0 = G->slot[r0];
