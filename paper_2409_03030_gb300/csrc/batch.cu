@@ -306,7 +306,7 @@ cudaError_t BatchEngine::rebuild() {
       for (int r = 0; r < ns; ++r) {
         lp_tiles.push_back(make_int2((int)gi * 16 + r, j));
         if (r % 2 == 0 && r + 1 < ns) lp2_tiles.push_back(make_int2((int)gi * 16 + r, j));
-        if (r % 2 == 0 && r + 1 == ns) lp1_tiles.push_back(make_int2((int)gi * 16 + r, j));
+        if (r % 2 == 0 && r + 1 == ns) lp1_tiles.push_back(make_int2(groups[gi].slot[r], j));
       }
   }
   if ((int64_t)lp_tiles.size() > max_lp_tiles_) {

@@ -58,8 +58,8 @@ struct BatchArgs {
   const int *n_lp_tiles;
   int2 *lp2_tiles;       // the same with the first slot of each pair of a group (slots
   const int *n_lp2_tiles;  // 0, 2, 4, ...): items of the packed low-precision stages
-  int2 *lp1_tiles;       // the last slot of each group with an odd count: items of the
-  const int *n_lp1_tiles;  // one-lane low-precision stages beside the packed ones
+  int2 *lp1_tiles;       // (slot, block of kLpThreads sites) for the last slot of each group
+  const int *n_lp1_tiles;  // with an odd count: items of the one-lane stages beside the packed ones
   int *any_update;       // nonzero when some slot requested a reliable update
   int nslots;            // descriptors allocated (grid of per-slot kernels)
 };

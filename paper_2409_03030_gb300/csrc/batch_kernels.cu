@@ -103,17 +103,18 @@ __global__ void __launch_bounds__(kLpThreads) batch_lp_hop_kernel(const BatchArg
   for (int it = blockIdx.x; it < n; it += gridDim.x) {
     const int2 W = Wnext;
     if (it + (int)gridDim.x < n) Wnext = items[it + gridDim.x];
-    const GroupDev *G = A.groups + (W.x >> 4);
-    const int si = G->slot[W.x & 15];
+    // single items carry the slot itself; the others (group, slot in group)
+    const int si = SINGLES ? W.x : A.groups[W.x >> 4].slot[W.x & 15];
     if (!slot_running(A, si)) continue;  // uniform over the block
     const SlotDev &Sl = A.slots[si];
-    const Geom g = G->g;
+    const Geom g = Sl.g;
     const int64_t idx = (int64_t)W.y * kLpThreads + threadIdx.x;
     float n2 = 0.f;
     if (idx < g.vh) {
       const void *in = STAGE == 0 ? Sl.p : (STAGE == 2 ? Sl.w : Sl.t);
       cf acc[4][3];
-      lp_hop_site<PREC, DAG, true>(lsm, in, G->gauge_f32, g, OUTP, idx, acc);
+      // a single solve's links are read once per site: streamed past L1
+      lp_hop_site<PREC, DAG, !SINGLES>(lsm, in, Sl.gauge_f32, g, OUTP, idx, acc);
       n2 = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, Sl, A.S[si], g.vh, idx);
     }
     if (NORM) {
