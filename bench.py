@@ -437,15 +437,17 @@ def bench_batch(ctx, jqcd, synth, np):
     ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode, out=outs)  # warm-up + autotune
     gA.cg_solve(bs[0], KAPPA, tol=TOL, mode=mode, out=outs[0])  # warm-up
     reps = 3  # both ways alternate; each is reported as the best of its repetitions
-    tb, ts = [], []
+    tb, ts, tsg = [], [], []
     for _ in range(reps):
         t0 = time.perf_counter()
         xs, infos, st = ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode, out=outs)
         tb.append(time.perf_counter() - t0)
         t0 = time.perf_counter()
+        gpu = 0.0
         for g, b, o in zip(gauges, bs, outs):
-            g.cg_solve(b, KAPPA, tol=TOL, mode=mode, out=o)
+            gpu += g.cg_solve(b, KAPPA, tol=TOL, mode=mode, out=o)[1]["gpu_seconds"]
         ts.append(time.perf_counter() - t0)
+        tsg.append(gpu)
     t_batch, t_seq = min(tb), min(ts)
     out = {"workload": "12 point sources 24^3x48 + 12 Gaussian 16^4, kappa 0.12, tol 1e-10, "
                        "mixed FP16, one batch (pinned host buffers, reused)",
@@ -453,6 +455,7 @@ def bench_batch(ctx, jqcd, synth, np):
            "speedup": round(t_seq / t_batch, 3), "solves_per_s": round(24 / t_batch, 2),
            "repetitions": reps, "batch_all_s": [round(v, 4) for v in tb],
            "sequential_all_s": [round(v, 4) for v in ts],
+           "sequential_gpu_s": round(min(tsg), 4),  # device time of the 24 solves proper
            "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
            "iters": [infos[0]["iters"], infos[12]["iters"]], "status": st}
     gA.free()
@@ -724,8 +727,19 @@ def run_gpu(args):
     multishift = bench_multishift(jqcd, g, stream, be)
     staggered = bench_staggered(jqcd, synth, torch, stream, g)
     hmc = bench_hmc(ctx, jqcd, synth, np)
-    batch = bench_batch(ctx, jqcd, synth, np) if not args.no_batch else None
-    serve = (bench_serve(ctx, jqcd, synth, np, args.serve_requests, host=args.serve_host)
+    def with_clocks(fn):
+        """fn() with the SM clocks sampled while it runs (added as "clocks")."""
+        smp = ClockSampler(local)
+        smp.start()
+        out = fn()
+        clk = smp.stop()
+        if out is not None:
+            out["clocks"] = clk
+        return out
+
+    batch = with_clocks(lambda: bench_batch(ctx, jqcd, synth, np)) if not args.no_batch else None
+    serve = (with_clocks(lambda: bench_serve(ctx, jqcd, synth, np, args.serve_requests,
+                                             host=args.serve_host))
              if args.serve_requests > 0 else None)
 
     # 32^3x64: each mode's solution against the plain FP64 GPU solve's
