@@ -171,11 +171,12 @@ def peaks():
 
 # FP32 lane operations (add, mul or fma, each on one lane) per output site of
 # the plain double-word hop, counted from its arithmetic: per hop, projection
-# 6 x 9, link conjugation 9 x 2, mat-vec 2 x 3 x (2 x 17 + 2) (offset-grid
-# sums: 5 + 6 + 6 per sum of three products, 2 to join A + iB) and
-# reconstruction 2 x 3 x 17 packed two-lane operations; epilogue 12 x 10
-# packed; times 2 lanes; plus the grid bounds, 2 x 5 + 1 scalar per hop.
-DW_HOP_LANE_OPS = 2 * (8 * (6 * 9 + 9 * 2 + 2 * 3 * (2 * 17 + 2) + 2 * 3 * 17) + 12 * 10) + 8 * (2 * 5 + 1)
+# 6 x 9, mat-vec 2 x 3 x (2 x 17 + 2) (offset-grid sums: 5 + 6 + 6 per sum of
+# three products, 2 to join A + iB) and reconstruction 2 x 3 x 17 packed
+# two-lane operations; epilogue 12 x 10 packed; times 2 lanes; plus the grid
+# bounds, 2 x 5 + 1 scalar per hop.  The backward links are conjugated by
+# flipping sign bits, which is no floating-point operation.
+DW_HOP_LANE_OPS = 2 * (8 * (6 * 9 + 2 * 3 * (2 * 17 + 2) + 2 * 3 * 17) + 12 * 10) + 8 * (2 * 5 + 1)
 NOMINAL_HBM_GBS = 7900.0
 
 

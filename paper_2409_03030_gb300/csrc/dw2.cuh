@@ -87,6 +87,12 @@ __device__ __forceinline__ p2 p2_norm(p2 a) {  // Fast2Sum per lane
 }
 __device__ __forceinline__ p2 p2_swap(p2 a) { return p2{f2_swap(a.h), f2_swap(a.l)}; }
 __device__ __forceinline__ p2 p2_scale_sgn(p2 a, f2 sg) { return p2{f2_mul(sg, a.h), f2_mul(sg, a.l)}; }
+// complex conjugate of a double-word complex number: the sign bits of both
+// words' imaginary lanes flipped (integer ALU, no floating-point operation)
+__device__ __forceinline__ p2 p2_conj(p2 a) {
+  constexpr f2 kLane1Sign = 0x8000000000000000ull;
+  return p2{a.h ^ kLane1Sign, a.l ^ kLane1Sign};
+}
 
 // Compensated accumulator pair: sum of exact high products in s (TwoSum),
 // every error and low-order term in c.

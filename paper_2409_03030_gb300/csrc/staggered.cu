@@ -71,9 +71,8 @@ __device__ __forceinline__ void stag_hop_sum(const Geom &g, int p, int64_t cb, c
       h[c] = p2{v.x, v.y};
     }
     if (bwd) {
-      const f2 cc = f2_make(1.f, -1.f);
 #pragma unroll
-      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_scale_sgn(W[k / 3][k % 3], cc);
+      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = p2_conj(W[k / 3][k % 3]);
     }
     p2 r[3];
     matvec_half_ts(W, h, r);
