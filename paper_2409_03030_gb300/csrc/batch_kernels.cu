@@ -17,8 +17,6 @@
 
 namespace jqcd {
 
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 __device__ __forceinline__ bool slot_running(const BatchArgs &A, int si) {
   return A.slots[si].active && !A.S[si].halt;
 }

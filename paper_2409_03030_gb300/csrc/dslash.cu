@@ -191,12 +191,8 @@ static cudaError_t launch_hop_p(const HopParams &P, bool dag, bool axpy, bool no
 // mul.rn.f32x2 per complex operation halves the instruction issue of a
 // scalar double-word hop, which was bound by issue rather than by the FP32
 // datapath.
-#ifndef JQCD_DWP_MIN_BLOCKS  // resident blocks per SM the register budget is cut for
-#define JQCD_DWP_MIN_BLOCKS 3
-#endif
-
 template <bool DAG, bool AXPY, bool NORM>
-__global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kernel(const HopParams P) {
+__global__ void __launch_bounds__(kDwp1Threads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kernel(const HopParams P) {
   extern __shared__ float4 dsm[];
   pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
@@ -204,8 +200,8 @@ __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kern
   dwacc nrm{0.f, 0.f};
   if (idx < P.g.vh) {
     p2 acc[4][3];
-    dwp_hop_site<DAG>(dsm, reinterpret_cast<const float4 *>(P.in),
-                      reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
+    dwp_hop_site<DAG, kDwp1Threads>(dsm, reinterpret_cast<const float4 *>(P.in),
+                                    reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
     nrm = dwp_store<AXPY, NORM>(acc, reinterpret_cast<float4 *>(P.out),
                                 reinterpret_cast<const float4 *>(P.x), P.g.vh, idx, P.a_split, P.b_split);
   }
@@ -217,9 +213,9 @@ __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp_kern
 
 // Small lattices: two threads per output site (dwp_pair_combine), so the
 // grid holds twice as many warps when one thread per site cannot fill the
-// GPU.  Blocks of kHopThreads threads cover kHopThreads / 2 sites.
+// GPU.  Blocks of kDwp2Threads threads cover kDwp2Threads / 2 sites.
 template <bool DAG, bool AXPY, bool NORM>
-__global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp2_kernel(const HopParams P) {
+__global__ void __launch_bounds__(kDwp2Threads, JQCD_DWP2_MIN_BLOCKS) hop_dwp2_kernel(const HopParams P) {
   extern __shared__ float4 dsm[];
   pdl_enter();
   if (P.guard && *P.guard) return;  // uniform across the grid
@@ -229,8 +225,9 @@ __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp2_ker
   const bool active = idx < P.g.vh;  // the same for both threads of a site
   p2 acc[4][3];
   if (active) {
-    dwp_hop_dirs<DAG>(dsm, reinterpret_cast<const float4 *>(P.in),
-                      reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q, 2, 4, acc);
+    dwp_hop_dirs<DAG, kDwp2Threads>(dsm, reinterpret_cast<const float4 *>(P.in),
+                                     reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q,
+                                     2, 4, acc);
   } else {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -251,22 +248,26 @@ __global__ void __launch_bounds__(kHopThreads, JQCD_DWP_MIN_BLOCKS) hop_dwp2_ker
 }
 
 // Two threads per site pay off only while their grid fits in one wave of
-// resident blocks (measured on GB300: 8^4 hop 9.6 -> 7.5 us; at 16^4, where
+// resident warps (measured on GB300: 8^4 hop 9.6 -> 5.9 us; at 16^4, where
 // the split grid needs 1.12 waves, 19.1 -> 18.6 us and the solve slower;
-// 16^3x32 at 2.25 waves 24.8 -> 30.4 us).
+// 16^3x32 at 2.25 waves 24.8 -> 30.4 us).  Twelve warps per SM is the most
+// the split kernel's 164-168 registers allow: a thirteenth puts a fourth
+// warp on one SM sub-partition, whose register file then caps every thread
+// at 128 registers (the kernel spilled 402 bytes and ran 25-40% slower).
 bool dw_hop_split(int64_t vh) {
   static const int64_t max_vh = [] {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
       return (int64_t)0;
-    return (int64_t)sms * JQCD_DWP_MIN_BLOCKS * kHopThreads / 2;
+    return (int64_t)sms * JQCD_DWP2_MIN_BLOCKS * kDwp2Threads / 2;
   }();
   return vh <= max_vh && vh <= JQCD_DWP_SPLIT_MAX_VH;
 }
 
 unsigned dw_hop_blocks(int64_t vh) {
-  return dw_hop_split(vh) ? (unsigned)((2 * vh + kHopThreads - 1) / kHopThreads) : hop_blocks(vh);
+  return dw_hop_split(vh) ? (unsigned)((2 * vh + kDwp2Threads - 1) / kDwp2Threads)
+                          : (unsigned)((vh + kDwp1Threads - 1) / kDwp1Threads);
 }
 
 unsigned hop_norm_partials(int prec, int64_t vh) {
@@ -280,14 +281,14 @@ static cudaError_t launch_hop_dw_t(const HopParams &P, cudaStream_t s) {
   auto kern = hop_dwp_kernel<DAG, AXPY, NORM>;
   auto kern2 = hop_dwp2_kernel<DAG, AXPY, NORM>;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwp1Smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwpSmem);
+      e = cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwp2Smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  if (dw_hop_split(P.g.vh)) return launch_pdl(kern2, dw_hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P);
-  return launch_pdl(kern, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P);
+  if (dw_hop_split(P.g.vh)) return launch_pdl(kern2, dw_hop_blocks(P.g.vh), kDwp2Threads, kDwp2Smem, s, P);
+  return launch_pdl(kern, dw_hop_blocks(P.g.vh), kDwp1Threads, kDwp1Smem, s, P);
 }
 
 static cudaError_t launch_hop_dw(const HopParams &P, bool dag, bool axpy, bool norm, cudaStream_t s) {

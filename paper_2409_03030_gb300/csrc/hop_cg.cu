@@ -68,7 +68,7 @@ __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&v)[NC], int k0, const f
 }
 
 template <bool XUPD>
-__global__ void __launch_bounds__(kHopThreads, 3)
+__global__ void __launch_bounds__(kDwp1Threads, JQCD_DWP_MIN_BLOCKS)
     hop_dwp_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
                       float4 *__restrict__ r, const float2 *__restrict__ alpha) {
   extern __shared__ float4 dsm[];
@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(kHopThreads, 3)
   dwacc nrm{0.f, 0.f};
   if (idx < P.g.vh) {
     p2 acc[4][3];
-    dwp_hop_site<true>(dsm, reinterpret_cast<const float4 *>(P.in),
-                       reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
+    dwp_hop_site<true, kDwp1Threads>(dsm, reinterpret_cast<const float4 *>(P.in),
+                                     reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, acc);
     p2 v[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = acc[k / 3][k % 3];
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kHopThreads, 3)
 // The same with two threads per output site (small lattices, see
 // dwp_pair_combine): thread q updates components 6q .. 6q + 5.
 template <bool XUPD>
-__global__ void __launch_bounds__(kHopThreads, 3)
+__global__ void __launch_bounds__(kDwp2Threads, JQCD_DWP2_MIN_BLOCKS)
     hop_dwp2_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
                        float4 *__restrict__ r, const float2 *__restrict__ alpha) {
   extern __shared__ float4 dsm[];
@@ -105,8 +105,9 @@ __global__ void __launch_bounds__(kHopThreads, 3)
   const bool active = idx < P.g.vh;
   p2 acc[4][3];
   if (active) {
-    dwp_hop_dirs<true>(dsm, reinterpret_cast<const float4 *>(P.in),
-                       reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q, 2, 4, acc);
+    dwp_hop_dirs<true, kDwp2Threads>(dsm, reinterpret_cast<const float4 *>(P.in),
+                                      reinterpret_cast<const float4 *>(P.gauge), P.g, P.out_parity, idx, q, 2,
+                                      4, acc);
   } else {
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -191,17 +192,18 @@ static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x
   static bool configured = false;  // one attribute call per instantiation
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDwpSmem);
+                                         (int)kDwp1Smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(hop_dwp2_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)kDwpSmem);
+                               (int)kDwp2Smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   if (dw_hop_split(P.g.vh))
-    return launch_pdl(hop_dwp2_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P, p, x,
+    return launch_pdl(hop_dwp2_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kDwp2Threads, kDwp2Smem, s, P, p, x,
                       r, alpha);
-  return launch_pdl(hop_dwp_cg_kernel<XUPD>, hop_blocks(P.g.vh), kHopThreads, kDwpSmem, s, P, p, x, r, alpha);
+  return launch_pdl(hop_dwp_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kDwp1Threads, kDwp1Smem, s, P, p, x, r,
+                    alpha);
 }
 
 cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,

@@ -51,6 +51,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool ke
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Neighbour of hop d (mu = d/2, backward when d is odd) and its boundary sign.
 __device__ __forceinline__ int64_t hop_neighbour(const Geom &g, int x, int y, int z, int t, int d,

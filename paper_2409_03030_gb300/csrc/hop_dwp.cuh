@@ -19,19 +19,50 @@ namespace jqcd {
 
 constexpr int kDwpStageChunks = 12;  // one double-word spinor per thread
 constexpr int kDwpLinkChunks = 9;    // one double-word link per thread and stage
-// one neighbour-spinor stage and two link stages, chunk-major [k][thread]
-constexpr size_t kDwpSmem = (size_t)(kDwpStageChunks + 2 * kDwpLinkChunks) * kHopThreads * 16;
+// one neighbour-spinor stage and two link stages, chunk-major [k][thread],
+// for blocks of nt threads
+constexpr size_t dwp_smem(int nt = kHopThreads) {
+  return (size_t)(kDwpStageChunks + 2 * kDwpLinkChunks) * nt * 16;
+}
+constexpr size_t kDwpSmem = dwp_smem();
 
-// Issue the copies of the neighbour spinor of one hop into its stage.
+// Launch shapes of the single-field kernels: threads per block and the
+// resident blocks per SM their register budget is cut for, one thread per
+// output site (DWP) and two (DWP2, small lattices).  One-warp blocks spread
+// a small lattice's split grid over more SMs (measured on GB300: 8^4 hop
+// 7.35 -> 5.87 us, 12^4 10.9 -> 8.85 us against 128-thread blocks).  The
+// one-thread kernel keeps 128: with one-warp blocks its plain hop ran 1%
+// faster at 24^3x48 but the solve 1.2% slower (four times the norm partials).
+#ifndef JQCD_DWP_THREADS
+#define JQCD_DWP_THREADS 128
+#endif
+#ifndef JQCD_DWP_MIN_BLOCKS
+#define JQCD_DWP_MIN_BLOCKS 3
+#endif
+#ifndef JQCD_DWP2_THREADS
+#define JQCD_DWP2_THREADS 32
+#endif
+#ifndef JQCD_DWP2_MIN_BLOCKS
+#define JQCD_DWP2_MIN_BLOCKS 12
+#endif
+constexpr int kDwp1Threads = JQCD_DWP_THREADS;
+constexpr size_t kDwp1Smem = dwp_smem(kDwp1Threads);
+constexpr int kDwp2Threads = JQCD_DWP2_THREADS;
+constexpr size_t kDwp2Smem = dwp_smem(kDwp2Threads);
+
+// Issue the copies of the neighbour spinor of one hop into its stage (NT:
+// threads per block, the stride of the chunk-major stage).
+template <int NT = kHopThreads>
 __device__ __forceinline__ void stage_hop_p(float4 *st, const float4 *in, int64_t vh, int64_t nb) {
   const int tid = threadIdx.x;
 #pragma unroll
-  for (int k = 0; k < 12; ++k) cp_async16(st + k * kHopThreads + tid, in + k * vh + nb, true);
+  for (int k = 0; k < 12; ++k) cp_async16(st + k * NT + tid, in + k * vh + nb, true);
 }
 
 // Issue the copies of the link of hop d (mu = d/2, backward when d is odd)
 // into a link stage, element (a, b) at chunk 3a + b: U_mu(x) for a forward
 // hop, the transpose of U_mu(x - mu) (conjugated at use) for a backward one.
+template <int NT = kHopThreads>
 __device__ __forceinline__ void stage_link_p(float4 *st, const float4 *gauge, int64_t vh, int p, int d,
                                              int64_t idx, int64_t nb) {
   const int tid = threadIdx.x;
@@ -43,7 +74,7 @@ __device__ __forceinline__ void stage_link_p(float4 *st, const float4 *gauge, in
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int b = 0; b < 3; ++b)
-      cp_async16(st + (a * 3 + b) * kHopThreads + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
+      cp_async16(st + (a * 3 + b) * NT + tid, L + (int64_t)(a * sa + b * sb) * vh, false);
 }
 
 __device__ __forceinline__ p2 ld_p2(const float4 *p) {
@@ -200,14 +231,14 @@ __device__ __forceinline__ void reconstruct_half_mu(int mu, const p2 (&r)[3], p2
 // idx of parity p (DAG: the adjoint hop), unnormalised double-word
 // accumulators.  All eight hops (d0 = 0, dstep = 1, nd = 8) give
 // (H_{p,1-p} in)(idx).  dsm: this block's kDwpSmem bytes of shared memory;
-// blockDim.x must be kHopThreads.
+// blockDim.x must be NT.
 //
 // Copies run one hop ahead: the links of the next hop are issued when hop d
 // starts (two link stages), the neighbour spinor of the next hop as soon as
 // hop d's has been read into registers and projected (one stage).  Every
 // thread reads and overwrites only its own column, so no block barrier is
 // needed; the completed-group wait of each hop covers both of its copies.
-template <bool DAG>
+template <bool DAG, int NT = kHopThreads>
 __device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, const float4 *gauge,
                                              const Geom &g, int p, int64_t idx, int d0, int dstep,
                                              int nd, p2 (&acc)[4][3]) {
@@ -219,11 +250,11 @@ __device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, cons
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[a][c] = p2{0ull, 0ull};
   const int tid = threadIdx.x;
-  float4 *const lnk = dsm + kDwpStageChunks * kHopThreads;  // two link stages
+  float4 *const lnk = dsm + kDwpStageChunks * NT;  // two link stages
   bool neg_next;
   int64_t nb = hop_neighbour(g, x, y, z, t, d0, neg_next);
-  stage_hop_p(dsm, in, vh, nb);
-  stage_link_p(lnk, gauge, vh, p, d0, idx, nb);
+  stage_hop_p<NT>(dsm, in, vh, nb);
+  stage_link_p<NT>(lnk, gauge, vh, p, d0, idx, nb);
   cp_async_commit();
 #pragma unroll 1
   for (int j = 0; j < nd; ++j) {
@@ -234,18 +265,18 @@ __device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, cons
     const bool more = j + 1 < nd;
     if (more) {  // the other link stage was read during the previous hop
       nb = hop_neighbour(g, x, y, z, t, d + dstep, neg_next);
-      stage_link_p(lnk + ((j + 1) & 1) * kDwpLinkChunks * kHopThreads, gauge, vh, p, d + dstep, idx, nb);
+      stage_link_p<NT>(lnk + ((j + 1) & 1) * kDwpLinkChunks * NT, gauge, vh, p, d + dstep, idx, nb);
     }
     cp_async_commit();
     cp_async_wait1();  // this thread's spinor and link copies of hop d have landed
     p2 psi[4][3];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(dsm + k * kHopThreads + tid);
+    for (int k = 0; k < 12; ++k) psi[k / 3][k % 3] = ld_p2(dsm + k * NT + tid);
     p2 W[3][3];
     {
-      const float4 *ls = lnk + (j & 1) * kDwpLinkChunks * kHopThreads + tid;
+      const float4 *ls = lnk + (j & 1) * kDwpLinkChunks * NT + tid;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = ld_p2(ls + k * kHopThreads);
+      for (int k = 0; k < 9; ++k) W[k / 3][k % 3] = ld_p2(ls + k * NT);
     }
     const float S = (bwd != DAG) ? 1.f : -1.f;
     p2 h[2][3];
@@ -255,7 +286,7 @@ __device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, cons
       case 2: project_p<2>(psi, h, S); break;
       default: project_p<3>(psi, h, S);
     }
-    if (more) stage_hop_p(dsm, in, vh, nb);  // the spinor stage has been read
+    if (more) stage_hop_p<NT>(dsm, in, vh, nb);  // the spinor stage has been read
     cp_async_commit();
     if (neg) {
       const f2 mm = f2_make(-1.f, -1.f);
@@ -283,10 +314,10 @@ __device__ __forceinline__ void dwp_hop_dirs(float4 *dsm, const float4 *in, cons
 }
 
 // (H_{p,1-p} in)(idx): all eight hops in one thread.
-template <bool DAG>
+template <bool DAG, int NT = kHopThreads>
 __device__ __forceinline__ void dwp_hop_site(float4 *dsm, const float4 *in, const float4 *gauge,
                                              const Geom &g, int p, int64_t idx, p2 (&acc)[4][3]) {
-  dwp_hop_dirs<DAG>(dsm, in, gauge, g, p, idx, 0, 1, 8, acc);
+  dwp_hop_dirs<DAG, NT>(dsm, in, gauge, g, p, idx, 0, 1, 8, acc);
 }
 
 // Two threads per output site (lanes 2i and 2i + 1 of a warp, q = lane & 1):
