@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kLpThreads, JQCD_BATCH_LP2_MIN_BLOCKS) batch_l
         lp2_lane(acc2, 1, acc);
         n2b = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, S1, A.S[sb], g.vh, idx);
       } else {  // a single running slot: the one-lane site loop
-        lp_hop_site<PREC, DAG, true>(lsm, in0, G->gauge_f32, g, OUTP, idx, acc);
+        lp_hop_site<PREC, DAG, true, Lp2Stage<PREC>::kChunks, 2 * Lp2Stage<PREC>::kSpin>(lsm, in0, G->gauge_f32,
+                                                                                     g, OUTP, idx, acc);
         n2a = lp_stage_epilogue<PREC, STAGE, UPDATE>(acc, S0, A.S[sa], g.vh, idx);
       }
     }

@@ -30,14 +30,30 @@ template <int PREC> constexpr size_t lp_stage_smem() {
   return 2ull * LpStage<PREC>::kChunks * kHopThreads * 16;
 }
 
+// The FP16 site norm of a stage slot sits in the fourth chunk plane at a
+// 4-byte stride (thread t at float t of the plane): one 128-byte wavefront
+// per warp to write and to read, where a 16-byte stride took four.
+#ifndef JQCD_LP_DENSE_NORM
+#define JQCD_LP_DENSE_NORM 1
+#endif
+__device__ __forceinline__ float *lp_norm_slot(float4 *plane, int tid) {
+  return JQCD_LP_DENSE_NORM ? reinterpret_cast<float *>(plane) + tid : reinterpret_cast<float *>(plane + tid);
+}
+// The same from a thread-offset stage pointer (st = stage + tid).
+__device__ __forceinline__ float lp_norm_read(const float4 *st_plane_tid, int tid) {
+  return JQCD_LP_DENSE_NORM ? reinterpret_cast<const float *>(st_plane_tid - tid)[tid]
+                            : reinterpret_cast<const float *>(st_plane_tid)[0];
+}
+
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 
 // Copies of hop d's neighbour spinor (site nb of the input parity) and link
-// (forward: U_mu(idx) of parity p; backward: U_mu(nb) of parity 1-p).
-template <int PREC, bool LINK_L1>
+// (forward: U_mu(idx) of parity p; backward: U_mu(nb) of parity 1-p); the
+// link goes to chunk planes LK .. LK + 2 of the stage.
+template <int PREC, bool LINK_L1, int LK = LpStage<PREC>::kSpin>
 __device__ __forceinline__ void lp_stage_issue(float4 *st, const void *in, const float4 *gauge,
                                                int64_t vh, int p, int64_t idx, int d, int64_t nb) {
   typedef LpStage<PREC> S;
@@ -50,22 +66,21 @@ __device__ __forceinline__ void lp_stage_issue(float4 *st, const void *in, const
     const uint4 *src = reinterpret_cast<const uint4 *>(in);
 #pragma unroll
     for (int k = 0; k < 3; ++k) cp_async16(st + k * kHopThreads + tid, src + k * vh + nb, true);
-    cp_async4(st + 3 * kHopThreads + tid, reinterpret_cast<const float *>(src + 3 * vh) + nb);
+    cp_async4(lp_norm_slot(st + 3 * kHopThreads, tid), reinterpret_cast<const float *>(src + 3 * vh) + nb);
   }
   const int mu = d >> 1;
   const bool bwd = (d & 1) != 0;
   const float4 *L = gauge + (size_t)(((bwd ? 1 - p : p) * 4 + mu) * 3) * vh + (bwd ? nb : idx);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) cp_async16(st + (S::kSpin + k) * kHopThreads + tid, L + k * vh, LINK_L1);
+  for (int k = 0; k < 3; ++k) cp_async16(st + (LK + k) * kHopThreads + tid, L + k * vh, LINK_L1);
 }
 
 // Spinor and link of one stage slot (st already offset by the thread).  For
 // FP16 the spinor comes back unscaled and *norm holds the site norm (the
 // caller scales the projected half-spinor: 12 multiplies instead of 24);
 // for FP32 *norm = 1.
-template <int PREC>
+template <int PREC, int LK = LpStage<PREC>::kSpin>
 __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3], cf (&u)[3][3], float *norm) {
-  typedef LpStage<PREC> S;
   if (PREC == PREC_F32) {
 #pragma unroll
     for (int j = 0; j < 6; ++j) {
@@ -75,7 +90,7 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
     }
     *norm = 1.f;
   } else {
-    *norm = reinterpret_cast<const float *>(st + 3 * kHopThreads)[0];
+    *norm = lp_norm_read(st + 3 * kHopThreads, threadIdx.x);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const uint4 v = reinterpret_cast<const uint4 *>(st)[j * kHopThreads];
@@ -88,8 +103,8 @@ __device__ __forceinline__ void lp_stage_read(const float4 *st, cf (&psi)[4][3],
       }
     }
   }
-  PT_F32Links::link_from_chunks(st[S::kSpin * kHopThreads], st[(S::kSpin + 1) * kHopThreads],
-                                st[(S::kSpin + 2) * kHopThreads], u);
+  PT_F32Links::link_from_chunks(st[LK * kHopThreads], st[(LK + 1) * kHopThreads], st[(LK + 2) * kHopThreads],
+                                u);
 }
 
 // One hop: project, site norm (FP16) and boundary sign, link multiply,
@@ -114,11 +129,14 @@ __device__ __forceinline__ void lp_apply(const cf (&psi)[4][3], const cf (&u)[3]
 }
 
 // acc = (H_{p,1-p} in)(idx) (DAG: the adjoint hop); smem: this block's
-// lp_stage_smem<PREC>() bytes; blockDim.x must be kHopThreads.
-template <int PREC, bool DAG, bool LINK_L1>
+// lp_stage_smem<PREC>() bytes; blockDim.x must be kHopThreads.  C and LK: the
+// chunk planes of a stage and the first link plane; a kernel that also runs
+// the two-lane hop of hop_lp2.cuh in the same buffer passes that layout's,
+// so that every shared-memory word keeps one owner thread in both (the site
+// norms are not in their thread's own column).
+template <int PREC, bool DAG, bool LINK_L1, int C = LpStage<PREC>::kChunks, int LK = LpStage<PREC>::kSpin>
 __device__ __forceinline__ void lp_hop_site(float4 *smem, const void *in, const float4 *gauge,
                                             const Geom &g, int p, int64_t idx, cf (&acc)[4][3]) {
-  constexpr int C = LpStage<PREC>::kChunks;
   const int64_t vh = g.vh;
   int x, y, z, t;
   cb_coords(g, idx, p, x, y, z, t);
@@ -129,20 +147,21 @@ __device__ __forceinline__ void lp_hop_site(float4 *smem, const void *in, const 
   const int tid = threadIdx.x;
   bool neg_next;
   int64_t nb = hop_neighbour(g, x, y, z, t, 0, neg_next);
-  lp_stage_issue<PREC, LINK_L1>(smem, in, gauge, vh, p, idx, 0, nb);
+  lp_stage_issue<PREC, LINK_L1, LK>(smem, in, gauge, vh, p, idx, 0, nb);
   cp_async_commit();
 #pragma unroll
   for (int d = 0; d < 8; ++d) {
     const bool neg = neg_next;
     if (d < 7) {
       nb = hop_neighbour(g, x, y, z, t, d + 1, neg_next);
-      lp_stage_issue<PREC, LINK_L1>(smem + ((d + 1) & 1) * C * kHopThreads, in, gauge, vh, p, idx, d + 1, nb);
+      lp_stage_issue<PREC, LINK_L1, LK>(smem + ((d + 1) & 1) * C * kHopThreads, in, gauge, vh, p, idx, d + 1,
+                                        nb);
     }
     cp_async_commit();
     cp_async_wait1();  // this thread's copies of hop d have landed
     cf psi[4][3], u[3][3];
     float nrm;
-    lp_stage_read<PREC>(smem + (d & 1) * C * kHopThreads + tid, psi, u, &nrm);
+    lp_stage_read<PREC, LK>(smem + (d & 1) * C * kHopThreads + tid, psi, u, &nrm);
     switch (d) {  // d is a constant after unrolling
       case 0: lp_apply<PREC, 0, false, DAG>(psi, u, nrm, neg, acc); break;
       case 1: lp_apply<PREC, 0, true, DAG>(psi, u, nrm, neg, acc); break;

@@ -31,10 +31,8 @@ template <int PREC> struct Lp2Stage {
 template <int PREC> constexpr size_t lp2_stage_smem() {
   return 2ull * Lp2Stage<PREC>::kChunks * kHopThreads * 16;
 }
-// The packed kernels fall back to the one-lane site loop in the same buffer.
-static_assert(lp2_stage_smem<PREC_F32>() >= lp_stage_smem<PREC_F32>() &&
-                  lp2_stage_smem<PREC_F16N>() >= lp_stage_smem<PREC_F16N>(),
-              "the packed stages hold the one-lane stages");
+// The packed kernels fall back to the one-lane site loop in the same buffer,
+// laid out as the packed stages (lp_hop_site with C = kChunks, LK = 2 kSpin).
 
 // a + PH * b for a phase code PH (0: +1, 1: +i, 2: -1, 3: -i), lane-wise.
 template <int PH> __device__ __forceinline__ cp2 add_phase(cp2 a, cp2 b) {
@@ -56,7 +54,7 @@ __device__ __forceinline__ void lp2_issue_spinor(float4 *st, const void *in, int
     const uint4 *src = reinterpret_cast<const uint4 *>(in);
 #pragma unroll
     for (int k = 0; k < 3; ++k) cp_async16(st + k * kHopThreads + tid, src + k * vh + nb, true);
-    cp_async4(st + 3 * kHopThreads + tid, reinterpret_cast<const float *>(src + 3 * vh) + nb);
+    cp_async4(lp_norm_slot(st + 3 * kHopThreads, tid), reinterpret_cast<const float *>(src + 3 * vh) + nb);
   }
 }
 
@@ -90,8 +88,8 @@ __device__ __forceinline__ void lp2_read_spinors(const float4 *st, cp2 (&psi)[4]
     }
     nrm = f2_make(1.f, 1.f);
   } else {
-    nrm = f2_make(reinterpret_cast<const float *>(st + 3 * kHopThreads)[0],
-                  reinterpret_cast<const float *>(st + (S::kSpin + 3) * kHopThreads)[0]);
+    nrm = f2_make(lp_norm_read(st + 3 * kHopThreads, threadIdx.x),
+                  lp_norm_read(st + (S::kSpin + 3) * kHopThreads, threadIdx.x));
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const uint4 va = reinterpret_cast<const uint4 *>(st)[j * kHopThreads];
