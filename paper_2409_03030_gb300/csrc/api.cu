@@ -464,6 +464,17 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
   std::vector<int> done;
   jqcd_status worst = JQCD_OK;
   double t_collect = 0.0;
+  // verbose >= 2: device time of the iteration graphs beside the wall time
+  struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  const bool graph_time = timing && cudaEventCreate(&ev.a) == cudaSuccess && cudaEventCreate(&ev.b) == cudaSuccess;
+  double t_graphs = 0.0;
+  int n_polls = 0;
   auto finish_one = [&](int i) {
     jqcd_solve_info inf;
     E->finish(i, &inf);
@@ -471,10 +482,18 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
     if (inf.status != JQCD_OK && worst == JQCD_OK) worst = inf.status;
     --left;
   };
+  // The device waits on the host between polls; keeping the next graph
+  // queued during a poll was measured slower (0.159 against 0.155 s of
+  // iterations for the 24-solve batch on GB300), so the loop stays simple.
   while (E->running() > 0) {
+    if (graph_time) cudaEventRecord(ev.a, ctx->stream);
     CK(E->run(8), "batch iterations");
+    if (graph_time) cudaEventRecord(ev.b, ctx->stream);
     done.clear();
     CK(E->poll(&done), "batch poll");
+    ++n_polls;
+    float ms = 0.f;
+    if (graph_time && cudaEventElapsedTime(&ms, ev.a, ev.b) == cudaSuccess) t_graphs += 1e-3 * ms;
     // solutions of finished solves go to the host while the others iterate
     const auto c0 = std::chrono::steady_clock::now();
     for (int i : done) CK(E->collect_async(i, x[i]), "batch collect");
@@ -495,8 +514,10 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
     auto sec = [](std::chrono::steady_clock::time_point a, std::chrono::steady_clock::time_point b) {
       return std::chrono::duration<double>(b - a).count();
     };
-    fprintf(stderr, "jqcd batch: admit %.4f s, autotune %.4f s, iterate+collect %.4f s (collect %.4f s)\n",
-            sec(t0, t1), sec(t1, t2), sec(t2, t3), t_collect);
+    fprintf(stderr,
+            "jqcd batch: admit %.4f s, autotune %.4f s, iterate+collect %.4f s (collect %.4f s; "
+            "iteration graphs %.4f s of device time over %d polls)\n",
+            sec(t0, t1), sec(t1, t2), sec(t2, t3), t_collect, t_graphs, n_polls);
   }
   if (worst != JQCD_OK) return fail(ctx, worst, "cg_solve_batch: a solve did not converge");
   return JQCD_OK;
