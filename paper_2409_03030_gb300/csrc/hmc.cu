@@ -8,9 +8,9 @@
 //   U dS_g/dU_mu(x) = -(beta/3) U_mu(x) V_mu(x) (V: the six staples),
 //   P = i sum_a p^a T^a, T^a = lambda^a / 2, K = -sum Tr P^2 = sum (p^a)^2 / 2,
 //   dP/dt = TA(U dS/dU) / 2, dU/dt = P U, TA(G) = (G - G^dag)/2 - Tr(G - G^dag)/6.
-// The gauge kernels run in native FP64; the FP64 links are the master copy and the
-// double-word and 12-real FP32 copies are refreshed from them after every
-// update.  Layouts: FP64 link-type fields double2[2][4][9][vh] (parity, mu,
+// The FP64 links are the master copy (link update, plaquette and momenta in
+// native FP64); the double-word and 12-real FP32 copies are refreshed from
+// them after every update, and the staple force runs on the double-word copy.  Layouts: FP64 link-type fields double2[2][4][9][vh] (parity, mu,
 // element 3a+b, checkerboard site), like the uploaded FP64 gauge field.
 #include <cuda_runtime.h>
 
@@ -20,6 +20,7 @@
 
 #include "dw.cuh"
 #include "hmc.h"
+#include "hop_dwp.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
 #include "solver.h"
@@ -40,7 +41,7 @@ __device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
 __device__ __forceinline__ double2 cadd_d(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 
 // 3x3 complex product accumulated in FMAs: 2 multiplies and 10 FMAs per
-// element (the FP64 pipe is the bound of every gauge kernel here).
+// element (the FP64 pipe bounds the FP64 gauge kernels).
 __device__ __forceinline__ m3 m3_mul(const m3 &A, const m3 &B) {
   m3 r;
 #pragma unroll
@@ -99,40 +100,100 @@ __device__ __forceinline__ void site_of_thread(const Geom &g, int64_t q, int *p,
   cb_coords(g, *cb, *p, c[0], c[1], c[2], c[3]);
 }
 
-// U dS_g/dU for every link: one thread per (site, mu)
-__global__ void __launch_bounds__(kHmcThreads) gauge_force_kernel(Geom g, const double2 *__restrict__ U, double beta,
-                                                                  double2 *__restrict__ out) {
+// ---- U dS_g/dU for every link, in double-word arithmetic -------------------
+// One thread per (site, mu) sums the six staples of its link on the
+// double-word copy of the links (refreshed from the FP64 masters after every
+// link update) and multiplies by U_mu(x).  Each 3x3 product is three
+// offset-grid mat-vecs (matvec_half_p: exact products on a fixed grid, a few
+// 1e-14 relative per product) on the FP32 pipes; in native FP64 the same
+// sums were bound by the FP64 pipe (707.6 against 143 us at 16^4 on GB300).
+struct m3p {
+  p2 e[3][3];
+};
+
+__device__ __forceinline__ m3p m3p_load(const float4 *U, int64_t vh, int p, int mu, int64_t cb) {
+  m3p r;
+  const ulonglong2 *q = reinterpret_cast<const ulonglong2 *>(U) + (size_t)((p * 4 + mu) * 9) * vh + cb;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const ulonglong2 v = __ldg(q + k * vh);
+    r.e[k / 3][k % 3] = p2{v.x, v.y};
+  }
+  return r;
+}
+__device__ __forceinline__ m3p m3p_dag(const m3p &A) {
+  m3p r;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) r.e[a][b] = p2_conj(A.e[b][a]);
+  return r;
+}
+// C = A B, column by column; the results normalised (Fast2Sum per lane)
+__device__ __forceinline__ m3p m3p_mul(const m3p &A, const m3p &B) {
+  const float amax = link_max_hi(A.e) * 1.0000019f;  // raised as in the hop (matvec_half_p)
+  m3p C;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const p2 col[3] = {B.e[0][b], B.e[1][b], B.e[2][b]};
+    p2 r[3];
+    matvec_half_p(A.e, amax, col, r);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) C.e[a][b] = p2_norm(r[a]);
+  }
+  return C;
+}
+__device__ __forceinline__ m3p link_at_dw(const float4 *U, const Geom &g, const int c[4], int nu, int mu1, int s1,
+                                          int mu2, int s2) {
+  int d[4] = {c[0], c[1], c[2], c[3]};
+  const int n1 = mu1 == 0 ? g.nx : (mu1 == 1 ? g.ny : (mu1 == 2 ? g.nz : g.nt));
+  const int n2 = mu2 == 0 ? g.nx : (mu2 == 1 ? g.ny : (mu2 == 2 ? g.nz : g.nt));
+  if (s1) d[mu1] = (d[mu1] + s1 + n1) % n1;
+  if (s2) d[mu2] = (d[mu2] + s2 + n2) % n2;
+  return m3p_load(U, g.vh, (d[0] + d[1] + d[2] + d[3]) & 1, nu, cb_index(g, d[0], d[1], d[2], d[3]));
+}
+
+__global__ void __launch_bounds__(kHmcThreads) gauge_force_dw_kernel(Geom g, const float4 *__restrict__ U,
+                                                                     double beta, double2 *__restrict__ out) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= 8 * g.vh) return;
   const int mu = (int)(q / (2 * g.vh));
   int p, c[4];
   int64_t cb;
   site_of_thread(g, q % (2 * g.vh), &p, &cb, c);
-  m3 V;
+  m3p V;
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int b = 0; b < 3; ++b) V.e[a][b] = make_double2(0.0, 0.0);
+    for (int b = 0; b < 3; ++b) V.e[a][b] = p2{0ull, 0ull};
+#pragma unroll 1
   for (int nu = 0; nu < 4; ++nu) {
     if (nu == mu) continue;
     // upper staple U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
-    const m3 up = m3_mul(m3_mul(link_at(U, g, c, nu, mu, 1, nu, 0), m3_dag(link_at(U, g, c, mu, nu, 1, mu, 0))),
-                         m3_dag(link_at(U, g, c, nu, mu, 0, nu, 0)));
-    // lower staple U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
-    const m3 dn = m3_mul(m3_mul(m3_dag(link_at(U, g, c, nu, mu, 1, nu, -1)), m3_dag(link_at(U, g, c, mu, nu, -1, mu, 0))),
-                         link_at(U, g, c, nu, nu, -1, mu, 0));
+    m3p T = m3p_mul(link_at_dw(U, g, c, nu, mu, 1, nu, 0), m3p_dag(link_at_dw(U, g, c, mu, nu, 1, mu, 0)));
+    m3p S = m3p_mul(T, m3p_dag(link_at_dw(U, g, c, nu, mu, 0, nu, 0)));
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int b = 0; b < 3; ++b) V.e[a][b] = cadd_d(V.e[a][b], cadd_d(up.e[a][b], dn.e[a][b]));
+      for (int b = 0; b < 3; ++b) V.e[a][b] = p2_add(V.e[a][b], S.e[a][b]);
+    // lower staple U_nu(x+mu-nu)^dag U_mu(x-nu)^dag U_nu(x-nu)
+    T = m3p_mul(m3p_dag(link_at_dw(U, g, c, nu, mu, 1, nu, -1)), m3p_dag(link_at_dw(U, g, c, mu, nu, -1, mu, 0)));
+    S = m3p_mul(T, link_at_dw(U, g, c, nu, nu, -1, mu, 0));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) V.e[a][b] = p2_norm(p2_add(V.e[a][b], S.e[a][b]));
   }
-  m3 G = m3_mul(m3_load(U, g.vh, p, mu, cb), V);
+  const m3p G = m3p_mul(m3p_load(U, g.vh, p, mu, cb), V);
   const double f = -beta / 3.0;
+  double2 *o = out + (size_t)((p * 4 + mu) * 9) * g.vh + cb;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int b = 0; b < 3; ++b) G.e[a][b] = make_double2(f * G.e[a][b].x, f * G.e[a][b].y);
-  m3_store(out, g.vh, p, mu, cb, G);
+  for (int k = 0; k < 9; ++k) {
+    float hr, hi, lr, li;
+    f2_split(G.e[k / 3][k % 3].h, hr, hi);
+    f2_split(G.e[k / 3][k % 3].l, lr, li);
+    o[k * g.vh] = make_double2(f * ((double)hr + (double)lr), f * ((double)hi + (double)li));
+  }
 }
 
 // per-block partials of sum_{mu<nu} Re Tr P_munu(x): one thread per site
@@ -465,7 +526,7 @@ cudaError_t hmc_momenta_set(GaugeEntry &G, const double *normals_dev, cudaStream
 
 cudaError_t hmc_gauge_force(GaugeEntry &G, double beta, cudaStream_t s) {
   note_launch();
-  gauge_force_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (const double2 *)G.gauge_f64, beta, G.hG);
+  gauge_force_dw_kernel<<<link_blocks(G.g.vh), kHmcThreads, 0, s>>>(G.g, (const float4 *)G.gauge_dw, beta, G.hG);
   return cudaGetLastError();
 }
 
