@@ -67,8 +67,8 @@ __device__ __forceinline__ dwacc dwp_store_cg(const p2 (&v)[NC], int k0, const f
   return dwacc{s, __fadd_rn(__fadd_rn(c0, c1), e)};
 }
 
-template <bool XUPD>
-__global__ void __launch_bounds__(kDwp1Threads, JQCD_DWP_MIN_BLOCKS)
+template <bool XUPD, int MINB>
+__global__ void __launch_bounds__(kDwp1Threads, MINB)
     hop_dwp_cg_kernel(const HopParams P, const float4 *__restrict__ p, float4 *__restrict__ xs,
                       float4 *__restrict__ r, const float2 *__restrict__ alpha) {
   extern __shared__ float4 dsm[];
@@ -191,8 +191,11 @@ static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x
   note_launch();
   static bool configured = false;  // one attribute call per instantiation
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDwp1Smem);
+    cudaError_t e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD, JQCD_DWP_MIN_BLOCKS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwp1Smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(hop_dwp_cg_kernel<XUPD, JQCD_DWP_SMALL_MIN_BLOCKS>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDwp1Smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(hop_dwp2_cg_kernel<XUPD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kDwp2Smem);
@@ -202,8 +205,11 @@ static cudaError_t launch_dw_cg_t(const HopParams &P, const float4 *p, float4 *x
   if (dw_hop_split(P.g.vh))
     return launch_pdl(hop_dwp2_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kDwp2Threads, kDwp2Smem, s, P, p, x,
                       r, alpha);
-  return launch_pdl(hop_dwp_cg_kernel<XUPD>, dw_hop_blocks(P.g.vh), kDwp1Threads, kDwp1Smem, s, P, p, x, r,
-                    alpha);
+  if (dw_hop_small(P.g.vh))
+    return launch_pdl(hop_dwp_cg_kernel<XUPD, JQCD_DWP_SMALL_MIN_BLOCKS>, dw_hop_blocks(P.g.vh), kDwp1Threads,
+                      kDwp1Smem, s, P, p, x, r, alpha);
+  return launch_pdl(hop_dwp_cg_kernel<XUPD, JQCD_DWP_MIN_BLOCKS>, dw_hop_blocks(P.g.vh), kDwp1Threads, kDwp1Smem,
+                    s, P, p, x, r, alpha);
 }
 
 cudaError_t launch_hop_dw_cg(const HopParams &P, const float4 *p, float4 *x, float4 *r,

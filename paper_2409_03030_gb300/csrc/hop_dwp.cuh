@@ -39,6 +39,12 @@ constexpr size_t kDwpSmem = dwp_smem();
 #ifndef JQCD_DWP_MIN_BLOCKS
 #define JQCD_DWP_MIN_BLOCKS 3
 #endif
+// Lattices whose one-thread grid fits in SMs x JQCD_DWP_SMALL_MIN_BLOCKS
+// blocks (16^4) run the same kernel compiled for that many blocks per SM:
+// the register budget, not the occupancy, limits them there.
+#ifndef JQCD_DWP_SMALL_MIN_BLOCKS
+#define JQCD_DWP_SMALL_MIN_BLOCKS 2
+#endif
 #ifndef JQCD_DWP2_THREADS
 #define JQCD_DWP2_THREADS 32
 #endif

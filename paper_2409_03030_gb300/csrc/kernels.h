@@ -41,6 +41,13 @@ cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool n
 #define JQCD_DWP_SPLIT_MAX_VH 65536
 #endif
 bool dw_hop_split(int64_t vh);
+// Lattices one size up (at most JQCD_DWP_SMALL_MAX_VH sites per parity and a
+// one-thread grid that fits in one wave at a lower occupancy) run one thread
+// per site compiled with a larger register budget.
+#ifndef JQCD_DWP_SMALL_MAX_VH
+#define JQCD_DWP_SMALL_MAX_VH 65536
+#endif
+bool dw_hop_small(int64_t vh);
 unsigned dw_hop_blocks(int64_t vh);                 // blocks of a double-word hop launch
 unsigned hop_norm_partials(int prec, int64_t vh);   // partials of a hop launch with norm
 
