@@ -163,16 +163,18 @@ def test_hop_dw_magnitudes(jq, case, dagger):
     g.free()
 
 
+@pytest.mark.parametrize("dims", [(10, 10, 10, 134), (10, 10, 10, 66)])
 @pytest.mark.parametrize("dagger", [0, 1])
-def test_hop_dw_one_thread_per_site_ragged(jq, dagger):
-    """Double-word hop above the two-threads-per-site size (10^3x134: 67,000
-    sites per parity, a ragged last block of one thread per site), with the
-    fused axpy and norm, against the oracle.  Every smaller lattice of these
-    tests runs the two-threads-per-site kernels."""
+def test_hop_dw_one_thread_per_site_ragged(jq, dagger, dims):
+    """Double-word hop above the two-threads-per-site size, one thread per
+    site with a ragged last block, with the fused axpy and norm, against the
+    oracle: 10^3x134 (67,000 sites per parity) runs the kernel of large
+    lattices, 10^3x66 (33,000, between the split limit and two blocks per SM
+    on 152 SMs) the same kernel compiled for two blocks per SM.  Every smaller
+    lattice of these tests runs the two-threads-per-site kernels."""
     jqcd, ctx = jq
     import torch
-    dims = (10, 10, 10, 134)
-    assert np.prod(dims) // 2 > 65536 and (np.prod(dims) // 2) % 128 != 0
+    assert np.prod(dims) // 2 > 29184 and (np.prod(dims) // 2) % 128 != 0
     U = synth.gauge(dims, "expi", eps=0.3, seed=41)
     g = ctx.gauge_upload(dims, U, t_antiperiodic=True)
     psi = synth.gaussian_spinor(dims, seed=42)
