@@ -9,6 +9,7 @@
 #include "dw.cuh"
 #include "kernels.h"
 #include "pdl.cuh"
+#include "cg_steps.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -105,80 +106,29 @@ __global__ void dw_xpay_kernel(float4 *__restrict__ p, const float4 *__restrict_
 }
 
 // ---- single-block scalar steps -------------------------------------------------
-__device__ __forceinline__ double sum_partials(const double *partials, int n) {
-  double v = 0.0;
-  // all of a thread's loads are in flight before its first add; the adds keep
-  // the fixed order i = tid, tid + blockDim.x, ... (out-of-range slots add 0)
-  constexpr int kU = 16;
-  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
-    double t[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int i = base + u * (int)blockDim.x;
-      t[u] = i < n ? partials[i] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v += t[u];
-  }
-  return block_sum_d(v);  // valid in thread 0
-}
-
-__device__ __forceinline__ float2 split_d(double v) {
-  const float h = __double2float_rn(v);
-  return make_float2(h, __double2float_rn(v - (double)h));
-}
 
 __global__ void finalize_sum_kernel(const double *partials, int n, double *out) {
-  const double s = sum_partials(partials, n);
+  const double s = block_sum_partials(partials, n);
   if (threadIdx.x == 0) *out = s;
 }
 
 __global__ void cg_alpha_kernel(const double *partials, int n, SolverScalars *S) {
   pdl_enter();
   if (S->halt) return;
-  const double pAp = sum_partials(partials, n);
-  if (threadIdx.x == 0) {
-    S->pAp = pAp;
-    if (!(pAp > 0.0) || !isfinite(pAp)) {  // breakdown: A not positive or NaN
-      S->done = 2;
-      S->halt = 1;
-      return;
-    }
-    const double a = S->rr / pAp;
-    S->alpha = a;
-    S->alpha_dw = split_d(a);
-    S->malpha_dw = split_d(-a);
-    S->alpha_f = (float)a;
-    S->malpha_f = (float)-a;
-  }
+  const double pAp = block_sum_partials(partials, n);
+  if (threadIdx.x == 0) cg_alpha_step(pAp, S);
 }
 
 __global__ void cg_beta_kernel(const double *partials, int n, SolverScalars *S) {
   pdl_enter();
   if (S->halt) return;
-  const double rr_new = sum_partials(partials, n);
-  if (threadIdx.x == 0) {
-    S->rr_new = rr_new;
-    S->iters += 1;
-    if (!isfinite(rr_new)) { S->done = 2; S->halt = 1; return; }
-    if (rr_new <= S->stop_rr) {
-      S->rr = rr_new;
-      S->done = 1;
-      S->halt = 1;
-      return;
-    }
-    if (S->iters >= S->max_iters) { S->done = 3; S->halt = 1; }
-    const double b = rr_new / S->rr;
-    S->beta = b;
-    S->beta_dw = split_d(b);
-    S->beta_f = (float)b;
-    S->rr = rr_new;
-  }
+  const double rr_new = block_sum_partials(partials, n);
+  if (threadIdx.x == 0) cg_beta_step(rr_new, S);
 }
 
 __global__ void cg_start_kernel(const double *partials, int n, SolverScalars *S, double tol2,
                                 int max_iters, double delta2) {
-  const double rr = sum_partials(partials, n);
+  const double rr = block_sum_partials(partials, n);
   if (threadIdx.x == 0) {
     S->rr = rr;
     S->true_rr = rr;  // the start residual is computed from x, not recursively
@@ -189,6 +139,7 @@ __global__ void cg_start_kernel(const double *partials, int n, SolverScalars *S,
     S->halt = S->done != 0;
     S->need_update = 0;
     S->rr_max = rr;
+    S->fin_count = 0;
   }
 }
 

@@ -14,6 +14,7 @@
 #include "fields.cuh"
 #include "kernels.h"
 #include "pdl.cuh"
+#include "cg_steps.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -82,47 +83,15 @@ __global__ void dw_add_f32_kernel(float4 *__restrict__ x, float4 *__restrict__ x
   }
 }
 
-__device__ __forceinline__ double sum_partials_m(const double *partials, int n) {
-  double v = 0.0;
-  // all of a thread's loads are in flight before its first add; the adds keep
-  // the fixed order i = tid, tid + blockDim.x, ... (out-of-range slots add 0)
-  constexpr int kU = 16;
-  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
-    double t[kU];
-#pragma unroll
-    for (int u = 0; u < kU; ++u) {
-      const int i = base + u * (int)blockDim.x;
-      t[u] = i < n ? partials[i] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < kU; ++u) v += t[u];
-  }
-  return block_sum_d(v);
-}
-
 __global__ void mixed_beta_kernel(const double *partials, int n, SolverScalars *S) {
   pdl_enter();
   if (S->halt) return;
-  const double rr_new = sum_partials_m(partials, n);
-  if (threadIdx.x == 0) {
-    S->rr_new = rr_new;
-    S->iters += 1;
-    if (!isfinite(rr_new)) { S->done = 2; S->halt = 1; return; }
-    if (rr_new <= S->stop_rr || rr_new < S->delta2 * S->rr_max || S->iters >= S->max_iters) {
-      S->need_update = 1;  // the host runs the double-word update next
-      S->halt = 1;
-      return;
-    }
-    const double b = rr_new / S->rr;
-    S->beta = b;
-    S->beta_f = (float)b;
-    S->rr = rr_new;
-    if (rr_new > S->rr_max) S->rr_max = rr_new;
-  }
+  const double rr_new = block_sum_partials(partials, n);
+  if (threadIdx.x == 0) mixed_beta_step(rr_new, S);
 }
 
 __global__ void mixed_after_update_kernel(const double *partials, int n, SolverScalars *S) {
-  const double rr_true = sum_partials_m(partials, n);
+  const double rr_true = block_sum_partials(partials, n);
   if (threadIdx.x == 0) {
     S->reliable_updates += 1;
     S->need_update = 0;

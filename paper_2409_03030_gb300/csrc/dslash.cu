@@ -16,6 +16,7 @@
 #include "hop_dw.cuh"
 #include "hop_dwp.cuh"
 #include "hop_lp.cuh"
+#include "cg_steps.cuh"
 #include "reduce.cuh"
 
 namespace jqcd {
@@ -116,6 +117,7 @@ __global__ void __launch_bounds__(kHopThreads) hop_kernel(const HopParams P) {
   if (NORM) {
     const double s = PREC == PREC_F64 ? block_sum_d(nrm64) : block_sum_dw(nrm);
     if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+    if (P.fin) hop_finish_scalars(P);  // uniform over the grid
   }
 }
 
@@ -155,6 +157,7 @@ __global__ void __launch_bounds__(kHopThreads) hop_lp_kernel(const HopParams P) 
   if (NORM) {
     const double s = block_sum_dw(nrm);
     if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+    if (P.fin) hop_finish_scalars(P);  // uniform over the grid
   }
 }
 
@@ -327,6 +330,11 @@ static cudaError_t launch_hop_dw(const HopParams &P, bool dag, bool axpy, bool n
 
 cudaError_t launch_hop(int prec, const HopParams &P, bool dag, bool axpy, bool norm,
                        cudaStream_t s) {
+  // the last-block scalar step (FP64, FP32 and FP16 hops) needs the partials
+  // and at most JQCD_FIN_MAX_BLOCKS of them
+  if (P.fin && (prec == PREC_DW || !norm || !P.fin_S ||
+                hop_norm_partials(prec, P.g.vh) > (unsigned)JQCD_FIN_MAX_BLOCKS))
+    return cudaErrorInvalidValue;
   switch (prec) {
     case PREC_DW: return launch_hop_dw(P, dag, axpy, norm, s);
     case PREC_F64: return launch_hop_p<PREC_F64>(P, dag, axpy, norm, s);

@@ -16,6 +16,7 @@
 #include "hop_lp.cuh"
 #include "kernels.h"
 #include "pdl.cuh"
+#include "cg_steps.cuh"
 #include "reduce.cuh"
 #include "solver.h"
 
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(kHopThreads)
   }
   const double s = block_sum_f(n2);
   if (threadIdx.x == 0) P.partials[blockIdx.x] = s;
+  if (P.fin) hop_finish_scalars(P);  // uniform over the grid
 }
 
 template <int PREC>
@@ -178,6 +180,7 @@ cudaError_t launch_lp_cg_t(const HopParams &P, const void *p, float4 *xs, float4
 cudaError_t launch_hop_lp_cg(int prec, const HopParams &P, const void *p, float4 *xs, float4 *rs,
                              const SolverScalars *S, cudaStream_t s) {
   note_launch();
+  if (P.fin && (!P.fin_S || hop_blocks(P.g.vh) > (unsigned)JQCD_FIN_MAX_BLOCKS)) return cudaErrorInvalidValue;
   switch (prec) {
     case PREC_F32: return launch_lp_cg_t<PREC_F32>(P, p, xs, rs, S, s);
     case PREC_F16N: return launch_lp_cg_t<PREC_F16N>(P, p, xs, rs, S, s);

@@ -14,6 +14,15 @@ void note_launch(int64_t n = 1);
 constexpr int kHopThreads = 128;
 inline unsigned hop_blocks(int64_t vh) { return (unsigned)((vh + kHopThreads - 1) / kHopThreads); }
 
+struct SolverScalars;
+// Scalar step the last block of a hop launch with norm takes (cg_steps.cuh)
+enum { FIN_NONE = 0, FIN_ALPHA = 1, FIN_BETA = 2, FIN_MIXED_BETA = 3 };
+// Grids of at most this many blocks take the scalar steps in their last block
+// instead of a separate single-block launch.
+#ifndef JQCD_FIN_MAX_BLOCKS
+#define JQCD_FIN_MAX_BLOCKS 1024
+#endif
+
 struct HopParams {
   void *out;
   const void *in;
@@ -25,6 +34,8 @@ struct HopParams {
   float2 a_split, b_split;
   double *partials;   // one per hop block when norm
   const int *guard;   // when non-null and *guard != 0 the launch does nothing
+  SolverScalars *fin_S;  // with fin != FIN_NONE (and norm): the scalars the last block updates
+  int fin;
 };
 
 // out_p = a x_p + b H_{p,1-p} in (dag: adjoint hop); partials get per-block
@@ -89,7 +100,8 @@ struct SolverScalars {
   int max_iters;
   int halt;         // loop kernels return at once while nonzero (done or need_update)
   int reliable_updates;
-  int pad0, pad1;
+  int fin_count;    // blocks of the current hop launch that have written their partial
+  int pad1;
 };
 
 // sum of partials[0..n) in a fixed order -> *out

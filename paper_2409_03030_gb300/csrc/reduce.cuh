@@ -65,4 +65,24 @@ __device__ __forceinline__ double block_sum_d(double v) {
   return block_sum_warp_values(v);
 }
 
+// sum of partials[0..n) by the whole block in a fixed order (valid in
+// thread 0): all of a thread's loads are in flight before its first add;
+// the adds keep the order i = tid, tid + blockDim.x, ... (out-of-range
+// slots add 0), then the block tree.
+__device__ __forceinline__ double block_sum_partials(const double *partials, int n) {
+  double v = 0.0;
+  constexpr int kU = 16;
+  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
+    double t[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * (int)blockDim.x;
+      t[u] = i < n ? partials[i] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v += t[u];
+  }
+  return block_sum_d(v);
+}
+
 }  // namespace jqcd

@@ -214,6 +214,14 @@ struct DwSystem {
 // w = Mhat p with ||w||^2 = <p, Mhat^dag Mhat p> fused into the second hop,
 // alpha, then the last hop of Mhat^dag w applies x += alpha p, r -= alpha Ap
 // and forms ||r||^2 itself (Ap is never stored), beta, p = r + beta p.
+// The inner solver of the mixed CG on small grids (at most
+// JQCD_FIN_MAX_BLOCKS hop blocks) takes alpha and beta in the last block of
+// the hop that writes their partials (cg_steps.cuh) instead of a
+// single-block launch after it (measured on GB300: mixed FP16 solve at 16^4
+// 3.08 -> 2.83 ms).  The double-word iteration keeps the separate launches:
+// there the last-block form gained nothing at 16^4 and lost 2% at 8^4.
+static bool fuse_scalar_steps(int nb) { return nb <= JQCD_FIN_MAX_BLOCKS; }
+
 cudaError_t dw_eo_cg_iteration(GaugeEntry &G, double kappa, SolverScalars *S, cudaStream_t s) {
   const double k2 = -kappa * kappa;
   const int nb = (int)dw_hop_blocks(G.g.vh);
@@ -249,6 +257,7 @@ cudaError_t lp_eo_cg_iteration(GaugeEntry &G, int hp, int mk, double kappa, Solv
                                cudaStream_t s) {
   const double k2 = -kappa * kappa;
   const int nb = (int)hop_blocks(G.g.vh);
+  const bool fuse = fuse_scalar_steps(nb);
   const int *guard = &S->halt;
   void *p = G.mp[mk], *t = G.mt[mk], *w = G.mw[mk];
   HopParams P = G.hop_params(hp, 1, p, nullptr, t, 0.0, 1.0, nullptr);
@@ -257,20 +266,26 @@ cudaError_t lp_eo_cg_iteration(GaugeEntry &G, int hp, int mk, double kappa, Solv
   if (e) return e;
   P = G.hop_params(hp, 0, t, p, w, 1.0, k2, G.partials);
   P.guard = guard;
+  if (fuse) {
+    P.fin = FIN_ALPHA;
+    P.fin_S = S;
+  }
   e = launch_hop(hp, P, false, true, true, s);  // w = p - k^2 H_eo t, ||w||^2
   if (e) return e;
-  e = launch_cg_alpha(G.partials, nb, S, s);
-  if (e) return e;
+  if (!fuse && (e = launch_cg_alpha(G.partials, nb, S, s))) return e;
   P = G.hop_params(hp, 1, w, nullptr, t, 0.0, 1.0, nullptr);
   P.guard = guard;
   e = launch_hop(hp, P, true, false, false, s);  // t = H^dag_oe w
   if (e) return e;
   P = G.hop_params(hp, 0, t, w, nullptr, 1.0, k2, G.partials);
   P.guard = guard;
+  if (fuse) {
+    P.fin = FIN_MIXED_BETA;
+    P.fin_S = S;
+  }
   e = launch_hop_lp_cg(hp, P, p, (float4 *)G.mx, (float4 *)G.mr, S, s);
   if (e) return e;
-  e = launch_mixed_beta(G.partials, nb, S, s);
-  if (e) return e;
+  if (!fuse && (e = launch_mixed_beta(G.partials, nb, S, s))) return e;
   return launch_mixed_xpay(hp, p, (const float4 *)G.mr, G.g.vh, S, s);
 }
 
