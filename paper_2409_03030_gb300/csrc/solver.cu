@@ -34,6 +34,9 @@ GaugeEntry::~GaugeEntry() {
   if (ms_S_host) cudaFreeHost(ms_S_host);
   if (ev0) cudaEventDestroy(ev0);
   if (ev1) cudaEventDestroy(ev1);
+  if (ev_fork) cudaEventDestroy(ev_fork);
+  if (ev_join) cudaEventDestroy(ev_join);
+  if (side) cudaStreamDestroy(side);
 }
 
 cudaError_t GaugeEntry::alloc(void **p, size_t bytes) {
@@ -54,6 +57,9 @@ int GaugeEntry::n_partials() const {
 
 cudaError_t GaugeEntry::ensure_reduce() {
   cudaError_t e = cudaSuccess;
+  if (!side) e = cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ev_fork) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ev_join) e = cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming);
   if (!partials) e = alloc_t(&partials, sizeof(double) * n_partials());
   if (e == cudaSuccess && !S) e = alloc_t(&S, sizeof(SolverScalars));
   if (e == cudaSuccess && !S_host) e = cudaMallocHost(&S_host, sizeof(SolverScalars));
@@ -222,6 +228,24 @@ struct DwSystem {
 // there the last-block form gained nothing at 16^4 and lost 2% at 8^4.
 static bool fuse_scalar_steps(int nb) { return nb <= JQCD_FIN_MAX_BLOCKS; }
 
+// alpha = rr / <p, A p> from the partials of the hop just queued on s, on
+// the side stream: the next hop (t = H^dag_oe w) does not read alpha, so the
+// single-block step runs beside it; s waits for it before the last hop
+// (measured on GB300: double-word solve 33.62 -> 33.53 ms at 24^3x48, 4.48 ->
+// 4.39 ms at 16^4; mixed FP16 13.90 -> 13.81 ms).
+static cudaError_t alpha_fork(GaugeEntry &G, int nb, SolverScalars *S, cudaStream_t s) {
+  if (!G.side) return launch_cg_alpha(G.partials, nb, S, s);
+  cudaError_t e = cudaEventRecord(G.ev_fork, s);
+  if (!e) e = cudaStreamWaitEvent(G.side, G.ev_fork, 0);
+  if (!e) e = launch_cg_alpha(G.partials, nb, S, G.side);
+  if (!e) e = cudaEventRecord(G.ev_join, G.side);
+  return e;
+}
+static cudaError_t alpha_join(GaugeEntry &G, cudaStream_t s) {
+  if (!G.side) return cudaSuccess;
+  return cudaStreamWaitEvent(s, G.ev_join, 0);
+}
+
 cudaError_t dw_eo_cg_iteration(GaugeEntry &G, double kappa, SolverScalars *S, cudaStream_t s) {
   const double k2 = -kappa * kappa;
   const int nb = (int)dw_hop_blocks(G.g.vh);
@@ -235,11 +259,13 @@ cudaError_t dw_eo_cg_iteration(GaugeEntry &G, double kappa, SolverScalars *S, cu
   P.guard = guard;
   e = launch_hop(PREC_DW, P, false, true, true, s);  // w = p - k^2 H_eo t, ||w||^2
   if (e) return e;
-  e = launch_cg_alpha(G.partials, nb, S, s);
+  e = alpha_fork(G, nb, S, s);
   if (e) return e;
   P = G.hop_params(PREC_DW, 1, w, nullptr, t, 0.0, 1.0, nullptr);
   P.guard = guard;
   e = launch_hop(PREC_DW, P, true, false, false, s);  // t = H^dag_oe w
+  if (e) return e;
+  e = alpha_join(G, s);
   if (e) return e;
   P = G.hop_params(PREC_DW, 0, t, w, nullptr, 1.0, k2, G.partials);
   P.guard = guard;
@@ -272,11 +298,12 @@ cudaError_t lp_eo_cg_iteration(GaugeEntry &G, int hp, int mk, double kappa, Solv
   }
   e = launch_hop(hp, P, false, true, true, s);  // w = p - k^2 H_eo t, ||w||^2
   if (e) return e;
-  if (!fuse && (e = launch_cg_alpha(G.partials, nb, S, s))) return e;
+  if (!fuse && (e = alpha_fork(G, nb, S, s))) return e;
   P = G.hop_params(hp, 1, w, nullptr, t, 0.0, 1.0, nullptr);
   P.guard = guard;
   e = launch_hop(hp, P, true, false, false, s);  // t = H^dag_oe w
   if (e) return e;
+  if (!fuse && (e = alpha_join(G, s))) return e;
   P = G.hop_params(hp, 0, t, w, nullptr, 1.0, k2, G.partials);
   P.guard = guard;
   if (fuse) {

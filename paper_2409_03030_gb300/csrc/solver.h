@@ -49,6 +49,10 @@ struct GaugeEntry {
   double *hNormals = nullptr;
   double *hPart = nullptr;  // per-block partials of the HMC reductions
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // a second stream for the CG's alpha step, which runs beside the hop that
+  // follows it (fork and join events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void *> device_allocs;
 
   ~GaugeEntry();
