@@ -280,10 +280,20 @@ jqcd_status solve_multishift(GaugeEntry &G, const jqcd_solve_params &P, int nshi
     H = G.hop_params(PREC_DW, 0, t, pb, w, 1.0, k2, G.partials);
     H.guard = &S->halt;
     if ((e = launch_hop(PREC_DW, H, false, true, true, s))) return e;
-    if ((e = launch_ms_alpha(G.partials, nhop, S, s))) return e;
+    // the alpha step runs on the side stream beside t = H^dag_oe w, which
+    // does not read it; the last hop waits for it
+    if (G.side) {
+      if ((e = cudaEventRecord(G.ev_fork, s))) return e;
+      if ((e = cudaStreamWaitEvent(G.side, G.ev_fork, 0))) return e;
+      if ((e = launch_ms_alpha(G.partials, nhop, S, G.side))) return e;
+      if ((e = cudaEventRecord(G.ev_join, G.side))) return e;
+    } else if ((e = launch_ms_alpha(G.partials, nhop, S, s))) {
+      return e;
+    }
     H = G.hop_params(PREC_DW, 1, w, nullptr, t, 0.0, 1.0, nullptr);
     H.guard = &S->halt;
     if ((e = launch_hop(PREC_DW, H, true, false, false, s))) return e;
+    if (G.side && (e = cudaStreamWaitEvent(s, G.ev_join, 0))) return e;
     H = G.hop_params(PREC_DW, 0, t, w, nullptr, 1.0, k2, G.partials);
     H.guard = &S->halt;
     if ((e = launch_hop_dw_r(H, r, &S->alpha_dw, s))) return e;
