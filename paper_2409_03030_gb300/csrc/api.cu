@@ -370,9 +370,15 @@ jqcd_status jqcd_cg_solve(jqcd_ctx *ctx, uint64_t gauge_id, const jqcd_solve_par
   jqcd_solve_info inf;
   memset(&inf, 0, sizeof inf);
   std::string msg;
+  G->x_host_out = x;  // the solve copies x out while it computes the full residual
   st = solve_resident(*G, *params, s, &inf, &msg);
+  G->x_host_out = nullptr;
+  const bool queued = G->x_host_queued;
+  G->x_host_queued = false;
   if (st == JQCD_ECUDA) ctx->poisoned = true;
-  if (st == JQCD_OK || st == JQCD_ENOCONV) {
+  if (queued) {
+    CK(cudaEventSynchronize(G->ev_join), "x copy");
+  } else if (st == JQCD_OK || st == JQCD_ENOCONV) {
     CK(launch_spinor_unpack(G->g, PREC_DW, G->vec_even(G->vsol), G->vec_odd(G->vsol), G->canon, s),
        "x unpack");
     CK(cudaMemcpyAsync(x, G->canon, G->canon_bytes(), cudaMemcpyDeviceToHost, s), "x D2H");

@@ -502,6 +502,15 @@ static jqcd_status solve_cg(GaugeEntry &G, const jqcd_solve_params &P, cudaStrea
     A.count(0, 1);
   }
   CKS(cudaEventRecord(G.ev1, s));
+  G.x_host_queued = false;
+  if (G.x_host_out && G.side && (st == JQCD_OK || st == JQCD_ENOCONV)) {
+    // x is final: its unpack and copy to the host overlap the residual below
+    CKS(cudaStreamWaitEvent(G.side, G.ev1, 0));
+    CKS(launch_spinor_unpack(G.g, PREC_DW, G.vec_even(G.vsol), G.vec_odd(G.vsol), G.canon, G.side));
+    CKS(cudaMemcpyAsync(G.x_host_out, G.canon, G.canon_bytes(), cudaMemcpyDeviceToHost, G.side));
+    CKS(cudaEventRecord(G.ev_join, G.side));
+    G.x_host_queued = true;
+  }
   // ||b - D x||^2 (not part of the timed solve)
   CKS(apply_dirac_dw(G, P.kappa, false, G.vsol, G.vw, nullptr, nullptr, s));
   CKS(launch_dw_xmy_norm(G.vAp, G.vb, G.vw, 24 * vh, G.partials, s));

@@ -53,6 +53,12 @@ struct GaugeEntry {
   // follows it (fork and join events)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // host destination of the canonical solution: when set, the solve queues
+  // its unpack and copy on the side stream as soon as x is final (while the
+  // full-system residual is computed) and sets x_host_queued; the caller
+  // then waits for ev_join instead of copying x itself
+  double *x_host_out = nullptr;
+  bool x_host_queued = false;
   std::vector<void *> device_allocs;
 
   ~GaugeEntry();
