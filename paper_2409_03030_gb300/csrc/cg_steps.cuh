@@ -1,5 +1,6 @@
-// Scalar steps of the conjugate gradient (Sec. 3 of the paper: alpha =
-// ||r||^2 / <p, A p>, beta = ||r_new||^2 / ||r||^2, the stopping test), run
+// Scalar steps of the conjugate gradient of the paper's solver (section
+// "Definition of Dirac operators", solve_DinvX! with eps_CG): alpha =
+// ||r||^2 / <p, A p>, beta = ||r_new||^2 / ||r||^2, the stopping test; run
 // by thread 0 of the block that holds the fixed-order sum of a hop's
 // per-block partials.  The single-block kernels of blas.cu and blas_mixed.cu
 // call them; on small grids the last block of the hop that writes the

@@ -1,7 +1,7 @@
 // Last hop of the double-word even-odd normal operator fused with the CG
-// update (conjugate gradient on Mhat^dag Mhat, Sec. 3 of the paper), for the
-// double-word solver and for the FP32 / FP16-with-norm inner solver of the
-// mixed-precision CG.
+// update (conjugate gradient on Mhat^dag Mhat, the paper's solve_DinvX! in
+// section "Definition of Dirac operators"), for the double-word solver and
+// for the FP32 / FP16-with-norm inner solver of the mixed-precision CG.
 //
 // In one CG iteration alpha = ||r||^2 / <p, Mhat^dag Mhat p> and
 // <p, Mhat^dag Mhat p> = ||Mhat p||^2 are known once the second hop has
