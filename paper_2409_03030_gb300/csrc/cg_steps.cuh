@@ -84,6 +84,24 @@ __device__ __forceinline__ void mixed_beta_step(double rr_new, SolverScalars *S)
   if (rr_new > S->rr_max) S->rr_max = rr_new;
 }
 
+// block_sum_partials with its loads from L2 (ld.global.cg): the partials
+// were written by other blocks of the same launch.
+__device__ __forceinline__ double block_sum_partials_l2(const double *partials, int n) {
+  double v = 0.0;
+  constexpr int kU = 16;
+  for (int base = threadIdx.x; base < n; base += kU * blockDim.x) {
+    double t[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int i = base + u * (int)blockDim.x;
+      t[u] = i < n ? __ldcg(partials + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v += t[u];
+  }
+  return block_sum_d(v);
+}
+
 // Called by every thread of every block of a hop launch after thread 0 has
 // written the block's partial (P.partials[blockIdx.x]) when P.fin is set: the
 // block that finishes last (a counter in P.fin_S, no waiting) sums all the
@@ -100,7 +118,7 @@ __device__ __forceinline__ void hop_finish_scalars(const HopParams &P) {
   __syncthreads();
   if (!is_last) return;  // uniform over the block
   __threadfence();
-  const double v = block_sum_partials(P.partials, (int)gridDim.x);
+  const double v = block_sum_partials_l2(P.partials, (int)gridDim.x);
   if (threadIdx.x == 0) {
     SolverScalars *S = P.fin_S;
     S->fin_count = 0;
