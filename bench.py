@@ -427,18 +427,32 @@ def bench_multishift(jqcd, g, stream, rhs_even):
 
 def bench_batch(ctx, jqcd, synth, np):
     """12 point sources on 24^3x48 + 12 Gaussian sources on 16^4 (kappa 0.12,
-    exp(i 0.3 H) links, tol 1e-10, FP16 inner): one jqcd_cg_solve_batch call
-    vs the same 24 solves one after another through jqcd_cg_solve."""
+    exp(i 0.3 H) links, tol 1e-10): one jqcd_cg_solve_batch call vs the same
+    24 solves one after another through jqcd_cg_solve, with FP16 inner
+    solves; `f32_inner` repeats it with FP32 inner solves (FP32/FP64 mixed)."""
     dA, dB = (24, 24, 24, 48), (16, 16, 16, 16)
     gA = ctx.gauge_upload(dA, synth.gauge(dA, "expi", eps=EPS, seed=31))
     gB = ctx.gauge_upload(dB, synth.gauge(dB, "expi", eps=EPS, seed=32))
     bs = [synth.point_source(dA, s, c) for s in range(4) for c in range(3)]
     bs += [synth.gaussian_spinor(dB, seed=100 + i) for i in range(12)]
     gauges = [gA] * 12 + [gB] * 12
-    mode = jqcd.CG_MIXED_F16
     # pinned host buffers, reused by both ways of solving (no page faults in the timing)
     bs = [pinned_copy(b) for b in bs]
     outs = [pinned_copy(np.zeros_like(b)) for b in bs]
+    out = batch_vs_sequential(ctx, jqcd, gauges, bs, outs, gA, jqcd.CG_MIXED_F16)
+    out["workload"] = ("12 point sources 24^3x48 + 12 Gaussian 16^4, kappa 0.12, tol 1e-10, "
+                       "mixed FP16, one batch (pinned host buffers, reused)")
+    f32 = batch_vs_sequential(ctx, jqcd, gauges, bs, outs, gA, jqcd.CG_MIXED_F32)
+    out["f32_inner"] = {k: f32[k] for k in ("batch_s", "sequential_s", "speedup", "sequential_gpu_s",
+                                            "max_true_rel_resid", "iters", "status")}
+    gA.free()
+    gB.free()
+    return out
+
+
+def batch_vs_sequential(ctx, jqcd, gauges, bs, outs, gA, mode):
+    """Best of three alternating repetitions of one batch call and of the same
+    solves one after another."""
     ctx.cg_solve_batch(gauges, bs, [KAPPA] * 24, [TOL] * 24, mode=mode, out=outs)  # warm-up + autotune
     gA.cg_solve(bs[0], KAPPA, tol=TOL, mode=mode, out=outs[0])  # warm-up
     reps = 3  # both ways alternate; each is reported as the best of its repetitions
@@ -454,17 +468,13 @@ def bench_batch(ctx, jqcd, synth, np):
         ts.append(time.perf_counter() - t0)
         tsg.append(gpu)
     t_batch, t_seq = min(tb), min(ts)
-    out = {"workload": "12 point sources 24^3x48 + 12 Gaussian 16^4, kappa 0.12, tol 1e-10, "
-                       "mixed FP16, one batch (pinned host buffers, reused)",
-           "batch_s": round(t_batch, 4), "sequential_s": round(t_seq, 4),
+    out = {"batch_s": round(t_batch, 4), "sequential_s": round(t_seq, 4),
            "speedup": round(t_seq / t_batch, 3), "solves_per_s": round(24 / t_batch, 2),
            "repetitions": reps, "batch_all_s": [round(v, 4) for v in tb],
            "sequential_all_s": [round(v, 4) for v in ts],
            "sequential_gpu_s": round(min(tsg), 4),  # device time of the 24 solves proper
            "max_true_rel_resid": max(i["true_rel_resid"] for i in infos),
            "iters": [infos[0]["iters"], infos[12]["iters"]], "status": st}
-    gA.free()
-    gB.free()
     return out
 
 
