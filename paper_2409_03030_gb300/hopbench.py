@@ -16,7 +16,11 @@ threshold, the links and the hopping parameter.
 --op hmc: --iters trajectories (10 leapfrog steps, beta 5.5, two Wilson
 flavours at --kappa, solves to 1e-10 in --mode; each trajectory is
 accepted and the next one continues from its links), wall time per
-trajectory."""
+trajectory.
+
+--op multishift: --iters multi-shift solves of Mhat^dag Mhat + sigma for the
+eight shifts 1e-4 ... 0.3 to 1e-10 (double-word) from one Gaussian even-site
+right-hand side, timed by the library's events."""
 from __future__ import annotations
 
 import argparse
@@ -37,7 +41,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--axpy", action="store_true")
     ap.add_argument("--dagger", action="store_true")
-    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg", "hmc"])
+    ap.add_argument("--op", default="wilson", choices=["wilson", "staggered", "force", "cg", "hmc", "multishift"])
     ap.add_argument("--mode", default="mixed_f16", choices=sorted(jqcd.MODES))
     ap.add_argument("--delta", type=float, default=0.0, help="reliable-update threshold (0: library default)")
     ap.add_argument("--eps", type=float, default=0.3, help="link generator exp(i eps H)")
@@ -64,6 +68,24 @@ def main():
             iters = info["cg_iters"]
         print(json.dumps({"op": "hmc", "dims": dims, "mode": a.mode, "cg_iters": iters,
                           "s_per_trajectory": round(sum(secs) / len(secs), 4)}))
+        g.free()
+        ctx.close()
+        return
+    if a.op == "multishift":
+        shifts = [1e-4, 3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 0.1, 0.3]
+        with torch.cuda.stream(stream):
+            rhs, _ = g.pack(synth.gaussian_spinor(dims, seed=2), jqcd.PREC_DW, stream=stream)
+            xs = [g.empty(jqcd.PREC_DW) for _ in shifts]
+        for _ in range(a.warmup):
+            g.cg_multishift_dev(rhs, xs, a.kappa, shifts, tol=1e-10, stream=stream)
+        secs = []
+        for _ in range(a.iters):
+            infos, _ = g.cg_multishift_dev(rhs, xs, a.kappa, shifts, tol=1e-10, stream=stream)
+            secs.append(infos[0]["gpu_seconds"])
+        print(json.dumps({"op": "multishift", "dims": dims, "shifts": shifts, "kappa": a.kappa,
+                          "iters": [i["iters"] for i in infos],
+                          "ms_per_solve": round(1e3 * sum(secs) / len(secs), 3),
+                          "max_true_rel_resid": max(i["true_rel_resid"] for i in infos)}))
         g.free()
         ctx.close()
         return
