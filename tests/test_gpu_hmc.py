@@ -42,10 +42,12 @@ def test_plaquette_and_download(jq):
     g.free()
 
 
-@pytest.mark.parametrize("fermions", [False, True])
-def test_trajectory_vs_oracle(jq, fermions):
+@pytest.mark.parametrize("fermions,dims", [(False, (4, 4, 4, 4)), (True, (4, 4, 4, 4)),
+                                            (False, (8, 8, 8, 8))])
+def test_trajectory_vs_oracle(jq, fermions, dims):
+    """The trajectory against the oracle's; 8^4 without fermions covers the
+    double-word staple force and the link exponential on a larger lattice."""
     jqcd, ctx = jq
-    dims = (4, 4, 4, 4)
     U = synth.gauge(dims, "expi", eps=0.5, seed=172)
     normals = normals_for(dims, 173)
     xi = synth.gaussian_spinor(dims, seed=174) if fermions else None
@@ -58,7 +60,7 @@ def test_trajectory_vs_oracle(jq, fermions):
     assert abs(info["H_old"] - H0) <= 1e-10 * abs(H0)
     assert abs(info["H_new"] - H1) <= gate * abs(H1)
     assert abs(info["dH"] - (H1 - H0)) <= gate * abs(H1)
-    assert abs(info["plaquette"] - oracle.plaquette_sum(dims, U1) / (18 * 256)) <= 1e-12
+    assert abs(info["plaquette"] - oracle.plaquette_sum(dims, U1) / (18 * np.prod(dims))) <= 1e-12
     if fermions:
         assert info["cg_iters"] > 0
     g.free()
