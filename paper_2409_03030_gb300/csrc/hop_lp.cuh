@@ -32,17 +32,15 @@ template <int PREC> constexpr size_t lp_stage_smem() {
 
 // The FP16 site norm of a stage slot sits in the fourth chunk plane at a
 // 4-byte stride (thread t at float t of the plane): one 128-byte wavefront
-// per warp to write and to read, where a 16-byte stride took four.
-#ifndef JQCD_LP_DENSE_NORM
-#define JQCD_LP_DENSE_NORM 1
-#endif
+// per warp to write and to read, where a 16-byte stride took four.  A thread's
+// norm is then not in its own column of the plane, so a kernel that mixes
+// stage layouts in one buffer must keep every word's owner (lp_hop_site).
 __device__ __forceinline__ float *lp_norm_slot(float4 *plane, int tid) {
-  return JQCD_LP_DENSE_NORM ? reinterpret_cast<float *>(plane) + tid : reinterpret_cast<float *>(plane + tid);
+  return reinterpret_cast<float *>(plane) + tid;
 }
 // The same from a thread-offset stage pointer (st = stage + tid).
 __device__ __forceinline__ float lp_norm_read(const float4 *st_plane_tid, int tid) {
-  return JQCD_LP_DENSE_NORM ? reinterpret_cast<const float *>(st_plane_tid - tid)[tid]
-                            : reinterpret_cast<const float *>(st_plane_tid)[0];
+  return reinterpret_cast<const float *>(st_plane_tid - tid)[tid];
 }
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
