@@ -462,27 +462,7 @@ jqcd_status jqcd_cg_solve_batch(jqcd_ctx *ctx, int32_t n, const uint64_t *gauge_
     return std::chrono::steady_clock::now();
   };
   const auto t0 = tnow();
-  // Admission by increasing lattice volume: the solves on the smallest lattice
-  // are admitted first and iterate alone for a few graphs while the larger
-  // lattices' sources copy to the device beside them (the copies of a batch
-  // are gigabytes); then the rest join.  Each admitted set has its own tuned
-  // grid (cached after the first call).
-#ifndef JQCD_BATCH_STAGE_GRAPHS
-#define JQCD_BATCH_STAGE_GRAPHS 3
-#endif
-  std::vector<int> order(n);
-  for (int i = 0; i < n; ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return G[a]->g.vh < G[c]->g.vh; });
-  int first = 0;
-  while (first < n && G[order[first]]->g.vh == G[order[0]]->g.vh) ++first;
-  if (JQCD_BATCH_STAGE_GRAPHS <= 0) first = n;
-  for (int j = 0; j < first; ++j) CK(E->admit(order[j], G[order[j]], params[order[j]], b[order[j]]), "batch admit");
-  if (first < n) {
-    CK(E->autotune(), "batch autotune");
-    for (int k = 0; k < JQCD_BATCH_STAGE_GRAPHS; ++k) CK(E->run(8), "batch iterations");
-    for (int j = first; j < n; ++j)
-      CK(E->admit(order[j], G[order[j]], params[order[j]], b[order[j]]), "batch admit");
-  }
+  for (int i = 0; i < n; ++i) CK(E->admit(i, G[i], params[i], b[i]), "batch admit");
   const auto t1 = tnow();
   CK(E->autotune(), "batch autotune");
   const auto t2 = tnow();
