@@ -57,9 +57,9 @@ HOP_BYTES = {"dw": 1536, "f64": 1536, "f32": 576, "f16n": 488}  # per output sit
 AXPY_BYTES = {"dw": 192, "f64": 192, "f32": 96, "f16n": 52}
 HOP_FLOPS_PER_SITE = 1320  # conventional Wilson hop count per output site (axpy not counted)
 # The sources hop_dwp_kernel is compiled from: its translation unit and the
-# headers it reaches (dslash.cu also includes hop_lp.cuh, whose low-precision
-# kernels this one does not use).  The committed ncu traffic is reported only
-# while their hash matches the one the capture was taken at.
+# headers it reaches (dslash.cu also includes hop_lp.cuh and cg_steps.cuh,
+# which serve the low-precision kernels only).  The committed ncu traffic is
+# reported only while their hash matches the one the capture was taken at.
 HOP_KERNEL_SOURCES = ["dslash.cu", "hop_dwp.cuh", "hop_dw.cuh", "hop.cuh", "dw2.cuh", "dw.cuh",
                       "fields.cuh", "lattice.cuh", "reduce.cuh", "kernels.h", "pdl.cuh"]
 

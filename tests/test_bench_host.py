@@ -82,3 +82,28 @@ def test_profiled_traffic_tracks_kernel_sources(tmp_path, monkeypatch):
     (prof / "hop_dw_24x24x24x48.md").write_text(
         "- kernel_sources_sha256_16: `0000000000000000`\n- dram_bytes_per_launch: 123\n")
     assert bench.profiled_traffic() is None
+
+
+def test_kernel_hash_covers_the_double_word_hop_sources():
+    """The hash that ties the committed ncu traffic to the double-word hop
+    covers exactly the kernel's translation unit and every project header it
+    reaches, less the two headers that serve only the low-precision kernels:
+    a header added to that chain must join the list, or a changed kernel would
+    keep reporting stale traffic."""
+    import re
+    import bench
+    csrc = os.path.join(ROOT, "paper_2409_03030_gb300", "csrc")
+
+    def includes(name):
+        with open(os.path.join(csrc, name)) as fh:
+            return [m for m in re.findall(r'#include\s+"([^"]+)"', fh.read())
+                    if os.path.exists(os.path.join(csrc, m))]
+
+    reached, todo = set(), ["dslash.cu"]
+    while todo:
+        f = todo.pop()
+        if f in reached or f in ("hop_lp.cuh", "cg_steps.cuh"):
+            continue
+        reached.add(f)
+        todo.extend(includes(f))
+    assert reached == set(bench.HOP_KERNEL_SOURCES), sorted(reached ^ set(bench.HOP_KERNEL_SOURCES))
